@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Throughput of the 4DGS rendering routine and its adjoint on one GB300.
+
+One step = the whole hot path over one batch: fgs4d_slice_project ->
+fgs4d_bin_sort -> fgs4d_render -> fgs4d_render_backward for every view of
+the batch.  Workload (the one the headline metric is quoted on): 1M 4D
+Gaussians with clustered means, SH degree 3 x 2 Fourier frequencies, a batch
+of 20 cameras on a forward-facing arc at 1352x1014, each at its own time out
+of 300 frames (seeded synthetic data standing in for Plenoptic-Video-like
+scenes).  The parameters (644 MB) are larger than L2, so no flush is needed.
+
+Printed: one JSON line.  ``value`` is forward+backward Mpix/s with inputs
+resident in HBM; ``e2e`` is the same step through the C ABI with host
+buffers (parameters and dL/dimage copied in, image and gradients copied out
+inside the timed region).  ``fwd_mpix_s`` is forward only and ``single_view``
+the plain one-view-per-call FP32 path on the same GPU.
+
+``--impl reference`` times the FP64 CPU oracle instead (a bounded crop sample
+of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="4dgs-render-fwd+bwd", gaussians=1_000_000, clustered=True, sh_degree=3, n_freq=2,
+                views=20, width=1352, height=1014, frames=300, config_index=3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fgs4d", choices=["fgs4d", "reference"])
+    ap.add_argument("--n", type=int, default=None, help="override the number of Gaussians (smoke runs)")
+    ap.add_argument("--views", type=int, default=None)
+    ap.add_argument("--scale", type=float, default=1.0, help="image scale (smoke runs only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shs-bf16", action="store_true", help="store 4DSH coefficients in BF16")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi during the timed region (median SM clock, reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, val in zip(names, r[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------- reference arm
+def workload_inputs(n=None, views=None, scale=1.0):
+    from paper_2310_10642_gb300 import inputs as I
+    c = I.config(3, n=n, scale=scale)
+    vs = c["views"][: (views or WORKLOAD["views"])]
+    return c["gaussians"], vs, c["options"]
+
+
+def oracle_sample(G, views, budget_s=20.0, crop=32):
+    """FP64 oracle forward+backward on crop x crop windows at the centre of
+    successive views until ~budget_s of CPU work; returns (Mpix/s, sample)."""
+    import numpy as np
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    pix = 0
+    done = 0
+    rng = np.random.default_rng(0)
+    for v in views:
+        x0 = v["width"] // 2 - crop // 2
+        y0 = v["height"] // 2 - crop // 2
+        win = (x0, y0, crop, crop)
+        O.render(G, v, window=win, prefilter=True)
+        O.backward(G, v, rng.normal(size=(3, crop, crop)), window=win, prefilter=True)
+        pix += crop * crop
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return pix / dt / 1e6, f"{done} views x {crop}x{crop} centre crop, forward+backward, {G['logit'].shape[0]} Gaussians"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    G, views, _ = workload_inputs(args.n, args.views, args.scale)
+    vals = []
+    sample = ""
+    for _ in range(args.warmup):
+        oracle_sample(G, views[:1], budget_s=0.0, crop=16)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, sample = oracle_sample(G, views, budget_s=15.0 / max(1, args.steps), crop=32)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    out = dict(metric="Mpix/s fwd+bwd (4DGS render, 1M Gaussians, 1352x1014)", value=value, unit="Mpix/s",
+               n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, ms_per_step=wall * 1e3 / args.steps,
+               higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+               config=dict(WORKLOAD, l2="inputs larger than L2"), impl="reference",
+               cpu_baseline=dict(value=value, unit="Mpix/s", cores=1, kind="oracle", sample=sample),
+               e2e=dict(value=value, unit="Mpix/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0), gpu_launches=0)
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2310_10642_gb300 import native as N
+    from paper_2310_10642_gb300 import render as R
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    N.build()
+    N.lib()
+
+    G, views, opts = workload_inputs(args.n, args.views, args.scale)
+    n = G["logit"].shape[0]
+    shs_dtype = torch.bfloat16 if args.shs_bf16 else torch.float32
+    p = R.params_to_device(G, shs_dtype=shs_dtype)
+    frame = R.Frame(n, views, opts)
+    stream = torch.cuda.current_stream()
+    npix = frame.total_pixels
+    gen = torch.Generator(device="cuda").manual_seed(1234)
+    dL = torch.randn(3 * npix, device="cuda", generator=gen) * (1.0 / npix)
+    grads = {k: torch.empty(p[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
+
+    # size the pair capacity once (outside the timed region), with headroom
+    frame.forward(p, check=True)
+    c = frame.last_counters
+    if c.n_pairs * 1.1 > frame.pair_capacity:
+        frame._alloc(int(c.n_pairs * 1.15) + 4096)
+        frame.forward(p, check=True)
+    counters = frame.last_counters
+
+    stages = ["slice_project", "bin_sort", "render", "render_backward"]
+
+    def step(events=None):
+        if events is not None:
+            events[0].record(stream)
+        frame.slice_project(p)
+        if events is not None:
+            events[1].record(stream)
+        frame.bin_sort()
+        if events is not None:
+            events[2].record(stream)
+        frame.render()
+        if events is not None:
+            events[3].record(stream)
+        frame.backward(p, dL, grads)
+        if events is not None:
+            events[4].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    launches0 = N.fgs4d_launch_count()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    for k in range(args.steps):
+        step(ev[k])
+    torch.cuda.synchronize()
+    launches = N.fgs4d_launch_count() - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = ev[0][0].elapsed_time(ev[-1][4])
+    stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, s in enumerate(stages)}
+    t_tensor = torch.tensor([total_ms], device="cuda")
+    if dist:
+        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
+    total_ms = float(t_tensor.item())
+    ms_step = total_ms / args.steps
+    value = npix * world * args.steps / (total_ms * 1e-3) / 1e6
+    fwd_ms = stage_ms["slice_project"] + stage_ms["bin_sort"] + stage_ms["render"]
+    fwd_mpix = npix / (fwd_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel (algorithmic bytes per launch / time)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    L, K = G["sh_degree"], G["n_freq"]
+    C = 3 * (L + 1) ** 2 * (K + 1)
+    shs_b = 2 if args.shs_bf16 else 4
+    V = len(views)
+    nvis, npairs = counters.n_visible, counters.n_pairs
+    alg = {
+        # parameters read once + records/tile counts/depth keys written
+        "slice_project": n * (17 * 4 + C * shs_b) + nvis * 48 + V * n * 8,
+        # compaction (read tile counts + depth keys, write 8 B per visible splat), depth sort (4 passes x 20 B),
+        # offsets scan (8 B), emission (8 B per pair), pair sort (passes x 20 B per pair), ranges (4 B per pair)
+        "bin_sort": V * n * 8 + nvis * (8 + 4 * 20 + 8) + npairs * (8 + 4)
+        + npairs * 20 * ((_bits(frame.layout().total_tiles) + 7) // 8),
+        # list ids + gathered records (36 B) per pair, 20 B written per pixel
+        "render": npairs * (4 + 36) + npix * 20,
+        # same gathers + dL/dimage, T, n_last per pixel + 48 B gradient record per visible splat (zero+atomics)
+        # + per-Gaussian parameters and gradients
+        "render_backward": npairs * (4 + 36) + npix * 20 + nvis * 48 * 2 + n * 2 * (17 * 4 + C * 4),
+    }
+    dom = max(stage_ms, key=stage_ms.get)
+    achieved = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=hbm, unit="GB/s", frac=round(achieved / hbm, 4),
+                    traffic=None, kernel=dom, peak_source=f"{peak_kind} hbm_gbs")
+
+    # ---- single-view plain FP32 path (one view per call), same GPU
+    single = None
+    if rank == 0:
+        fr1 = R.Frame(n, views[:1], opts)
+        fr1.forward(p, check=True)
+        dL1 = torch.randn(3 * fr1.total_pixels, device="cuda", generator=gen) * (1.0 / fr1.total_pixels)
+        for _ in range(3):
+            fr1.forward(p, check=False)
+            fr1.backward(p, dL1, grads)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            fr1.forward(p, check=False)
+            fr1.backward(p, dL1, grads)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1) / reps
+        single = dict(mpix_s=fr1.total_pixels / (ms1 * 1e-3) / 1e6, ms_per_view=ms1)
+        del fr1
+
+    # ---- e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_p = {k: p[k].cpu().pin_memory() for k in R.PARAM_KEYS}
+        host_dL = dL.cpu().pin_memory()
+        host_img = torch.empty(3 * npix, dtype=torch.float32).pin_memory()
+        host_g = {k: torch.empty(p[k].shape, dtype=torch.float32).pin_memory() for k in R.PARAM_KEYS}
+        dev_p = {k: torch.empty_like(p[k]) for k in R.PARAM_KEYS}
+        dev_p.update({k: p[k] for k in ("sh_degree", "n_freq", "period")})
+        dev_dL = torch.empty_like(dL)
+        h2d = sum(t.numel() * t.element_size() for t in host_p.values()) + host_dL.numel() * 4
+        d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_g.values())
+
+        def e2e_step():
+            for k in R.PARAM_KEYS:
+                dev_p[k].copy_(host_p[k], non_blocking=True)
+            dev_dL.copy_(host_dL, non_blocking=True)
+            frame.slice_project(dev_p)
+            frame.bin_sort()
+            frame.render()
+            frame.backward(dev_p, dev_dL, grads)
+            host_img.copy_(frame.image, non_blocking=True)
+            for k in R.PARAM_KEYS:
+                host_g[k].copy_(grads[k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ks = max(1, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(ks):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = e0.elapsed_time(e1) / ks
+        e2e = dict(value=npix * world / (ms_e2e * 1e-3) / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(d2h), ms_per_step=ms_e2e)
+
+    # ---- CPU baseline (oracle on the host cores, bounded sample)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sample = oracle_sample(G, views, budget_s=15.0)
+        cpu = dict(value=v, unit="Mpix/s", cores=1, kind="oracle", sample=sample)
+
+    if rank == 0:
+        out = dict(metric="Mpix/s fwd+bwd (4DGS render, 1M Gaussians, 1352x1014)", value=round(value, 3),
+                   unit="Mpix/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms_step, 4),
+                   higher_is_better=True, scaling="weak", vs_baseline=None,
+                   dtype="f32" + ("+bf16-shs" if args.shs_bf16 else ""), data="synthetic",
+                   config=dict(WORKLOAD, n=n, views=V, l2="inputs larger than L2 (644 MB parameters)",
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                               pixels_per_step=npix, visible_splats=nvis, pairs=npairs),
+                   fwd_mpix_s=round(fwd_mpix, 3), stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                   single_view=single, roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk,
+                   gpu_launches=int(launches))
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _bits(total_tiles: int) -> int:
+    b = 1
+    while b < 32 and (1 << b) < total_tiles:
+        b += 1
+    return b
+
+
+if __name__ == "__main__":
+    sys.exit(main())

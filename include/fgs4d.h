@@ -1,0 +1,219 @@
+/*
+ * fgs4d.h -- C ABI of libfgs4d: the rendering routine of 4D Gaussian
+ * Splatting (Yang et al., ICLR 2024, arxiv 2310.10642) and its adjoint, as
+ * hand-written CUDA kernels for sm_103a.
+ *
+ * The path, per (camera, time t) view:
+ *   fgs4d_slice_project   4D Gaussian -> conditional 3D Gaussian and marginal
+ *                         p(t) (Sec. 3.2, Eq. 7-10), 4DSH colour (Eq. 11),
+ *                         EWA projection to a 2D splat (Eq. 3-4)
+ *   fgs4d_bin_sort        splat -> screen tiles, ordered by depth (the
+ *                         "sorted according to their depth" of Sec. 3.1 and
+ *                         the tile-based rasteriser adapted in Sec. 3.2)
+ *   fgs4d_render          front-to-back compositing of Eq. 6
+ *   fgs4d_render_backward the adjoint of all three (end-to-end training with
+ *                         the rendering loss only, Sec. 3.3)
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Pointers named "device" must point to memory of the current CUDA device;
+ *   host arrays (views, options) are read during the call only.  The library
+ *   never allocates: the caller owns every buffer, including the per-frame
+ *   state whose size fgs4d_state_size() reports.
+ * - Every call is asynchronous on `stream` (NULL = legacy default stream),
+ *   issues no synchronisation and no allocation, and is safe to capture in a
+ *   CUDA graph.  The one exception is fgs4d_read_counters(), which copies
+ *   device counters to the host and synchronises the stream.
+ * - Argument errors are detected on the host and returned before any work is
+ *   enqueued.  Launch errors return FGS4D_ERR_CUDA.  Data-dependent errors
+ *   (pair-capacity overflow, non-finite or zero-norm parameters) are recorded
+ *   in a device status word inside the state and reported by
+ *   fgs4d_read_counters(); no kernel traps, asserts or spins.
+ * - Parameters are raw (before activation): log scales, opacity logit and
+ *   unnormalised quaternions.  Gradients are returned w.r.t. those raw values.
+ * - Images are planar RGB float32: view v occupies
+ *   image[3*P_v .. 3*(P_v + W_v*H_v)) as [3][H_v][W_v], where
+ *   P_v = sum_{u<v} W_u*H_u ("pixel offset").  final_T and n_last are
+ *   [P_v .. P_v + W_v*H_v) as [H_v][W_v].
+ * - Pixel (i, j) is sampled at image coordinates (x, y) = (i, j); a camera
+ *   maps camera coordinates (X, Y, Z), Z forward, to (fx X/Z + cx, fy Y/Z + cy).
+ */
+#ifndef FGS4D_H
+#define FGS4D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FGS4D_ABI_VERSION 1
+#define FGS4D_MAX_VIEWS 128   /* views per call */
+#define FGS4D_MAX_SH_DEGREE 3 /* L */
+#define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
+#define FGS4D_TILE 16         /* screen tiles are 16 x 16 pixels */
+
+typedef struct CUstream_st *fgs4d_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    FGS4D_OK = 0,
+    FGS4D_ERR_INVALID_ARG = 1, /* bad pointer, size, option or layout */
+    FGS4D_ERR_CAPACITY = 2,    /* the state is too small / pair capacity exceeded */
+    FGS4D_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
+    FGS4D_ERR_TIMEOUT = 4,     /* reserved: no kernel of this library waits */
+    FGS4D_ERR_NONFINITE = 5    /* non-finite input or a zero-norm quaternion */
+} fgs4d_status;
+
+typedef enum { FGS4D_F32 = 0, FGS4D_BF16 = 1 } fgs4d_dtype;
+
+/* Device status bits written into the state (see fgs4d_counters.status). */
+#define FGS4D_STATUS_PAIR_OVERFLOW 1u  /* more (splat, tile) pairs than capacity */
+#define FGS4D_STATUS_NONFINITE 2u      /* a Gaussian had non-finite values or |q| ~ 0 */
+
+/* 4D Gaussians in structure-of-arrays layout (Sec. 3.2 "Representation of
+   4D Gaussian"; Eq. 11 for the coefficients).  All arrays are device memory,
+   row-major with the Gaussian index fastest:
+     mu            [4][n] float  (mu_x, mu_y, mu_z, mu_t)
+     log_scale     [4][n] float  log(s_x, s_y, s_z, s_t); S = diag(exp(.))
+     q_left        [4][n] float  q_l = (a, b, c, d), scalar first, any norm > 0
+     q_right       [4][n] float  q_r = (p, q, r, s), scalar first, any norm > 0
+     opacity_logit [n]    float  alpha = 1 / (1 + exp(-logit))
+     shs           [3*(L+1)^2*(K+1)][n]  float32 or bfloat16 (shs_dtype):
+                   row (f*(L+1)^2 + j)*3 + ch holds k for Fourier order f,
+                   real SH index j = l^2 + l + m and colour channel ch.
+   Every array pointer must be 16-byte aligned. */
+typedef struct {
+    const float *mu;
+    const float *log_scale;
+    const float *q_left;
+    const float *q_right;
+    const float *opacity_logit;
+    const void *shs;
+    int64_t n;       /* 0 <= n < 2^31 / n_views */
+    int sh_degree;   /* L, 0..FGS4D_MAX_SH_DEGREE */
+    int n_freq;      /* K, 0..FGS4D_MAX_FREQ */
+    float period;    /* T of Eq. 11, > 0 */
+    int shs_dtype;   /* fgs4d_dtype */
+} fgs4d_gaussians;
+
+/* One camera at one time t (host memory). */
+typedef struct {
+    float viewmat[12]; /* row-major 3x4 [W | tau]: x_cam = W x_world + tau; W a rotation */
+    float fx, fy, cx, cy;
+    int width, height; /* 1..16384 each */
+    float t;           /* render time */
+    float bg[3];       /* background colour added with the final transmittance */
+} fgs4d_view;
+
+/* Rendering options; fgs4d_default_options() fills the values below. */
+typedef struct {
+    float p_min;      /* 0.05: drop Gaussians with p(t) < p_min (Sec. 4.2) */
+    float near_z;     /* 0.2: drop splats with camera depth below near_z */
+    float alpha_min;  /* 1/255: skip a splat at a pixel when alpha < alpha_min */
+    float alpha_max;  /* 0.99: clamp of alpha */
+    float T_min;      /* 1e-4: stop before a splat that would bring T below T_min */
+    float dilation;   /* 0.3: added to both diagonal entries of the 2D covariance */
+    float clamp_fov;  /* 1.3: clamp x/z to +-clamp_fov*W/(2 fx) inside J; 0 = off */
+    int record_fp16;  /* 0: FP32 splat records; 1: FP16 conic (mixed precision) */
+    float schur_cond; /* 1e-3: FP64 Schur complement when min_i Sigma3_ii/Sigma_ii is below */
+    float conic_cond; /* 1e-4: FP64 2x2 inversion when det/(S00*S11) is below */
+} fgs4d_options;
+
+/* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but
+   always float32.  Overwritten (not accumulated) by fgs4d_render_backward. */
+typedef struct {
+    float *mu;
+    float *log_scale;
+    float *q_left;
+    float *q_right;
+    float *opacity_logit;
+    float *shs;
+    float *mean2d_abs; /* optional [n]: sum over views of |dL/d mu_2d| (densification signal); may be NULL */
+} fgs4d_gaussian_grads;
+
+/* Counters read back by fgs4d_read_counters. */
+typedef struct {
+    uint32_t n_visible;   /* (view, Gaussian) splats that touch at least one tile */
+    uint32_t n_pairs;     /* (splat, tile) pairs needed */
+    uint32_t status;      /* FGS4D_STATUS_* bits */
+    uint32_t pair_capacity;
+} fgs4d_counters;
+
+/* Library version (FGS4D_ABI_VERSION). */
+int fgs4d_abi_version(void);
+
+/* Number of kernel launches this library has issued in the process so far
+   (all threads and devices; for benchmarks that report launch counts). */
+uint64_t fgs4d_launch_count(void);
+
+/* Human-readable text of a status code (static storage). */
+const char *fgs4d_status_string(fgs4d_status status);
+
+/* Fills *opt with the defaults documented in fgs4d_options. */
+void fgs4d_default_options(fgs4d_options *opt);
+
+/* Bytes of per-frame state needed for n Gaussians, these views and room for
+   pair_capacity (splat, tile) pairs.  The same n, views and pair capacity must
+   be used by every call that receives this state.  Returns INVALID_ARG for
+   bad sizes. */
+fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view *views, int n_views, int64_t pair_capacity,
+                              const fgs4d_options *opt, size_t *bytes);
+
+/* Number of pixels over all views (sum W*H): the length of final_T/n_last;
+   the image holds three times as many floats. */
+int64_t fgs4d_total_pixels(const fgs4d_view *views, int n_views);
+
+/* Slice, colour and project every Gaussian for every view (Eq. 3, 4, 7-11;
+   the p(t) filter of Sec. 4.2).  Writes the splat records and per-splat tile
+   counts into the state and clears its counters.  state must be 256-byte
+   aligned and state_bytes the value fgs4d_state_size() returned. */
+fgs4d_status fgs4d_slice_project(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
+                                 const fgs4d_options *opt, void *state, size_t state_bytes, fgs4d_stream stream);
+
+/* Bin the splats to 16x16 tiles and order each tile's list by (depth,
+   Gaussian index) with the library's on-device radix sort (Sec. 3.1/3.2).
+   Pairs beyond the capacity are dropped and FGS4D_STATUS_PAIR_OVERFLOW is set. */
+fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
+                            size_t state_bytes, fgs4d_stream stream);
+
+/* Front-to-back compositing of Eq. 6 for every pixel of every view.
+   image: device float [3 * total_pixels]; final_T: device float
+   [total_pixels]; n_last: device int32 [total_pixels] (list entries walked
+   up to the last contributing splat).  final_T and n_last are needed by the
+   backward pass. */
+fgs4d_status fgs4d_render(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
+                          size_t state_bytes, float *image, float *final_T, int32_t *n_last, fgs4d_stream stream);
+
+/* Adjoint of slice_project + bin_sort + render: given dL/d(image) (same
+   layout as image), writes dL/d(raw parameters) summed over all views into
+   grads (overwritten).  Transmittance is recomputed from final_T, not stored
+   per splat.  g, views, opt and the state must be those of the forward pass. */
+fgs4d_status fgs4d_render_backward(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
+                                   const fgs4d_options *opt, void *state, size_t state_bytes, const float *final_T,
+                                   const int32_t *n_last, const float *dL_dimage, fgs4d_gaussian_grads *grads,
+                                   fgs4d_stream stream);
+
+/* Byte offsets of the state's sections, for inspection and tests.
+   records: one per (view v, Gaussian g) at index v*n + g, record_bytes each
+   (FP32 layout: float u, v, conic a, b, c, alpha_eff, R, G, B, depth,
+   radius, uint32 flags); tiles_touched: uint32 per (v, g), 0 = culled;
+   ranges: uint32 pairs [start, end) per global tile (tiles of view v follow
+   those of views < v, row-major); pair_vals: uint32 splat index v*n + g per
+   list entry, in the buffer that holds the sorted lists. */
+typedef struct {
+    uint64_t counters, records, tiles_touched, ranges, pair_vals;
+    uint64_t record_bytes, n_splats, total_tiles, pair_capacity;
+} fgs4d_state_layout_info;
+
+/* Fills *out for the state of (n, views, opt, state_bytes). Host only. */
+fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt,
+                                size_t state_bytes, fgs4d_state_layout_info *out);
+
+/* Copies the state's counters to *out (synchronises `stream`). */
+fgs4d_status fgs4d_read_counters(const void *state, fgs4d_counters *out, fgs4d_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGS4D_H */

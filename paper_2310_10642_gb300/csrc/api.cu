@@ -1,0 +1,382 @@
+// api.cu -- the C ABI of libfgs4d (declared in include/fgs4d.h).
+//
+// Host-side argument checking, the per-frame state layout, the view set
+// passed by value to every kernel, and the launch sequence of each entry
+// point.  No entry point allocates device memory or synchronises, except
+// fgs4d_read_counters.
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+
+#include "fgs4d_internal.cuh"
+
+using namespace fgs4d;
+
+namespace fgs4d {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(unsigned k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace fgs4d
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+fgs4d_status check_options(const fgs4d_options* o) {
+    if (!o) return FGS4D_ERR_INVALID_ARG;
+    const float vals[] = {o->p_min, o->near_z, o->alpha_min, o->alpha_max, o->T_min, o->dilation, o->clamp_fov,
+                          o->schur_cond, o->conic_cond};
+    for (float v : vals)
+        if (!isfinite(v) || v < 0.0f) return FGS4D_ERR_INVALID_ARG;
+    if (!(o->alpha_min > 0.0f && o->alpha_min <= o->alpha_max && o->alpha_max < 1.0f)) return FGS4D_ERR_INVALID_ARG;
+    if (!(o->near_z > 0.0f) || o->p_min > 1.0f || o->T_min >= 1.0f) return FGS4D_ERR_INVALID_ARG;
+    if (o->record_fp16 != 0) return FGS4D_ERR_INVALID_ARG;  // mixed-precision records: not in this build
+    return FGS4D_OK;
+}
+
+DevOpts dev_options(const fgs4d_options* o) {
+    DevOpts d;
+    d.p_min = o->p_min;
+    d.near_z = o->near_z;
+    d.alpha_min = o->alpha_min;
+    d.alpha_max = o->alpha_max;
+    d.T_min = o->T_min;
+    d.dilation = o->dilation;
+    d.schur_cond = o->schur_cond;
+    d.conic_cond = o->conic_cond;
+    d.ln_alpha_min = logf(o->alpha_min);
+    d.record_fp16 = o->record_fp16;
+    return d;
+}
+
+// Builds the view set; checks sizes.  clamp_fov from the options.
+fgs4d_status make_views(const fgs4d_view* views, int n_views, const fgs4d_options* o, ViewSet* VS) {
+    if (!views || n_views < 1 || n_views > FGS4D_MAX_VIEWS) return FGS4D_ERR_INVALID_ARG;
+    memset(VS, 0, sizeof(*VS));
+    VS->n = n_views;
+    uint64_t tiles = 0, pix = 0;
+    for (int i = 0; i < n_views; i++) {
+        const fgs4d_view& h = views[i];
+        DevView& d = VS->v[i];
+        if (h.width < 1 || h.height < 1 || h.width > 16384 || h.height > 16384) return FGS4D_ERR_INVALID_ARG;
+        for (int k = 0; k < 12; k++)
+            if (!isfinite(h.viewmat[k])) return FGS4D_ERR_INVALID_ARG;
+        if (!(isfinite(h.fx) && isfinite(h.fy) && isfinite(h.cx) && isfinite(h.cy) && isfinite(h.t)) ||
+            !(h.fx > 0.0f && h.fy > 0.0f))
+            return FGS4D_ERR_INVALID_ARG;
+        for (int r = 0; r < 3; r++) {
+            for (int c = 0; c < 3; c++) d.W[r * 3 + c] = h.viewmat[r * 4 + c];
+            d.tau[r] = h.viewmat[r * 4 + 3];
+        }
+        for (int c = 0; c < 3; c++) {
+            double acc = 0.0;
+            for (int r = 0; r < 3; r++) acc -= (double)d.W[r * 3 + c] * (double)d.tau[r];
+            d.campos[c] = (float)acc;
+            d.bg[c] = h.bg[c];
+        }
+        d.fx = h.fx;
+        d.fy = h.fy;
+        d.cx = h.cx;
+        d.cy = h.cy;
+        d.t = h.t;
+        if (o->clamp_fov > 0.0f) {
+            d.limx = o->clamp_fov * 0.5f * (float)h.width / h.fx;
+            d.limy = o->clamp_fov * 0.5f * (float)h.height / h.fy;
+        } else {
+            d.limx = FLT_MAX;
+            d.limy = FLT_MAX;
+        }
+        d.width = h.width;
+        d.height = h.height;
+        d.tiles_x = (h.width + kTile - 1) / kTile;
+        d.tiles_y = (h.height + kTile - 1) / kTile;
+        d.tile_base = (uint32_t)tiles;
+        d.pix_base = (uint32_t)pix;
+        tiles += (uint64_t)d.tiles_x * d.tiles_y;
+        pix += (uint64_t)h.width * h.height;
+    }
+    if (tiles > 0x7fffffffull || pix > 0x7fffffffull) return FGS4D_ERR_INVALID_ARG;
+    VS->total_tiles = (uint32_t)tiles;
+    return FGS4D_OK;
+}
+
+// Lays out the state for n Gaussians and the views; capacity < 0 means
+// "derive it from state_bytes".
+fgs4d_status make_layout(int64_t n, const ViewSet& VS, int64_t capacity, size_t state_bytes, StateLayout* L) {
+    if (n < 0) return FGS4D_ERR_INVALID_ARG;
+    const int64_t S = n * (int64_t)VS.n;
+    if (S >= 0x7fffffffll) return FGS4D_ERR_INVALID_ARG;
+    memset(L, 0, sizeof(*L));
+    L->n_splats = S;
+    L->record_bytes = sizeof(SplatRecord);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        return at;
+    };
+    const size_t s = (size_t)S;
+    L->counters = take(16 * sizeof(uint32_t));
+    L->records = take(s * L->record_bytes);
+    L->tiles_touched = take(s * 4);
+    L->depth_key = take(s * 4);
+    L->sort_keys[0] = take(s * 4);
+    L->sort_keys[1] = take(s * 4);
+    L->sort_vals[0] = take(s * 4);
+    L->sort_vals[1] = take(s * 4);
+    L->offsets = take(s * 4);
+    L->scan_tmp = take((kScanBlocksMax + 32) * 4);
+    L->hist = take((256 * kSortBlocksMax + 256) * 4);
+    L->ranges = take((size_t)VS.total_tiles * 8);
+    L->grad2d = take(s * 48);
+    L->fixed_bytes = off;
+    if (capacity < 0) {
+        if (state_bytes < L->fixed_bytes) return FGS4D_ERR_CAPACITY;
+        // four uint32 arrays of `capacity`, each padded to the alignment
+        int64_t cap = (int64_t)((state_bytes - L->fixed_bytes) / 16);
+        while (cap > 0 && L->fixed_bytes + 4 * align_up((size_t)cap * 4) > state_bytes) cap--;
+        capacity = cap;
+    }
+    if (capacity > 0xffffffffll) capacity = 0xffffffffll;
+    L->capacity = capacity;
+    const size_t pb = align_up((size_t)capacity * 4);
+    L->pair_keys[0] = off;
+    L->pair_keys[1] = off + pb;
+    L->pair_vals[0] = off + 2 * pb;
+    L->pair_vals[1] = off + 3 * pb;
+    L->total = off + 4 * pb;
+    return FGS4D_OK;
+}
+
+fgs4d_status check_gaussians(const fgs4d_gaussians* g, DevGauss* d) {
+    if (!g) return FGS4D_ERR_INVALID_ARG;
+    if (g->n < 0 || g->n >= 0x7fffffffll) return FGS4D_ERR_INVALID_ARG;
+    if (g->sh_degree < 0 || g->sh_degree > FGS4D_MAX_SH_DEGREE || g->n_freq < 0 || g->n_freq > FGS4D_MAX_FREQ)
+        return FGS4D_ERR_INVALID_ARG;
+    if (!(g->period > 0.0f) || !isfinite(g->period)) return FGS4D_ERR_INVALID_ARG;
+    if (g->shs_dtype != FGS4D_F32 && g->shs_dtype != FGS4D_BF16) return FGS4D_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        const void* ptrs[] = {g->mu, g->log_scale, g->q_left, g->q_right, g->opacity_logit, g->shs};
+        for (const void* p : ptrs)
+            if (!p || !aligned(p, 16)) return FGS4D_ERR_INVALID_ARG;
+    }
+    d->mu = g->mu;
+    d->log_s = g->log_scale;
+    d->ql = g->q_left;
+    d->qr = g->q_right;
+    d->logit = g->opacity_logit;
+    d->shs = g->shs;
+    d->n = (int)g->n;
+    d->L = g->sh_degree;
+    d->K = g->n_freq;
+    d->inv_period = 1.0f / g->period;
+    d->shs_bf16 = g->shs_dtype == FGS4D_BF16;
+    return FGS4D_OK;
+}
+
+struct Prepared {
+    ViewSet VS;
+    DevOpts O;
+    StateLayout L;
+};
+
+fgs4d_status prepare(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
+                     size_t state_bytes, Prepared* P) {
+    fgs4d_status s = check_options(opt);
+    if (s != FGS4D_OK) return s;
+    if (!state || !aligned(state, kAlign)) return FGS4D_ERR_INVALID_ARG;
+    if ((s = make_views(views, n_views, opt, &P->VS)) != FGS4D_OK) return s;
+    if ((s = make_layout(n, P->VS, -1, state_bytes, &P->L)) != FGS4D_OK) return s;
+    P->O = dev_options(opt);
+    return FGS4D_OK;
+}
+
+int sm_count_cached() {
+    static int count = 0;
+    if (count == 0) {
+        int dev = 0, c = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+            count = c;
+        else
+            return 152;
+    }
+    return count;
+}
+
+fgs4d_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FGS4D_OK : FGS4D_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int fgs4d_abi_version(void) { return FGS4D_ABI_VERSION; }
+
+uint64_t fgs4d_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* fgs4d_status_string(fgs4d_status s) {
+    switch (s) {
+        case FGS4D_OK: return "ok";
+        case FGS4D_ERR_INVALID_ARG: return "invalid argument";
+        case FGS4D_ERR_CAPACITY: return "state too small or pair capacity exceeded";
+        case FGS4D_ERR_CUDA: return "CUDA error";
+        case FGS4D_ERR_TIMEOUT: return "timeout";
+        case FGS4D_ERR_NONFINITE: return "non-finite input or zero-norm quaternion";
+    }
+    return "unknown status";
+}
+
+void fgs4d_default_options(fgs4d_options* o) {
+    if (!o) return;
+    o->p_min = 0.05f;
+    o->near_z = 0.2f;
+    o->alpha_min = 1.0f / 255.0f;
+    o->alpha_max = 0.99f;
+    o->T_min = 1e-4f;
+    o->dilation = 0.3f;
+    o->clamp_fov = 1.3f;
+    o->record_fp16 = 0;
+    o->schur_cond = 1e-3f;
+    o->conic_cond = 1e-4f;
+}
+
+int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {
+    if (!views || n_views < 0) return -1;
+    int64_t p = 0;
+    for (int i = 0; i < n_views; i++) p += (int64_t)views[i].width * views[i].height;
+    return p;
+}
+
+fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view* views, int n_views, int64_t pair_capacity,
+                              const fgs4d_options* opt, size_t* bytes) {
+    if (!bytes || pair_capacity < 0 || pair_capacity > 0xffffffffll) return FGS4D_ERR_INVALID_ARG;
+    fgs4d_status s = check_options(opt);
+    if (s != FGS4D_OK) return s;
+    ViewSet* VS = new ViewSet;
+    s = make_views(views, n_views, opt, VS);
+    StateLayout L;
+    if (s == FGS4D_OK) s = make_layout(n, *VS, pair_capacity, 0, &L);
+    delete VS;
+    if (s != FGS4D_OK) return s;
+    *bytes = L.total;
+    return FGS4D_OK;
+}
+
+fgs4d_status fgs4d_slice_project(const fgs4d_gaussians* g, const fgs4d_view* views, int n_views,
+                                 const fgs4d_options* opt, void* state, size_t state_bytes, fgs4d_stream stream) {
+    DevGauss G;
+    fgs4d_status s = check_gaussians(g, &G);
+    if (s != FGS4D_OK) return s;
+    Prepared* P = new Prepared;
+    s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK) {
+        char* st = static_cast<char*>(state);
+        cudaError_t e = launch_slice_project(G, P->VS, P->O, P->L, st, (uint32_t)P->L.capacity,
+                                             (cudaStream_t)stream);
+        s = cuda_status(e);
+    }
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
+                            size_t state_bytes, fgs4d_stream stream) {
+    Prepared* P = new Prepared;
+    fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK) {
+        int buf = 0;
+        s = cuda_status(launch_bin_sort(P->VS, P->O, P->L, static_cast<char*>(state), sm_count_cached(),
+                                        (cudaStream_t)stream, &buf));
+    }
+    delete P;
+    return s;
+}
+
+static int pair_buffer(const Prepared& P) {
+    if (P.L.capacity == 0) return 0;
+    const int bits = pair_sort_bits(P.VS.total_tiles + 1);
+    return ((bits + 7) / 8) & 1;
+}
+
+fgs4d_status fgs4d_render(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
+                          size_t state_bytes, float* image, float* final_T, int32_t* n_last, fgs4d_stream stream) {
+    if (!image || !final_T || !n_last) return FGS4D_ERR_INVALID_ARG;
+    if (!aligned(image, 4) || !aligned(final_T, 4) || !aligned(n_last, 4)) return FGS4D_ERR_INVALID_ARG;
+    Prepared* P = new Prepared;
+    fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK)
+        s = cuda_status(launch_render(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), image, final_T,
+                                      n_last, (cudaStream_t)stream));
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* views, int n_views,
+                                   const fgs4d_options* opt, void* state, size_t state_bytes, const float* final_T,
+                                   const int32_t* n_last, const float* dL_dimage, fgs4d_gaussian_grads* grads,
+                                   fgs4d_stream stream) {
+    DevGauss G;
+    fgs4d_status s = check_gaussians(g, &G);
+    if (s != FGS4D_OK) return s;
+    if (!final_T || !n_last || !dL_dimage || !grads) return FGS4D_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        const void* ptrs[] = {grads->mu, grads->log_scale, grads->q_left, grads->q_right, grads->opacity_logit,
+                              grads->shs};
+        for (const void* p : ptrs)
+            if (!p || !aligned(p, 4)) return FGS4D_ERR_INVALID_ARG;
+    }
+    Prepared* P = new Prepared;
+    s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK) {
+        char* st = static_cast<char*>(state);
+        cudaError_t e = launch_render_backward(P->VS, P->O, P->L, st, pair_buffer(*P), final_T, n_last, dL_dimage,
+                                               (cudaStream_t)stream);
+        if (e == cudaSuccess) e = launch_project_backward(G, P->VS, P->O, P->L, st, *grads, (cudaStream_t)stream);
+        s = cuda_status(e);
+    }
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt,
+                                size_t state_bytes, fgs4d_state_layout_info* out) {
+    if (!out) return FGS4D_ERR_INVALID_ARG;
+    fgs4d_status s = check_options(opt);
+    if (s != FGS4D_OK) return s;
+    Prepared* P = new Prepared;
+    s = make_views(views, n_views, opt, &P->VS);
+    if (s == FGS4D_OK) s = make_layout(n, P->VS, -1, state_bytes, &P->L);
+    if (s == FGS4D_OK) {
+        out->counters = P->L.counters;
+        out->records = P->L.records;
+        out->tiles_touched = P->L.tiles_touched;
+        out->ranges = P->L.ranges;
+        out->pair_vals = P->L.pair_vals[pair_buffer(*P)];
+        out->record_bytes = P->L.record_bytes;
+        out->n_splats = (uint64_t)P->L.n_splats;
+        out->total_tiles = P->VS.total_tiles;
+        out->pair_capacity = (uint64_t)P->L.capacity;
+    }
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_read_counters(const void* state, fgs4d_counters* out, fgs4d_stream stream) {
+    if (!state || !out || !aligned(state, kAlign)) return FGS4D_ERR_INVALID_ARG;
+    uint32_t h[4];
+    cudaError_t e = cudaMemcpyAsync(h, state, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return FGS4D_ERR_CUDA;
+    out->n_visible = h[0];
+    out->n_pairs = h[1];
+    out->status = h[2];
+    out->pair_capacity = h[3];
+    return FGS4D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,438 @@
+// bin_sort.cu -- tile binning with a depth order, on the device.
+//
+// Each tile's list must be ordered by (depth, Gaussian index) (Sec. 3.1:
+// splats are blended in depth order; ties broken by index).  Instead of one
+// radix sort of 64-bit (tile | depth) keys over all (splat, tile) pairs, the
+// pipeline sorts the visible splats once by depth and then stable-sorts the
+// pairs by tile id alone:
+//   1. compact the visible (view, Gaussian) splats in index order
+//   2. stable LSD radix sort of the compacted splats by depth (32-bit keys)
+//   3. exclusive scan of their tile counts in depth order -> pair offsets
+//   4. emit one (global tile id, splat id) pair per touched tile
+//   5. stable LSD radix sort of the pairs by tile id (only the bits in use)
+//   6. per-tile [start, end) ranges
+// Stability of both sorts makes each tile's list come out in (depth, index)
+// order.  The pair sort moves 8 bytes per pair per pass over ceil(bits/8)
+// passes instead of 12 bytes over ~6 passes of a (tile|depth) sort.
+//
+// All counts that depend on the data (visible splats, pairs) stay on the
+// device; grids are sized from capacities and every block derives its share
+// from the device count, so the whole pipeline is graph-capturable.
+#include "fgs4d_internal.cuh"
+
+namespace fgs4d {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 8;
+constexpr int kTileItems = kThreads * kItems;  // 2048
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t device_count(const uint32_t* d_n, uint32_t n_max) {
+    return d_n ? min(*d_n, n_max) : n_max;
+}
+
+// Contiguous chunk [begin, end) of a block, in whole tiles of kTileItems.
+__device__ __forceinline__ void block_chunk(uint32_t n, int G, uint32_t& begin, uint32_t& end) {
+    uint64_t per = ((uint64_t)n + G - 1) / G;
+    per = (per + kTileItems - 1) / kTileItems * kTileItems;
+    const uint64_t b = (uint64_t)blockIdx.x * per;
+    begin = (uint32_t)(b < (uint64_t)n ? b : (uint64_t)n);
+    end = (uint32_t)(b + per < (uint64_t)n ? b + per : (uint64_t)n);
+}
+
+// Exclusive scan of one value per thread over the block (blockDim % 32 == 0).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* s_warp, uint32_t& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t prefix = (wid > 0 ? s_warp[wid - 1] : 0u) + v - x;
+    total = s_warp[nw - 1];
+    __syncthreads();
+    return prefix;
+}
+
+// ---------------------------------------------------------------------------
+// Device-wide exclusive scan: reduce -> scan of block sums -> apply.
+// ---------------------------------------------------------------------------
+struct LoadVisible {  // 1 for a splat that touches a tile
+    const uint32_t* tiles;
+    __device__ uint32_t operator()(uint32_t i) const { return tiles[i] > 0u ? 1u : 0u; }
+};
+struct StoreCompact {  // visible splat -> (depth key, splat id) at its rank
+    const uint32_t* tiles;
+    const uint32_t* depth_key;
+    uint32_t* keys;
+    uint32_t* vals;
+    __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t x) const {
+        if (x) {
+            keys[prefix] = depth_key[i];
+            vals[prefix] = i;
+        }
+    }
+};
+struct LoadTilesSorted {  // tile count of the i-th splat in depth order
+    const uint32_t* tiles;
+    const uint32_t* sorted;
+    __device__ uint32_t operator()(uint32_t i) const { return tiles[sorted[i]]; }
+};
+struct StoreOffset {
+    uint32_t* offsets;
+    __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { offsets[i] = prefix; }
+};
+
+template <class Load>
+__global__ void __launch_bounds__(kThreads) scan_reduce_kernel(Load ld, const uint32_t* d_n, uint32_t n_max,
+                                                               uint32_t* block_sums) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t n = device_count(d_n, n_max);
+    uint32_t begin, end;
+    block_chunk(n, gridDim.x, begin, end);
+    uint32_t sum = 0;
+    for (uint32_t i = begin + threadIdx.x; i < end; i += kThreads) sum += ld(i);
+    uint32_t total;
+    block_exclusive_scan(sum, s_warp, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* block_sums, int G, uint32_t* total_out) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t x = threadIdx.x < G ? block_sums[threadIdx.x] : 0u;
+    uint32_t total;
+    const uint32_t p = block_exclusive_scan(x, s_warp, total);
+    if (threadIdx.x < G) block_sums[threadIdx.x] = p;
+    if (threadIdx.x == 0 && total_out) *total_out = total;
+}
+
+template <class Load, class Store>
+__global__ void __launch_bounds__(kThreads) scan_apply_kernel(Load ld, Store stv, const uint32_t* d_n, uint32_t n_max,
+                                                              const uint32_t* block_sums) {
+    __shared__ uint32_t s_warp[32];
+    const uint32_t n = device_count(d_n, n_max);
+    uint32_t begin, end;
+    block_chunk(n, gridDim.x, begin, end);
+    uint32_t running = block_sums[blockIdx.x];
+    for (uint32_t tile = begin; tile < end; tile += kTileItems) {
+        const uint32_t my = tile + threadIdx.x * kItems;
+        uint32_t x[kItems];
+        uint32_t local = 0;
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            x[k] = (my + k < end) ? ld(my + k) : 0u;
+            local += x[k];
+        }
+        uint32_t total;
+        uint32_t p = running + block_exclusive_scan(local, s_warp, total);
+#pragma unroll
+        for (int k = 0; k < kItems; k++) {
+            if (my + k < end) stv(my + k, p, x[k]);
+            p += x[k];
+        }
+        running += total;
+    }
+}
+
+template <class Load, class Store>
+static cudaError_t device_scan(Load ld, Store stv, const uint32_t* d_n, uint32_t n_max, uint32_t* block_sums,
+                               uint32_t* total_out, int G, cudaStream_t st) {
+    scan_reduce_kernel<Load><<<G, kThreads, 0, st>>>(ld, d_n, n_max, block_sums);
+    scan_blocks_kernel<<<1, 1024, 0, st>>>(block_sums, G, total_out);
+    scan_apply_kernel<Load, Store><<<G, kThreads, 0, st>>>(ld, stv, d_n, n_max, block_sums);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort of (uint32 key, uint32 value), 8-bit digits.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
+                                                                 uint32_t n_max, int shift, uint32_t* hist) {
+    __shared__ uint32_t s_h[kThreads / 32][256];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int w = 0; w < kThreads / 32; w++) s_h[w][tid] = 0u;
+    __syncthreads();
+    const uint32_t n = device_count(d_n, n_max);
+    uint32_t begin, end;
+    block_chunk(n, gridDim.x, begin, end);
+    // warp-strided so that every iteration is warp-uniform (needed by match_any)
+    for (uint32_t base = begin + wid * 32; base < end; base += kThreads) {
+        const uint32_t i = base + lane;
+        const uint32_t d = i < end ? (keys[i] >> shift) & 255u : 256u;
+        const uint32_t peers = __match_any_sync(kFull, d);
+        if (d < 256u && lane == __ffs(peers) - 1) s_h[wid][d] += __popc(peers);
+    }
+    __syncthreads();
+    uint32_t sum = 0;
+    for (int w = 0; w < kThreads / 32; w++) sum += s_h[w][tid];
+    hist[tid * gridDim.x + blockIdx.x] = sum;
+}
+
+// One block per digit: exclusive scan over the blocks, digit totals.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int G, uint32_t* digit_total) {
+    __shared__ uint32_t s_warp[32];
+    const int d = blockIdx.x;
+    uint32_t running = 0;
+    for (int b0 = 0; b0 < G; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        const uint32_t x = b < G ? hist[d * G + b] : 0u;
+        uint32_t total;
+        const uint32_t p = block_exclusive_scan(x, s_warp, total);
+        if (b < G) hist[d * G + b] = running + p;
+        running += total;
+    }
+    if (threadIdx.x == 0) digit_total[d] = running;
+}
+
+__global__ void __launch_bounds__(kThreads) radix_downsweep_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const uint32_t* d_n, uint32_t n_max, int shift, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ digit_total) {
+    __shared__ uint32_t s_global[256];
+    __shared__ uint32_t s_tile_start[256];
+    __shared__ uint32_t s_wcnt[kThreads / 32][256];
+    __shared__ uint32_t s_keys[kTileItems];
+    __shared__ uint32_t s_vals[kTileItems];
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t n = device_count(d_n, n_max);
+    uint32_t begin, end;
+    block_chunk(n, gridDim.x, begin, end);
+    if (begin >= end) return;  // uniform across the block
+    uint32_t tot;
+    const uint32_t dstart = block_exclusive_scan(digit_total[tid], s_warp, tot);
+    s_global[tid] = dstart + hist[tid * gridDim.x + blockIdx.x];
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t tile = begin; tile < end; tile += kTileItems) {
+        for (int w = 0; w < kThreads / 32; w++) s_wcnt[w][tid] = 0u;
+        __syncthreads();
+        uint32_t k[kItems], val[kItems], dig[kItems], rank[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const uint32_t idx = tile + wid * (32 * kItems) + i * 32 + lane;
+            const bool valid = idx < end;
+            k[i] = valid ? keys_in[idx] : 0u;
+            val[i] = valid ? vals_in[idx] : 0u;
+            dig[i] = valid ? (k[i] >> shift) & 255u : 256u;
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            const uint32_t peers = __match_any_sync(kFull, dig[i]);
+            const uint32_t base = dig[i] < 256u ? s_wcnt[wid][dig[i]] : 0u;
+            __syncwarp();
+            if (dig[i] < 256u && lane == __ffs(peers) - 1) s_wcnt[wid][dig[i]] = base + __popc(peers);
+            __syncwarp();
+            rank[i] = base + __popc(peers & lt);
+        }
+        __syncthreads();
+        uint32_t run = 0;
+        for (int w = 0; w < kThreads / 32; w++) {
+            const uint32_t c = s_wcnt[w][tid];
+            s_wcnt[w][tid] = run;
+            run += c;
+        }
+        const uint32_t tile_cnt = run;
+        uint32_t tile_total;
+        const uint32_t ts = block_exclusive_scan(tile_cnt, s_warp, tile_total);
+        s_tile_start[tid] = ts;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            if (dig[i] < 256u) {
+                const uint32_t pos = s_tile_start[dig[i]] + s_wcnt[wid][dig[i]] + rank[i];
+                s_keys[pos] = k[i];
+                s_vals[pos] = val[i];
+            }
+        }
+        __syncthreads();
+        const uint32_t tile_n = min((uint32_t)kTileItems, end - tile);
+        for (uint32_t j = tid; j < tile_n; j += kThreads) {
+            const uint32_t kk = s_keys[j];
+            const uint32_t d = (kk >> shift) & 255u;
+            const uint32_t out = s_global[d] + (j - s_tile_start[d]);
+            keys_out[out] = kk;
+            vals_out[out] = s_vals[j];
+        }
+        __syncthreads();
+        s_global[tid] += tile_cnt;
+        __syncthreads();
+    }
+}
+
+// Sorts keys[0]/vals[0] over `bits` low key bits; result in buffer (passes % 2).
+static cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], const uint32_t* d_n, uint32_t n_max, int bits,
+                              uint32_t* hist, uint32_t* digit_total, int G, cudaStream_t st, int* out_buf) {
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        radix_upsweep_kernel<<<G, kThreads, 0, st>>>(keys[cur], d_n, n_max, shift, hist);
+        radix_scan_kernel<<<256, 1024, 0, st>>>(hist, G, digit_total);
+        radix_downsweep_kernel<<<G, kThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, n_max,
+                                                        shift, hist, digit_total);
+        cur ^= 1;
+        count_launches(3);
+    }
+    *out_buf = cur;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pair emission and tile ranges
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void emit_one(const ViewSet& VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted_splats,
+                                         const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tiles,
+                                         const SplatRecord* __restrict__ rec,
+                                         uint32_t* counters, uint32_t capacity, uint32_t* __restrict__ pair_keys,
+                                         uint32_t* __restrict__ pair_vals, uint32_t p) {
+    const uint32_t sid = sorted_splats[p];
+    const uint32_t v = sid / n_gauss;
+    const DevView& V = VS.v[v];
+    const float4 r0 = rec[sid].r0;
+    const float radius = rec[sid].r2.z;
+    const float fx0 = fmaxf(ceilf(r0.x - radius), 0.0f);
+    const float fx1 = fminf(floorf(r0.x + radius), (float)(V.width - 1));
+    const float fy0 = fmaxf(ceilf(r0.y - radius), 0.0f);
+    const float fy1 = fminf(floorf(r0.y + radius), (float)(V.height - 1));
+    const int x0 = (int)fx0 / kTile, x1 = (int)fx1 / kTile, y0 = (int)fy0 / kTile, y1 = (int)fy1 / kTile;
+    // Exactly tiles[sid] pairs are written (the count the offsets were built
+    // from); should the rect ever disagree, surplus slots go to the dump tile
+    // id VS.total_tiles, which no CTA renders.
+    const uint32_t cnt = tiles[sid];
+    const int wx = x1 - x0 + 1;
+    const uint32_t cnt_rect = (uint32_t)(wx * (y1 - y0 + 1));
+    uint32_t o = offsets[p];
+    bool overflow = false;
+    for (uint32_t k = 0; k < cnt; k++, o++) {
+        if (o >= capacity) {
+            overflow = true;
+            break;
+        }
+        uint32_t key = VS.total_tiles;
+        if (k < cnt_rect) {
+            const int ty = y0 + (int)k / wx, tx = x0 + (int)k % wx;
+            key = V.tile_base + (uint32_t)(ty * V.tiles_x + tx);
+        }
+        pair_keys[o] = key;
+        pair_vals[o] = sid;
+    }
+    if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
+}
+
+__global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__ ViewSet VS, uint32_t n_gauss,
+                                                         const uint32_t* __restrict__ sorted_splats,
+                                                         const uint32_t* __restrict__ offsets,
+                                                         const uint32_t* __restrict__ tiles,
+                                                         const SplatRecord* __restrict__ rec, uint32_t n_max,
+                                                         uint32_t* counters, uint32_t capacity,
+                                                         uint32_t* __restrict__ pair_keys,
+                                                         uint32_t* __restrict__ pair_vals) {
+    const uint32_t n_vis = min(counters[0], n_max);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_vis; p += gridDim.x * blockDim.x)
+        emit_one(VS, n_gauss, sorted_splats, offsets, tiles, rec, counters, capacity, pair_keys, pair_vals, p);
+}
+
+
+__global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* counters,
+                                                          uint32_t capacity, uint32_t total_tiles,
+                                                          uint2* __restrict__ ranges) {
+    const uint32_t n = min(counters[1], capacity);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        if (k >= total_tiles) continue;  // dump tile (sorts last)
+        if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
+        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    }
+}
+
+static int grid_cap(uint32_t want, int cap) { return (int)(want < (uint32_t)cap ? (want > 0 ? want : 1) : (uint32_t)cap); }
+
+int pair_sort_bits(uint32_t total_tiles) {
+    int bits = 1;
+    while (bits < 32 && (1ull << bits) < (unsigned long long)total_tiles) bits++;
+    return bits;
+}
+
+cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int sm_count,
+                            cudaStream_t st, int* out_buf) {
+    (void)O;
+    const uint32_t S = (uint32_t)lay.n_splats;
+    uint32_t* counters = reinterpret_cast<uint32_t*>(state + lay.counters);
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
+    uint32_t* dkey = reinterpret_cast<uint32_t*>(state + lay.depth_key);
+    uint32_t* sk[2] = {reinterpret_cast<uint32_t*>(state + lay.sort_keys[0]),
+                       reinterpret_cast<uint32_t*>(state + lay.sort_keys[1])};
+    uint32_t* sv[2] = {reinterpret_cast<uint32_t*>(state + lay.sort_vals[0]),
+                       reinterpret_cast<uint32_t*>(state + lay.sort_vals[1])};
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(state + lay.offsets);
+    uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(state + lay.scan_tmp);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(state + lay.hist);
+    uint32_t* digit_total = hist + 256 * kSortBlocksMax;
+    uint2* ranges = reinterpret_cast<uint2*>(state + lay.ranges);
+    uint32_t* pk[2] = {reinterpret_cast<uint32_t*>(state + lay.pair_keys[0]),
+                       reinterpret_cast<uint32_t*>(state + lay.pair_keys[1])};
+    uint32_t* pv[2] = {reinterpret_cast<uint32_t*>(state + lay.pair_vals[0]),
+                       reinterpret_cast<uint32_t*>(state + lay.pair_vals[1])};
+    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    const uint32_t cap = (uint32_t)lay.capacity;
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)VS.total_tiles, st);
+    if (e != cudaSuccess) return e;
+    *out_buf = 0;
+    if (S == 0) return cudaSuccess;
+    auto grid_for = [&](uint32_t n) {
+        const uint32_t want = (n + kTileItems - 1) / kTileItems;
+        return (int)max(1u, min(want, (uint32_t)min(kSortBlocksMax, 4 * sm_count)));
+    };
+    // 1. compaction of visible splats -> counters[0]
+    const int Gs = grid_for(S);
+    e = device_scan(LoadVisible{tiles}, StoreCompact{tiles, dkey, sk[0], sv[0]}, nullptr, S, scan_tmp, &counters[0],
+                    Gs, st);
+    if (e != cudaSuccess) return e;
+    // 2. depth sort (positive float bits sort as unsigned integers)
+    int buf = 0;
+    e = radix_sort(sk, sv, &counters[0], S, 32, hist, digit_total, Gs, st, &buf);
+    if (e != cudaSuccess) return e;
+    const uint32_t* sorted = sv[buf];
+    // 3. pair offsets in depth order -> counters[1]
+    e = device_scan(LoadTilesSorted{tiles, sorted}, StoreOffset{offsets}, &counters[0], S, scan_tmp, &counters[1], Gs,
+                    st);
+    if (e != cudaSuccess) return e;
+    // 4. emission
+    const int stride_grid = 16 * sm_count;
+    emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, S,
+                                                       counters, cap, pk[0], pv[0]);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (cap == 0) return cudaSuccess;
+    // 5. stable sort of pairs by tile id
+    const int bits = pair_sort_bits(VS.total_tiles + 1);  // + the dump tile id
+    const int Gp = grid_for(cap);
+    e = radix_sort(pk, pv, &counters[1], cap, bits, hist, digit_total, Gp, st, out_buf);
+    if (e != cudaSuccess) return e;
+    // 6. ranges
+    tile_ranges_kernel<<<grid_cap((cap + 255) / 256, stride_grid), 256, 0, st>>>(pk[*out_buf], counters, cap,
+                                                                                         VS.total_tiles,
+                                                                                         ranges);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace fgs4d

@@ -1,0 +1,506 @@
+// fgs4d_internal.cuh -- device-side data structures and math shared by the
+// kernels of libfgs4d (slice/project, binning, compositing and their adjoint).
+//
+// Nothing here is visible through the C ABI.  The view set and the options
+// travel to every kernel by value as a __grid_constant__ parameter, so a
+// launch captured in a CUDA graph carries its own copy.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fgs4d.h"
+
+namespace fgs4d {
+
+constexpr int kTile = FGS4D_TILE;              // 16x16 pixel tiles
+constexpr int kTilePix = kTile * kTile;        // 256 pixels, one per thread
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e)
+constexpr float kLn2 = 0.6931471805599453f;
+
+// One view, pre-digested on the host.
+struct DevView {
+    float W[9];       // world -> camera rotation, row-major
+    float tau[3];     // translation
+    float campos[3];  // camera centre C = -W^T tau
+    float fx, fy, cx, cy;
+    float limx, limy;  // clamp of x/z, y/z inside the Jacobian (huge when off)
+    float t;
+    float bg[3];
+    int width, height, tiles_x, tiles_y;
+    uint32_t tile_base;  // first global tile id of this view
+    uint32_t pix_base;   // first pixel (offset into final_T / n_last)
+};
+
+struct ViewSet {
+    int n;
+    uint32_t total_tiles;
+    DevView v[FGS4D_MAX_VIEWS];
+};
+
+struct DevOpts {
+    float p_min, near_z, alpha_min, alpha_max, T_min, dilation;
+    float schur_cond, conic_cond;
+    float ln_alpha_min;
+    int record_fp16;
+};
+
+// Gaussian parameters (SoA) as the kernels see them.
+struct DevGauss {
+    const float* mu;
+    const float* log_s;
+    const float* ql;
+    const float* qr;
+    const float* logit;
+    const void* shs;
+    int n;
+    int L;
+    int K;
+    float inv_period;
+    int shs_bf16;
+};
+
+// ---------------------------------------------------------------------------
+// Per-frame state layout (byte offsets into the caller's state buffer).
+// ---------------------------------------------------------------------------
+struct StateLayout {
+    size_t counters;       // uint32[16]: n_visible, n_pairs, status, capacity
+    size_t records;        // SplatRecord[V*n]
+    size_t tiles_touched;  // uint32[V*n]
+    size_t depth_key;      // uint32[V*n]
+    size_t sort_keys[2];   // uint32[V*n] double buffer (depth sort)
+    size_t sort_vals[2];   // uint32[V*n]
+    size_t offsets;        // uint32[V*n] pair offsets per depth-sorted splat
+    size_t scan_tmp;       // uint32[kScanBlocksMax + 32]
+    size_t hist;           // uint32[256 * kSortBlocksMax + 256]
+    size_t ranges;         // uint2[total_tiles]
+    size_t grad2d;         // float4[3 * V*n] per-splat 2D gradient
+    size_t pair_keys[2];   // uint32[capacity] double buffer
+    size_t pair_vals[2];   // uint32[capacity]
+    size_t fixed_bytes;    // everything above except the pair buffers
+    size_t total;
+    int64_t capacity;
+    int64_t n_splats;      // V * n
+    uint32_t record_bytes;
+};
+
+constexpr int kScanBlocksMax = 1024;
+constexpr int kSortBlocksMax = 1024;
+
+// Splat record (FP32): 48 bytes, three 16-byte vectors.
+//   r0 = (u, v, conic_a, conic_b)   r1 = (conic_c, alpha_eff, R, G)
+//   r2 = (B, depth, radius, flags)  flags bit ch: colour channel ch clamped
+struct __align__(16) SplatRecord {
+    float4 r0, r1, r2;
+};
+
+// Splat record (mixed precision): 32 bytes.
+//   h0 = (u, v) fp32, h1 = (A', B') fp16x2, h2 = (C', alpha_eff) fp16x2 with
+//   the conic pre-scaled by -1/2 log2(e) (resp. -log2(e)) and by 2^e where
+//   e = exponent (stored in h3.w), h3 = (R, G, B) fp32 + packed (e, flags)
+struct __align__(16) SplatRecordH {
+    float2 uv;
+    __half2 ab;
+    __half2 c_alpha;
+    float rgb[3];
+    uint32_t meta;  // bits 0..2 colour clamp flags, bits 8..15 biased exponent
+};
+
+// ---------------------------------------------------------------------------
+// Small math helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Real spherical harmonics, degree <= 3, Cartesian form on the unit sphere
+// (Condon-Shortley phase; index j = l^2 + l + m).  Constants are
+// sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times the factors of the Cartesian
+// polynomials.
+__device__ __forceinline__ void sh_eval(int L, float x, float y, float z, float* Y) {
+    Y[0] = 0.28209479177387814f;
+    if (L < 1) return;
+    Y[1] = -0.4886025119029199f * y;
+    Y[2] = 0.4886025119029199f * z;
+    Y[3] = -0.4886025119029199f * x;
+    if (L < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, yz = y * z, xz = x * z;
+    Y[4] = 1.0925484305920792f * xy;
+    Y[5] = -1.0925484305920792f * yz;
+    Y[6] = 0.31539156525252005f * (2.0f * zz - xx - yy);
+    Y[7] = -1.0925484305920792f * xz;
+    Y[8] = 0.5462742152960396f * (xx - yy);
+    if (L < 3) return;
+    Y[9] = -0.5900435899266435f * y * (3.0f * xx - yy);
+    Y[10] = 2.890611442640554f * xy * z;
+    Y[11] = -0.4570457994644658f * y * (4.0f * zz - xx - yy);
+    Y[12] = 0.3731763325901154f * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
+    Y[13] = -0.4570457994644658f * x * (4.0f * zz - xx - yy);
+    Y[14] = 1.445305721320277f * z * (xx - yy);
+    Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
+}
+
+// Gradient of sum_j w_j Y_j (as polynomials in x, y, z) -> (gx, gy, gz).
+__device__ __forceinline__ void sh_grad(int L, float x, float y, float z, const float* w, float& gx, float& gy,
+                                        float& gz) {
+    gx = gy = gz = 0.0f;
+    if (L < 1) return;
+    gy += -0.4886025119029199f * w[1];
+    gz += 0.4886025119029199f * w[2];
+    gx += -0.4886025119029199f * w[3];
+    if (L < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    {
+        const float c0 = 1.0925484305920792f, c2 = 0.31539156525252005f, c4 = 0.5462742152960396f;
+        gx += c0 * y * w[4];
+        gy += c0 * x * w[4];
+        gy += -c0 * z * w[5];
+        gz += -c0 * y * w[5];
+        gx += c2 * (-2.0f * x) * w[6];
+        gy += c2 * (-2.0f * y) * w[6];
+        gz += c2 * (4.0f * z) * w[6];
+        gx += -c0 * z * w[7];
+        gz += -c0 * x * w[7];
+        gx += c4 * (2.0f * x) * w[8];
+        gy += c4 * (-2.0f * y) * w[8];
+    }
+    if (L < 3) return;
+    {
+        const float a = -0.5900435899266435f, b = 2.890611442640554f, c = -0.4570457994644658f;
+        const float d = 0.3731763325901154f, e = 1.445305721320277f;
+        // Y9 = a y (3xx - yy)
+        gx += a * 6.0f * x * y * w[9];
+        gy += a * (3.0f * xx - 3.0f * yy) * w[9];
+        // Y10 = b x y z
+        gx += b * y * z * w[10];
+        gy += b * x * z * w[10];
+        gz += b * x * y * w[10];
+        // Y11 = c y (4zz - xx - yy)
+        gx += c * y * (-2.0f * x) * w[11];
+        gy += c * (4.0f * zz - xx - 3.0f * yy) * w[11];
+        gz += c * y * 8.0f * z * w[11];
+        // Y12 = d z (2zz - 3xx - 3yy)
+        gx += d * z * (-6.0f * x) * w[12];
+        gy += d * z * (-6.0f * y) * w[12];
+        gz += d * (6.0f * zz - 3.0f * xx - 3.0f * yy) * w[12];
+        // Y13 = c x (4zz - xx - yy)
+        gx += c * (4.0f * zz - 3.0f * xx - yy) * w[13];
+        gy += c * x * (-2.0f * y) * w[13];
+        gz += c * x * 8.0f * z * w[13];
+        // Y14 = e z (xx - yy)
+        gx += e * z * 2.0f * x * w[14];
+        gy += e * z * (-2.0f * y) * w[14];
+        gz += e * (xx - yy) * w[14];
+        // Y15 = a x (xx - 3yy)
+        gx += a * (3.0f * xx - 3.0f * yy) * w[15];
+        gy += a * x * (-6.0f * y) * w[15];
+    }
+}
+
+__device__ __forceinline__ float load_sh(const DevGauss& G, int row, int g) {
+    const size_t i = (size_t)row * (size_t)G.n + (size_t)g;
+    if (G.shs_bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(G.shs)[i]);
+    return __ldg(reinterpret_cast<const float*>(G.shs) + i);
+}
+
+// ---------------------------------------------------------------------------
+// Per-Gaussian, view-independent part: activations, R = L(q_l) R(q_r),
+// M = R S, Sigma = M M^T (Eq. 7, Eq. 8).
+// ---------------------------------------------------------------------------
+struct Core {
+    float mu[4];
+    float s[4];
+    float alpha;
+    float qln[4], qrn[4];
+    float nl, nr;
+    float R[16];
+    float M[16];
+    float S[16];  // full symmetric Sigma
+    bool ok;
+};
+
+__device__ __forceinline__ void left_matrix(const float* q, float* L) {
+    const float a = q[0], b = q[1], c = q[2], d = q[3];
+    L[0] = a;  L[1] = -b; L[2] = -c;  L[3] = -d;
+    L[4] = b;  L[5] = a;  L[6] = -d;  L[7] = c;
+    L[8] = c;  L[9] = d;  L[10] = a;  L[11] = -b;
+    L[12] = d; L[13] = -c; L[14] = b; L[15] = a;
+}
+__device__ __forceinline__ void right_matrix(const float* q, float* R) {
+    const float p = q[0], qq = q[1], r = q[2], s = q[3];
+    R[0] = p;   R[1] = -qq; R[2] = -r;  R[3] = -s;
+    R[4] = qq;  R[5] = p;   R[6] = s;   R[7] = -r;
+    R[8] = r;   R[9] = -s;  R[10] = p;  R[11] = qq;
+    R[12] = s;  R[13] = r;  R[14] = -qq; R[15] = p;
+}
+
+__device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
+    const size_t n = (size_t)G.n;
+    float ls[4], ql[4], qr[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        c.mu[i] = __ldg(G.mu + i * n + g);
+        ls[i] = __ldg(G.log_s + i * n + g);
+        ql[i] = __ldg(G.ql + i * n + g);
+        qr[i] = __ldg(G.qr + i * n + g);
+    }
+    const float logit = __ldg(G.logit + g);
+    c.alpha = 1.0f / (1.0f + expf(-logit));
+    const float nl2 = ql[0] * ql[0] + ql[1] * ql[1] + ql[2] * ql[2] + ql[3] * ql[3];
+    const float nr2 = qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3];
+    c.nl = sqrtf(nl2);
+    c.nr = sqrtf(nr2);
+    bool finite = isfinite(logit) && isfinite(nl2) && isfinite(nr2);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        c.s[i] = expf(ls[i]);
+        finite = finite && isfinite(c.mu[i]) && isfinite(c.s[i]) && c.s[i] > 0.0f;
+        c.qln[i] = ql[i] / c.nl;
+        c.qrn[i] = qr[i] / c.nr;
+    }
+    c.ok = finite && nl2 > 1e-24f && nr2 > 1e-24f;
+    float Lm[16], Rm[16];
+    left_matrix(c.qln, Lm);
+    right_matrix(c.qrn, Rm);
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc = fmaf(Lm[i * 4 + k], Rm[k * 4 + j], acc);
+            c.R[i * 4 + j] = acc;
+            c.M[i * 4 + j] = acc * c.s[j];
+        }
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = i; j < 4; j++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc = fmaf(c.M[i * 4 + k], c.M[j * 4 + k], acc);
+            c.S[i * 4 + j] = acc;
+            c.S[j * 4 + i] = acc;
+        }
+}
+
+// Same Sigma in double precision (fallback for ill-conditioned slices).
+static __device__ __noinline__ void core_sigma_f64(const DevGauss& G, int g, double* Sd) {
+    const size_t n = (size_t)G.n;
+    double ql[4], qr[4], s[4], nl = 0.0, nr = 0.0;
+    for (int i = 0; i < 4; i++) {
+        ql[i] = (double)G.ql[i * n + g];
+        qr[i] = (double)G.qr[i * n + g];
+        s[i] = exp((double)G.log_s[i * n + g]);
+        nl += ql[i] * ql[i];
+        nr += qr[i] * qr[i];
+    }
+    nl = sqrt(nl);
+    nr = sqrt(nr);
+    for (int i = 0; i < 4; i++) {
+        ql[i] /= nl;
+        qr[i] /= nr;
+    }
+    const double a = ql[0], b = ql[1], c = ql[2], d = ql[3];
+    const double Lm[16] = {a, -b, -c, -d, b, a, -d, c, c, d, a, -b, d, -c, b, a};
+    const double p = qr[0], q = qr[1], r = qr[2], t = qr[3];
+    const double Rm[16] = {p, -q, -r, -t, q, p, t, -r, r, -t, p, q, t, r, -q, p};
+    double M[16];
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; k++) acc += Lm[i * 4 + k] * Rm[k * 4 + j];
+            M[i * 4 + j] = acc * s[j];
+        }
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; k++) acc += M[i * 4 + k] * M[j * 4 + k];
+            Sd[i * 4 + j] = acc;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// Per-view slice (Eq. 9, Eq. 10) and projection (Eq. 3, Eq. 4).
+// ---------------------------------------------------------------------------
+struct ViewGeom {
+    float p;         // marginal p(t)
+    float dt;        // t - mu_t
+    float mu3[3];    // conditional mean
+    float S3[6];     // conditional covariance (00, 01, 02, 11, 12, 22)
+    float xc[3];     // camera-space mean
+    float T[6];      // J W (2x3)
+    bool clx, cly;   // Jacobian clamp active
+    float cov[3];    // 2D covariance (00, 01, 11) incl. dilation
+    float conic[3];  // (a, b, c)
+    float u, v;
+    float alpha_eff;
+    float radius;
+    int rect[4];     // inclusive tile rect: x0, y0, x1, y1
+    int tiles;       // number of touched tiles (0 = invisible)
+};
+
+__device__ __forceinline__ void slice_view(const Core& c, const DevView& V, const DevOpts& O, const DevGauss& G, int g,
+                                           ViewGeom& w, bool allow_f64) {
+    const float sig = c.S[15];
+    w.dt = V.t - c.mu[3];
+    w.p = expf(-0.5f * w.dt * w.dt / sig);
+    const float inv = 1.0f / sig;
+    const float b0 = c.S[3], b1 = c.S[7], b2 = c.S[11];
+    const float k = w.dt * inv;
+    w.mu3[0] = fmaf(b0, k, c.mu[0]);
+    w.mu3[1] = fmaf(b1, k, c.mu[1]);
+    w.mu3[2] = fmaf(b2, k, c.mu[2]);
+    w.S3[0] = c.S[0] - b0 * b0 * inv;
+    w.S3[1] = c.S[1] - b0 * b1 * inv;
+    w.S3[2] = c.S[2] - b0 * b2 * inv;
+    w.S3[3] = c.S[5] - b1 * b1 * inv;
+    w.S3[4] = c.S[6] - b1 * b2 * inv;
+    w.S3[5] = c.S[10] - b2 * b2 * inv;
+    // Conditioning test: strong cancellation in the Schur complement.
+    if (allow_f64 && (w.S3[0] < O.schur_cond * c.S[0] || w.S3[3] < O.schur_cond * c.S[5] ||
+                      w.S3[5] < O.schur_cond * c.S[10])) {
+        double Sd[16];
+        core_sigma_f64(G, g, Sd);
+        const double sd = Sd[15];
+        const double dtd = (double)V.t - (double)c.mu[3];
+        const double bd[3] = {Sd[3], Sd[7], Sd[11]};
+        for (int i = 0; i < 3; i++) w.mu3[i] = (float)((double)c.mu[i] + bd[i] * dtd / sd);
+        w.S3[0] = (float)(Sd[0] - bd[0] * bd[0] / sd);
+        w.S3[1] = (float)(Sd[1] - bd[0] * bd[1] / sd);
+        w.S3[2] = (float)(Sd[2] - bd[0] * bd[2] / sd);
+        w.S3[3] = (float)(Sd[5] - bd[1] * bd[1] / sd);
+        w.S3[4] = (float)(Sd[6] - bd[1] * bd[2] / sd);
+        w.S3[5] = (float)(Sd[10] - bd[2] * bd[2] / sd);
+        w.p = (float)exp(-0.5 * dtd * dtd / sd);
+    }
+}
+
+// Camera transform, Jacobian, 2D covariance, conic, radius and tile rect.
+// Returns false when the splat is culled (near plane, alpha_eff, empty rect).
+__device__ __forceinline__ bool project_view(const Core& c, const DevView& V, const DevOpts& O, ViewGeom& w,
+                                             bool allow_f64) {
+    w.tiles = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+        w.xc[i] = fmaf(V.W[i * 3 + 0], w.mu3[0], fmaf(V.W[i * 3 + 1], w.mu3[1], fmaf(V.W[i * 3 + 2], w.mu3[2], V.tau[i])));
+    const float Z = w.xc[2];
+    if (!(Z >= O.near_z)) return false;
+    const float iz = 1.0f / Z;
+    float tx = w.xc[0] * iz, ty = w.xc[1] * iz;
+    w.u = fmaf(V.fx, tx, V.cx);
+    w.v = fmaf(V.fy, ty, V.cy);
+    w.clx = false;
+    w.cly = false;
+    if (tx < -V.limx) { tx = -V.limx; w.clx = true; }
+    if (tx > V.limx) { tx = V.limx; w.clx = true; }
+    if (ty < -V.limy) { ty = -V.limy; w.cly = true; }
+    if (ty > V.limy) { ty = V.limy; w.cly = true; }
+    const float J00 = V.fx * iz, J02 = -V.fx * tx * iz, J11 = V.fy * iz, J12 = -V.fy * ty * iz;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        w.T[k] = fmaf(J00, V.W[0 * 3 + k], J02 * V.W[2 * 3 + k]);
+        w.T[3 + k] = fmaf(J11, V.W[1 * 3 + k], J12 * V.W[2 * 3 + k]);
+    }
+    // Sigma_2d = T Sigma3 T^T + delta I
+    const float* S = w.S3;
+    float TS[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const float* t = &w.T[3 * r];
+        TS[r][0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+        TS[r][1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+        TS[r][2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    }
+    w.cov[0] = TS[0][0] * w.T[0] + TS[0][1] * w.T[1] + TS[0][2] * w.T[2] + O.dilation;
+    w.cov[1] = TS[0][0] * w.T[3] + TS[0][1] * w.T[4] + TS[0][2] * w.T[5];
+    w.cov[2] = TS[1][0] * w.T[3] + TS[1][1] * w.T[4] + TS[1][2] * w.T[5] + O.dilation;
+    float det = w.cov[0] * w.cov[2] - w.cov[1] * w.cov[1];
+    if (allow_f64 && det < O.conic_cond * w.cov[0] * w.cov[2]) {
+        // ill-conditioned 2x2: recompute covariance, determinant and inverse in FP64
+        double Td[6], Sd[6];
+        for (int i = 0; i < 6; i++) { Td[i] = w.T[i]; Sd[i] = w.S3[i]; }
+        double TSd[2][3];
+        for (int r = 0; r < 2; r++) {
+            const double* t = &Td[3 * r];
+            TSd[r][0] = t[0] * Sd[0] + t[1] * Sd[1] + t[2] * Sd[2];
+            TSd[r][1] = t[0] * Sd[1] + t[1] * Sd[3] + t[2] * Sd[4];
+            TSd[r][2] = t[0] * Sd[2] + t[1] * Sd[4] + t[2] * Sd[5];
+        }
+        const double c00 = TSd[0][0] * Td[0] + TSd[0][1] * Td[1] + TSd[0][2] * Td[2] + (double)O.dilation;
+        const double c01 = TSd[0][0] * Td[3] + TSd[0][1] * Td[4] + TSd[0][2] * Td[5];
+        const double c11 = TSd[1][0] * Td[3] + TSd[1][1] * Td[4] + TSd[1][2] * Td[5] + (double)O.dilation;
+        const double dd = c00 * c11 - c01 * c01;
+        if (!(dd > 0.0)) return false;
+        w.cov[0] = (float)c00;
+        w.cov[1] = (float)c01;
+        w.cov[2] = (float)c11;
+        w.conic[0] = (float)(c11 / dd);
+        w.conic[1] = (float)(-c01 / dd);
+        w.conic[2] = (float)(c00 / dd);
+        det = (float)dd;
+    } else {
+        if (!(det > 0.0f)) return false;
+        const float idet = 1.0f / det;
+        w.conic[0] = w.cov[2] * idet;
+        w.conic[1] = -w.cov[1] * idet;
+        w.conic[2] = w.cov[0] * idet;
+    }
+    w.alpha_eff = c.alpha * w.p;
+    if (!(w.alpha_eff >= O.alpha_min)) return false;
+    // support radius: beyond it alpha_eff * G < alpha_min (plus half a pixel margin)
+    const float mid = 0.5f * (w.cov[0] + w.cov[2]);
+    const float lmax = mid + sqrtf(fmaxf(mid * mid - det, 0.0f));
+    const float lnr = fmaxf(logf(w.alpha_eff) - O.ln_alpha_min, 0.0f);
+    w.radius = sqrtf(2.0f * lnr * lmax) + 0.5f;
+    // pixels i with |i - u| <= r, clamped to the image; tiles containing them
+    const float fx0 = fmaxf(ceilf(w.u - w.radius), 0.0f);
+    const float fx1 = fminf(floorf(w.u + w.radius), (float)(V.width - 1));
+    const float fy0 = fmaxf(ceilf(w.v - w.radius), 0.0f);
+    const float fy1 = fminf(floorf(w.v + w.radius), (float)(V.height - 1));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
+    w.rect[0] = (int)fx0 / kTile;
+    w.rect[1] = (int)fy0 / kTile;
+    w.rect[2] = (int)fx1 / kTile;
+    w.rect[3] = (int)fy1 / kTile;
+    w.tiles = (w.rect[2] - w.rect[0] + 1) * (w.rect[3] - w.rect[1] + 1);
+    return true;
+}
+
+// Unit view direction from the camera centre to the conditional mean.
+__device__ __forceinline__ float view_dir(const ViewGeom& w, const DevView& V, float* d) {
+    const float e0 = w.mu3[0] - V.campos[0], e1 = w.mu3[1] - V.campos[1], e2 = w.mu3[2] - V.campos[2];
+    const float nrm = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+    const float inv = 1.0f / nrm;
+    d[0] = e0 * inv;
+    d[1] = e1 * inv;
+    d[2] = e2 * inv;
+    return nrm;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (defined in the .cu files, called by the C ABI in api.cu).
+// ---------------------------------------------------------------------------
+cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const StateLayout& lay,
+                                 char* state, uint32_t capacity, cudaStream_t st);
+cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int sm_count,
+                            cudaStream_t st, int* out_buf);
+cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
+                          float* image, float* final_T, int32_t* n_last, cudaStream_t st);
+cudaError_t launch_render_backward(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
+                                   int pair_buf, const float* final_T, const int32_t* n_last, const float* dL_dimage,
+                                   cudaStream_t st);
+cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const StateLayout& lay,
+                                    char* state, const fgs4d_gaussian_grads& grads, cudaStream_t st);
+
+// number of radix passes etc. needed by the host to know which buffer holds the result
+int pair_sort_bits(uint32_t total_tiles);
+
+// Host-side count of kernel launches issued by this library (all threads).
+void count_launches(unsigned k);
+
+}  // namespace fgs4d

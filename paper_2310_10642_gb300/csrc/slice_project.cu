@@ -1,0 +1,410 @@
+// slice_project.cu -- per-Gaussian kernels of the 4DGS rendering routine.
+//
+// slice_project_kernel (forward): for each Gaussian and each view of the
+// batch, Eq. 7-8 (covariance from the quaternion pair), Eq. 9-10 (conditional
+// 3D Gaussian, marginal p(t) and the p(t) < p_min filter of Sec. 4.2),
+// Eq. 11 (4D spherindrical-harmonic colour) and Eq. 3-4 (EWA projection),
+// written as one 48-byte splat record per (view, Gaussian).
+//
+// project_backward_kernel (adjoint): for each Gaussian, sums over the views
+// the chain rule from the per-splat 2D gradient (written by the compositing
+// adjoint) back to the raw parameters.  One thread owns one Gaussian, so no
+// atomics are needed; the 4DSH coefficient gradients are accumulated in
+// shared memory (one column per thread) and written once, coalesced.
+#include "fgs4d_internal.cuh"
+
+namespace fgs4d {
+
+template <int L>
+__device__ __forceinline__ void color_forward(const DevGauss& G, int g, const ViewGeom& w, const DevView& V,
+                                              float* raw) {
+    constexpr int NB = (L + 1) * (L + 1);
+    float d[3];
+    view_dir(w, V, d);
+    float Y[16];
+    sh_eval(L, d[0], d[1], d[2], Y);
+    raw[0] = raw[1] = raw[2] = 0.0f;
+    for (int f = 0; f <= G.K; f++) {
+        const float cf = cospif(2.0f * (float)f * w.dt * G.inv_period);
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+            const float b = cf * Y[j];
+            const int row = (f * NB + j) * 3;
+            raw[0] = fmaf(b, load_sh(G, row + 0, g), raw[0]);
+            raw[1] = fmaf(b, load_sh(G, row + 1, g), raw[1]);
+            raw[2] = fmaf(b, load_sh(G, row + 2, g), raw[2]);
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, const __grid_constant__ ViewSet VS,
+                                                            const DevOpts O, SplatRecord* __restrict__ rec,
+                                                            uint32_t* __restrict__ tiles_touched,
+                                                            uint32_t* __restrict__ depth_key,
+                                                            uint32_t* __restrict__ counters) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G.n) return;
+    const size_t n = (size_t)G.n;
+    Core c;
+    load_core(G, g, c);
+    if (!c.ok) {
+        atomicOr(&counters[2], FGS4D_STATUS_NONFINITE);
+        for (int v = 0; v < VS.n; v++) tiles_touched[(size_t)v * n + g] = 0u;
+        return;
+    }
+    uint32_t n_vis = 0;
+    for (int v = 0; v < VS.n; v++) {
+        const DevView& V = VS.v[v];
+        const size_t idx = (size_t)v * n + g;
+        ViewGeom w;
+        slice_view(c, V, O, G, g, w, true);
+        const bool vis = (w.p >= O.p_min) && project_view(c, V, O, w, true);
+        if (!vis) {
+            tiles_touched[idx] = 0u;
+            continue;
+        }
+        float raw[3];
+        color_forward<L>(G, g, w, V, raw);
+        uint32_t flags = 0;
+        float col[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            const float x = raw[ch] + 0.5f;
+            flags |= (x > 0.0f) ? 0u : (1u << ch);
+            col[ch] = fmaxf(x, 0.0f);
+        }
+        SplatRecord r;
+        r.r0 = make_float4(w.u, w.v, w.conic[0], w.conic[1]);
+        r.r1 = make_float4(w.conic[2], w.alpha_eff, col[0], col[1]);
+        r.r2 = make_float4(col[2], w.xc[2], w.radius, __uint_as_float(flags));
+        rec[idx] = r;
+        tiles_touched[idx] = (uint32_t)w.tiles;
+        depth_key[idx] = __float_as_uint(w.xc[2]);
+        n_vis++;
+    }
+    (void)n_vis;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+constexpr int kBwdThreads = 128;
+
+template <int L>
+__global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
+    const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, const uint32_t* __restrict__ tiles_touched,
+    const float4* __restrict__ grad2d, const fgs4d_gaussian_grads out) {
+    constexpr int NB = (L + 1) * (L + 1);
+    extern __shared__ float s_acc[];  // [rows][kBwdThreads]
+    const int tid = threadIdx.x;
+    const int g = blockIdx.x * blockDim.x + tid;
+    if (g >= G.n) return;
+    const size_t n = (size_t)G.n;
+    const int rows = 3 * NB * (G.K + 1);
+    for (int r = 0; r < rows; r++) s_acc[r * kBwdThreads + tid] = 0.0f;
+
+    Core c;
+    load_core(G, g, c);
+    float gmu[4] = {0, 0, 0, 0};
+    float GS[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) GS[i] = 0.0f;
+    float galpha = 0.0f, m2d = 0.0f;
+
+    if (c.ok) {
+        const float sig = c.S[15];
+        const float b[3] = {c.S[3], c.S[7], c.S[11]};
+        for (int v = 0; v < VS.n; v++) {
+            const size_t idx = (size_t)v * n + g;
+            if (tiles_touched[idx] == 0u) continue;
+            const DevView& V = VS.v[v];
+            ViewGeom w;
+            slice_view(c, V, O, G, g, w, true);
+            if (!project_view(c, V, O, w, true)) continue;
+            const float4 q0 = grad2d[3 * idx + 0];
+            const float4 q1 = grad2d[3 * idx + 1];
+            const float4 q2 = grad2d[3 * idx + 2];
+            const float du = q0.x, dv = q0.y, da = q0.z, db = q0.w, dc = q1.x, dae = q1.y;
+            const float dcol[3] = {q1.z, q1.w, q2.x};
+            m2d += sqrtf(du * du + dv * dv);
+
+            // ---- colour (Eq. 11) ----
+            float d[3];
+            const float nrm = view_dir(w, V, d);
+            float Y[16];
+            sh_eval(L, d[0], d[1], d[2], Y);
+            float wsum[16];
+#pragma unroll
+            for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
+            float ddt = 0.0f;
+            for (int ch = 0; ch < 3; ch++) {
+                float P[16];
+#pragma unroll
+                for (int j = 0; j < NB; j++) P[j] = 0.0f;
+                float Q = 0.0f;
+                for (int f = 0; f <= G.K; f++) {
+                    const float arg = 2.0f * (float)f * w.dt * G.inv_period;
+                    const float cf = cospif(arg);
+                    const float sf = sinpif(arg);
+                    const float om = 6.283185307179586f * (float)f * G.inv_period;
+                    float kY = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < NB; j++) {
+                        const float k = load_sh(G, (f * NB + j) * 3 + ch, g);
+                        P[j] = fmaf(cf, k, P[j]);
+                        kY = fmaf(k, Y[j], kY);
+                    }
+                    Q = fmaf(-om * sf, kY, Q);
+                }
+                float raw = 0.0f;
+#pragma unroll
+                for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
+                const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
+                if (graw != 0.0f) {
+#pragma unroll
+                    for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
+                    ddt = fmaf(graw, Q, ddt);
+                    for (int f = 0; f <= G.K; f++) {
+                        const float cf = cospif(2.0f * (float)f * w.dt * G.inv_period);
+                        const float gc = graw * cf;
+#pragma unroll
+                        for (int j = 0; j < NB; j++) s_acc[((f * NB + j) * 3 + ch) * kBwdThreads + tid] += gc * Y[j];
+                    }
+                }
+            }
+            float gd[3];
+            sh_grad(L, d[0], d[1], d[2], wsum, gd[0], gd[1], gd[2]);
+            const float gdd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+            float dmu3[3];
+            const float inrm = 1.0f / nrm;
+#pragma unroll
+            for (int i = 0; i < 3; i++) dmu3[i] = (gd[i] - gdd * d[i]) * inrm;
+
+            // ---- conic -> 2D covariance: G2 = -Q Gc Q ----
+            const float a = w.conic[0], bq = w.conic[1], cq = w.conic[2];
+            const float g00 = da, g01 = 0.5f * db, g11 = dc;
+            // QG = Q * Gc
+            const float qg00 = a * g00 + bq * g01, qg01 = a * g01 + bq * g11;
+            const float qg10 = bq * g00 + cq * g01, qg11 = bq * g01 + cq * g11;
+            const float G200 = -(qg00 * a + qg01 * bq);
+            const float G201 = -(qg00 * bq + qg01 * cq);
+            const float G211 = -(qg10 * bq + qg11 * cq);
+
+            // ---- Eq. 4: dSigma3 = T^T G2 T, dT = 2 G2 T Sigma3 ----
+            const float* T = w.T;
+            float GT[2][3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                GT[0][k] = G200 * T[k] + G201 * T[3 + k];
+                GT[1][k] = G201 * T[k] + G211 * T[3 + k];
+            }
+            float G3[6];  // 00 01 02 11 12 22
+            G3[0] = T[0] * GT[0][0] + T[3] * GT[1][0];
+            G3[1] = T[0] * GT[0][1] + T[3] * GT[1][1];
+            G3[2] = T[0] * GT[0][2] + T[3] * GT[1][2];
+            G3[3] = T[1] * GT[0][1] + T[4] * GT[1][1];
+            G3[4] = T[1] * GT[0][2] + T[4] * GT[1][2];
+            G3[5] = T[2] * GT[0][2] + T[5] * GT[1][2];
+            const float* S3 = w.S3;
+            float dT[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                dT[r][0] = 2.0f * (GT[r][0] * S3[0] + GT[r][1] * S3[1] + GT[r][2] * S3[2]);
+                dT[r][1] = 2.0f * (GT[r][0] * S3[1] + GT[r][1] * S3[3] + GT[r][2] * S3[4]);
+                dT[r][2] = 2.0f * (GT[r][0] * S3[2] + GT[r][1] * S3[4] + GT[r][2] * S3[5]);
+            }
+            // dJ = dT W^T
+            float dJ[2][3];
+#pragma unroll
+            for (int r = 0; r < 2; r++)
+#pragma unroll
+                for (int m = 0; m < 3; m++)
+                    dJ[r][m] = dT[r][0] * V.W[m * 3 + 0] + dT[r][1] * V.W[m * 3 + 1] + dT[r][2] * V.W[m * 3 + 2];
+
+            // ---- J and the projected mean w.r.t. camera coordinates ----
+            const float X = w.xc[0], Yc = w.xc[1], Z = w.xc[2];
+            const float iz = 1.0f / Z, iz2 = iz * iz;
+            float tx = X * iz, ty = Yc * iz;
+            tx = fminf(fmaxf(tx, -V.limx), V.limx);
+            ty = fminf(fmaxf(ty, -V.limy), V.limy);
+            float dxc[3] = {0.0f, 0.0f, 0.0f};
+            dxc[2] += dJ[0][0] * (-V.fx * iz2) + dJ[1][1] * (-V.fy * iz2);
+            dxc[2] += dJ[0][2] * (V.fx * tx * iz2) + dJ[1][2] * (V.fy * ty * iz2);
+            if (!w.clx) {
+                dxc[0] += dJ[0][2] * (-V.fx * iz2);
+                dxc[2] += dJ[0][2] * (V.fx * X * iz2 * iz);
+            }
+            if (!w.cly) {
+                dxc[1] += dJ[1][2] * (-V.fy * iz2);
+                dxc[2] += dJ[1][2] * (V.fy * Yc * iz2 * iz);
+            }
+            dxc[0] += du * V.fx * iz;
+            dxc[1] += dv * V.fy * iz;
+            dxc[2] += -du * V.fx * X * iz2 - dv * V.fy * Yc * iz2;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+                dmu3[i] += V.W[0 * 3 + i] * dxc[0] + V.W[1 * 3 + i] * dxc[1] + V.W[2 * 3 + i] * dxc[2];
+
+            // ---- Eq. 9, Eq. 10 ----
+            const float dp = dae * c.alpha;
+            galpha += dae * w.p;
+            const float isig = 1.0f / sig;
+            float G3b[3];
+            G3b[0] = G3[0] * b[0] + G3[1] * b[1] + G3[2] * b[2];
+            G3b[1] = G3[1] * b[0] + G3[3] * b[1] + G3[4] * b[2];
+            G3b[2] = G3[2] * b[0] + G3[4] * b[1] + G3[5] * b[2];
+            const float mb = dmu3[0] * b[0] + dmu3[1] * b[1] + dmu3[2] * b[2];
+            const float bGb = b[0] * G3b[0] + b[1] * G3b[1] + b[2] * G3b[2];
+            const float dt = w.dt;
+            const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
+            ddt += mb * isig - dp * w.p * dt * isig;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
+                GS[i * 4 + 3] += 0.5f * dbi;
+                gmu[i] += dmu3[i];
+            }
+            gmu[3] -= ddt;
+            GS[0] += G3[0];
+            GS[1] += G3[1];
+            GS[2] += G3[2];
+            GS[5] += G3[3];
+            GS[6] += G3[4];
+            GS[10] += G3[5];
+            GS[15] += dsig;
+        }
+    }
+
+    // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
+    float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
+    if (c.ok) {
+        // symmetrise the accumulator (only the upper triangle was written)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
+        float dR[16];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], c.M[j * 4 + k], acc);
+                const float dM = 2.0f * acc;
+                dR[i * 4 + k] = dM * c.s[k];
+                gls[k] = fmaf(dM, c.R[i * 4 + k], gls[k]);
+            }
+#pragma unroll
+        for (int k = 0; k < 4; k++) gls[k] *= c.s[k];
+        float Lm[16], Rm[16];
+        left_matrix(c.qln, Lm);
+        right_matrix(c.qrn, Rm);
+        float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float x = 0.0f, y = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
+                    y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
+                }
+                D[i * 4 + j] = x;
+                E[i * 4 + j] = y;
+            }
+        const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
+                             -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
+        const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
+                             -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
+        float dl = 0.0f, dr = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            dl = fmaf(gl[i], c.qln[i], dl);
+            dr = fmaf(gr[i], c.qrn[i], dr);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            gql[i] = (gl[i] - dl * c.qln[i]) / c.nl;
+            gqr[i] = (gr[i] - dr * c.qrn[i]) / c.nr;
+        }
+        glogit = galpha * c.alpha * (1.0f - c.alpha);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        out.mu[i * n + g] = gmu[i];
+        out.log_scale[i * n + g] = gls[i];
+        out.q_left[i * n + g] = gql[i];
+        out.q_right[i * n + g] = gqr[i];
+    }
+    out.opacity_logit[g] = glogit;
+    if (out.mean2d_abs) out.mean2d_abs[g] = m2d;
+    for (int r = 0; r < rows; r++) out.shs[(size_t)r * n + g] = s_acc[r * kBwdThreads + tid];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+__global__ void init_counters_kernel(uint32_t* counters, uint32_t capacity) {
+    counters[0] = 0u;  // visible splats
+    counters[1] = 0u;  // pairs
+    counters[2] = 0u;  // status bits
+    counters[3] = capacity;
+}
+
+cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const StateLayout& lay,
+                                 char* state, uint32_t capacity, cudaStream_t st) {
+    uint32_t* counters = reinterpret_cast<uint32_t*>(state + lay.counters);
+    init_counters_kernel<<<1, 1, 0, st>>>(counters, capacity);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (G.n == 0) return cudaSuccess;
+    const int threads = 128;
+    const int blocks = (G.n + threads - 1) / threads;
+    auto* rec = reinterpret_cast<SplatRecord*>(state + lay.records);
+    auto* tt = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
+    auto* dk = reinterpret_cast<uint32_t*>(state + lay.depth_key);
+    switch (G.L) {
+        case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
+        case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
+        case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
+        default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
+                            const float4* g2, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
+    const int rows = 3 * (L + 1) * (L + 1) * (G.K + 1);
+    const size_t smem = (size_t)rows * kBwdThreads * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(project_backward_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (G.n + kBwdThreads - 1) / kBwdThreads;
+    project_backward_kernel<L><<<blocks, kBwdThreads, smem, st>>>(G, VS, O, tt, g2, grads);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const StateLayout& lay,
+                                    char* state, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
+    if (G.n == 0) return cudaSuccess;
+    auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
+    auto* g2 = reinterpret_cast<const float4*>(state + lay.grad2d);
+    switch (G.L) {
+        case 0: return launch_pb<0>(G, VS, O, tt, g2, grads, st);
+        case 1: return launch_pb<1>(G, VS, O, tt, g2, grads, st);
+        case 2: return launch_pb<2>(G, VS, O, tt, g2, grads, st);
+        default: return launch_pb<3>(G, VS, O, tt, g2, grads, st);
+    }
+}
+
+}  // namespace fgs4d

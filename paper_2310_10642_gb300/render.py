@@ -1,0 +1,200 @@
+"""PyTorch front end of libfgs4d: device buffers, streams and autograd.
+
+``Frame`` owns the per-frame state for one (number of Gaussians, views,
+options) configuration and calls the four C entry points in order.  PyTorch
+only allocates memory and supplies the stream; every step of the rendering
+routine and of its adjoint runs in the CUDA kernels behind the C ABI.
+
+``render(params, views)`` is the differentiable entry point: it returns the
+list of [3, H, W] images and, through ``Render4DGS``, back-propagates into the
+raw parameters (mu, log_s, ql, qr, logit, shs) with transmittance recomputed
+in the backward kernels rather than stored per splat.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import native as N
+
+PARAM_KEYS = ("mu", "log_s", "ql", "qr", "logit", "shs")
+
+
+def params_to_device(params: dict, device="cuda", shs_dtype=torch.float32) -> dict:
+    """Copies numpy/torch parameters (the inputs-module layout) to the device."""
+    out = {}
+    for k in PARAM_KEYS:
+        t = torch.as_tensor(params[k])
+        dt = shs_dtype if k == "shs" else torch.float32
+        out[k] = t.to(device=device, dtype=dt).contiguous()
+    for k in ("sh_degree", "n_freq", "period"):
+        out[k] = params[k]
+    return out
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def gaussians_struct(p: dict) -> N.Gaussians:
+    shs = p["shs"]
+    if shs.dtype == torch.bfloat16:
+        dtype = N.BF16
+    elif shs.dtype == torch.float32:
+        dtype = N.F32
+    else:
+        raise TypeError("shs must be float32 or bfloat16")
+    for k in PARAM_KEYS:
+        t = p[k]
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{k} must be a contiguous CUDA tensor")
+    n = p["logit"].shape[0]
+    return N.Gaussians(_ptr(p["mu"]), _ptr(p["log_s"]), _ptr(p["ql"]), _ptr(p["qr"]), _ptr(p["logit"]),
+                       _ptr(p["shs"]), n, int(p["sh_degree"]), int(p["n_freq"]), float(p.get("period", 1.0)), dtype)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Frame:
+    """State and output buffers for rendering ``n`` Gaussians into ``views``.
+
+    pair_capacity: room for (splat, tile) pairs; ``None`` picks an estimate
+    and ``forward(check=True)`` grows it when the device reports overflow.
+    """
+
+    def __init__(self, n: int, views: list, options: dict | None = None, pair_capacity: int | None = None,
+                 device="cuda"):
+        if len(views) < 1 or len(views) > N.MAX_VIEWS:
+            raise ValueError(f"1..{N.MAX_VIEWS} views per frame")
+        self.n = int(n)
+        self.views = list(views)
+        self.nv = len(views)
+        self.device = torch.device(device)
+        self.c_views = N.make_views(self.views)
+        self.c_opts = N.make_options(options)
+        self.total_pixels = N.fgs4d_total_pixels(self.c_views, self.nv)
+        self.pix_offsets = []
+        off = 0
+        for v in self.views:
+            self.pix_offsets.append(off)
+            off += int(v["width"]) * int(v["height"])
+        if pair_capacity is None:
+            tiles = sum(((int(v["width"]) + 15) // 16) * ((int(v["height"]) + 15) // 16) for v in self.views)
+            pair_capacity = max(1 << 16, min(self.n * self.nv * 8, tiles * 4096))
+        self.image = torch.empty(3 * self.total_pixels, device=self.device, dtype=torch.float32)
+        self.final_T = torch.empty(self.total_pixels, device=self.device, dtype=torch.float32)
+        self.n_last = torch.empty(self.total_pixels, device=self.device, dtype=torch.int32)
+        self._alloc(int(pair_capacity))
+
+    def _alloc(self, cap: int):
+        self.pair_capacity = cap
+        self.state_bytes = N.fgs4d_state_size(self.n, self.c_views, self.nv, cap, self.c_opts)
+        self.state = torch.empty(self.state_bytes, device=self.device, dtype=torch.uint8)
+        assert self.state.data_ptr() % 256 == 0
+
+    # ---------------------------------------------------------------- stages
+    def slice_project(self, params: dict, stream=None):
+        g = gaussians_struct(params)
+        if g.n != self.n:
+            raise ValueError("number of Gaussians differs from the frame's")
+        N.fgs4d_slice_project(g, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                              _stream(stream))
+
+    def bin_sort(self, stream=None):
+        N.fgs4d_bin_sort(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                         _stream(stream))
+
+    def render(self, stream=None):
+        N.fgs4d_render(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                       self.image.data_ptr(), self.final_T.data_ptr(), self.n_last.data_ptr(), _stream(stream))
+
+    def counters(self, stream=None) -> N.Counters:
+        return N.fgs4d_read_counters(self.state.data_ptr(), _stream(stream))
+
+    def forward(self, params: dict, stream=None, check: bool = True) -> torch.Tensor:
+        """slice_project -> bin_sort -> render.  With check=True, reads the
+        device counters (one synchronisation) and re-runs with a larger pair
+        capacity on overflow."""
+        for _ in range(4):
+            self.slice_project(params, stream)
+            self.bin_sort(stream)
+            self.render(stream)
+            if not check:
+                return self.image
+            c = self.counters(stream)
+            if c.status & N.STATUS_PAIR_OVERFLOW:
+                self._alloc(int(c.n_pairs * 1.25) + 1024)
+                continue
+            self.last_counters = c
+            return self.image
+        raise RuntimeError("pair capacity could not be sized")
+
+    def backward(self, params: dict, dL_dimage: torch.Tensor, grads: dict | None = None, stream=None,
+                 mean2d: bool = False) -> dict:
+        g = gaussians_struct(params)
+        if grads is None:
+            grads = {k: torch.empty(params[k].shape, device=self.device, dtype=torch.float32) for k in PARAM_KEYS}
+        if mean2d and "mean2d_abs" not in grads:
+            grads["mean2d_abs"] = torch.empty(self.n, device=self.device, dtype=torch.float32)
+        dL = dL_dimage.contiguous()
+        if dL.dtype != torch.float32 or dL.numel() != 3 * self.total_pixels:
+            raise ValueError("dL_dimage must be float32 with the image's layout")
+        gs = N.GaussianGrads(_ptr(grads["mu"]), _ptr(grads["log_s"]), _ptr(grads["ql"]), _ptr(grads["qr"]),
+                             _ptr(grads["logit"]), _ptr(grads["shs"]), _ptr(grads.get("mean2d_abs")))
+        N.fgs4d_render_backward(g, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                                self.final_T.data_ptr(), self.n_last.data_ptr(), dL.data_ptr(), gs, _stream(stream))
+        return grads
+
+    # ---------------------------------------------------------------- views of the packed outputs
+    def split(self, packed: torch.Tensor, channels: int = 3) -> list:
+        out = []
+        for v, off in zip(self.views, self.pix_offsets):
+            w, h = int(v["width"]), int(v["height"])
+            out.append(packed[channels * off: channels * (off + w * h)].view(channels, h, w) if channels > 1
+                       else packed[off: off + w * h].view(h, w))
+        return out
+
+    def pack(self, images: list) -> torch.Tensor:
+        return torch.cat([im.reshape(-1) for im in images])
+
+    def layout(self) -> N.StateLayoutInfo:
+        return N.fgs4d_state_layout(self.n, self.c_views, self.nv, self.c_opts, self.state_bytes)
+
+
+class Render4DGS(torch.autograd.Function):
+    """images_packed = Render4DGS.apply(frame, mu, log_s, ql, qr, logit, shs)."""
+
+    @staticmethod
+    def forward(ctx, frame: Frame, mu, log_s, ql, qr, logit, shs, sh_degree: int, n_freq: int, period: float):
+        params = dict(mu=mu.detach(), log_s=log_s.detach(), ql=ql.detach(), qr=qr.detach(), logit=logit.detach(),
+                      shs=shs.detach(), sh_degree=sh_degree, n_freq=n_freq, period=period)
+        img = frame.forward(params).clone()
+        ctx.frame = frame
+        ctx.meta = (sh_degree, n_freq, period)
+        ctx.save_for_backward(mu, log_s, ql, qr, logit, shs)
+        return img
+
+    @staticmethod
+    def backward(ctx, dimg):
+        mu, log_s, ql, qr, logit, shs = ctx.saved_tensors
+        L, K, T = ctx.meta
+        params = dict(mu=mu.detach(), log_s=log_s.detach(), ql=ql.detach(), qr=qr.detach(), logit=logit.detach(),
+                      shs=shs.detach(), sh_degree=L, n_freq=K, period=T)
+        g = ctx.frame.backward(params, dimg.float())
+        gshs = g["shs"].to(shs.dtype)
+        return None, g["mu"], g["log_s"], g["ql"], g["qr"], g["logit"], gshs, None, None, None
+
+
+def render(params: dict, views: list, options: dict | None = None, frame: Frame | None = None):
+    """Differentiable render of all views; returns (list of [3,H,W] images, frame)."""
+    n = params["logit"].shape[0]
+    if frame is None:
+        frame = Frame(n, views, options, device=params["mu"].device)
+    packed = Render4DGS.apply(frame, params["mu"], params["log_s"], params["ql"], params["qr"], params["logit"],
+                              params["shs"], int(params["sh_degree"]), int(params["n_freq"]),
+                              float(params.get("period", 1.0)))
+    return frame.split(packed), frame

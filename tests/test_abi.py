@@ -1,0 +1,104 @@
+"""The C-ABI library loads, exports every function include/*.h declares, and
+rejects bad arguments on the host (no GPU needed for any of this)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2310_10642_gb300 import inputs as I
+from paper_2310_10642_gb300 import native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    N.build()
+    return N.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//.*", "", text)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(fgs4d_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_path():
+    names = declared_functions()
+    for fn in ("fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward"):
+        assert fn in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for fn in names:
+        assert hasattr(lib, fn), f"{fn} declared but not exported"
+    assert set(N.EXPORTS) <= set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert lib.fgs4d_abi_version() == 1
+    for code in range(6):
+        assert len(lib.fgs4d_status_string(code)) > 0
+
+
+def test_default_options_match_readings(lib):
+    o = N.fgs4d_default_options()
+    assert abs(o.p_min - 0.05) < 1e-7 and abs(o.near_z - 0.2) < 1e-7
+    assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.alpha_max - 0.99) < 1e-7
+    assert abs(o.T_min - 1e-4) < 1e-10 and abs(o.dilation - 0.3) < 1e-7
+
+
+def _views(k=2, w=100, h=60):
+    return N.make_views([I.view((0, 0, 4), w, h, 0.5) for _ in range(k)])
+
+
+def test_state_size_grows_with_capacity(lib):
+    o = N.fgs4d_default_options()
+    v = _views()
+    a = N.fgs4d_state_size(1000, v, 2, 0, o)
+    b = N.fgs4d_state_size(1000, v, 2, 100000, o)
+    assert b - a >= 16 * 100000
+    info = N.fgs4d_state_layout(1000, v, 2, o, b)
+    assert 100000 <= info.pair_capacity < 100000 + 64 and info.n_splats == 2000
+    assert info.total_tiles == 2 * 7 * 4
+    assert N.fgs4d_total_pixels(v, 2) == 2 * 6000
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    o = N.fgs4d_default_options()
+    v = _views()
+    size = ctypes.c_size_t()
+    # bad view count, negative n, bad capacity
+    assert lib.fgs4d_state_size(10, v, 0, 10, ctypes.byref(o), ctypes.byref(size)) == 1
+    assert lib.fgs4d_state_size(10, v, N.MAX_VIEWS + 1, 10, ctypes.byref(o), ctypes.byref(size)) == 1
+    assert lib.fgs4d_state_size(-1, v, 2, 10, ctypes.byref(o), ctypes.byref(size)) == 1
+    assert lib.fgs4d_state_size(10, v, 2, -5, ctypes.byref(o), ctypes.byref(size)) == 1
+    # bad options
+    for field, val in (("alpha_max", 1.5), ("alpha_min", 0.0), ("near_z", 0.0), ("T_min", float("nan"))):
+        bad = N.fgs4d_default_options()
+        setattr(bad, field, val)
+        assert lib.fgs4d_state_size(10, v, 2, 10, ctypes.byref(bad), ctypes.byref(size)) == 1
+    # bad view sizes
+    bv = _views(1, 0, 10)
+    assert lib.fgs4d_state_size(10, bv, 1, 10, ctypes.byref(o), ctypes.byref(size)) == 1
+    # null / misaligned state and null gaussian arrays are rejected before any launch
+    g = N.Gaussians(None, None, None, None, None, None, 10, 1, 1, 1.0, 0)
+    assert lib.fgs4d_slice_project(ctypes.byref(g), v, 2, ctypes.byref(o), None, 0, None) == 1
+    g2 = N.Gaussians(16, 32, 48, 64, 80, 96, 10, 5, 1, 1.0, 0)  # sh degree out of range
+    assert lib.fgs4d_slice_project(ctypes.byref(g2), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    g3 = N.Gaussians(16, 32, 48, 64, 80, 96, 10, 1, 1, 0.0, 0)  # period 0
+    assert lib.fgs4d_slice_project(ctypes.byref(g3), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    g4 = N.Gaussians(16, 32, 48, 64, 80, 97, 10, 1, 1, 1.0, 0)  # misaligned shs
+    assert lib.fgs4d_slice_project(ctypes.byref(g4), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    # state smaller than the fixed part
+    assert lib.fgs4d_bin_sort(10, v, 2, ctypes.byref(o), 256, 1024, None) == 2
+    assert lib.fgs4d_render(10, v, 2, ctypes.byref(o), 256, 1 << 30, None, None, None, None) == 1

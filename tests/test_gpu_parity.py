@@ -1,0 +1,362 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+Images: max-abs <= 2e-4 per channel on every pixel the oracle does not flag
+(a flagged pixel has a discrete decision within rounding distance of its
+threshold, where FP32 may legitimately decide the other way; flagged pixels
+must stay rare).  Gradients: relative error <= 1e-3 per parameter group,
+with dL/dimage zero on flagged pixels so that both sides differentiate the
+same piecewise-smooth function.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2310_10642_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 2e-4
+GRAD_TOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10642_gb300 import native
+    native.build()
+    native.lib()
+
+
+def gpu_forward(G, views, opts=None, shs_dtype=None, capacity=None):
+    from paper_2310_10642_gb300 import render as R
+    p = R.params_to_device(G, shs_dtype=shs_dtype or torch.float32)
+    fr = R.Frame(G["logit"].shape[0], views, opts, pair_capacity=capacity)
+    fr.forward(p)
+    torch.cuda.synchronize()
+    imgs = [x.double().cpu().numpy() for x in fr.split(fr.image)]
+    Ts = [x.double().cpu().numpy() for x in fr.split(fr.final_T, 1)]
+    return fr, p, imgs, Ts
+
+
+def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.02):
+    ok = (ref["flags"] & 1) == 0
+    assert 1.0 - ok.mean() <= max_flag_frac, f"too many borderline pixels: {1 - ok.mean():.4f}"
+    err = np.abs(img - ref["image"])[:, ok]
+    assert err.max() <= tol, f"image max-abs {err.max():.3e}"
+    errT = np.abs(Tg - ref["T"])[ok]
+    assert errT.max() <= tol, f"T max-abs {errT.max():.3e}"
+
+
+# ---------------------------------------------------------------------------- forward
+def test_forward_config0_full_frame():
+    c = I.config(0)
+    G, views = c["gaussians"], c["views"]
+    fr, _, imgs, Ts = gpu_forward(G, views)
+    ref = O.render(G, views[0])
+    assert fr.last_counters.n_visible == ref["n_visible"]
+    assert_image_parity(imgs[0], Ts[0], ref)
+    assert ref["image"].max() > 0.1  # not a blank scene
+
+
+def ragged_scene(n=3000, seed=11, L=3, K=2):
+    G = I.gaussians(n, seed, L, K)
+    views = [I.view((0.3, 0.2, 4.0), 77, 53, 0.31, bg=(0.1, 0.3, 0.2)),
+             I.view((-2.0, 1.0, 3.3), 40, 96, 0.55),
+             I.view((1.5, -0.5, -3.6), 130, 31, 0.8, bg=(1.0, 1.0, 1.0))]
+    return G, views
+
+
+def test_forward_ragged_multiview():
+    G, views = ragged_scene()
+    _, _, imgs, Ts = gpu_forward(G, views)
+    for v, img, T in zip(views, imgs, Ts):
+        ref = O.render(G, v)
+        assert_image_parity(img, T, ref)
+
+
+def test_forward_bf16_coefficients_are_exact_inputs():
+    """BF16 4DSH storage: the oracle on the same (rounded) coefficients matches to FP32 tolerance."""
+    G, views = ragged_scene(n=1500, seed=12)
+    shs16 = torch.as_tensor(G["shs"]).to(torch.bfloat16)
+    G16 = dict(G, shs=shs16.float().numpy())
+    _, _, imgs, Ts = gpu_forward(dict(G, shs=shs16), views, shs_dtype=torch.bfloat16)
+    for v, img, T in zip(views, imgs, Ts):
+        assert_image_parity(img, T, O.render(G16, v))
+
+
+def read_state(fr):
+    """Records, tile counts, ranges and the sorted lists, via fgs4d_state_layout."""
+    info = fr.layout()
+    st = fr.state
+    S = int(info.n_splats)
+    rb = int(info.record_bytes)
+    rec = st[info.records: info.records + S * rb].view(torch.float32).view(S, rb // 4).cpu().numpy()
+    tiles = st[info.tiles_touched: info.tiles_touched + 4 * S].view(torch.int32).cpu().numpy()
+    nt = int(info.total_tiles)
+    ranges = st[info.ranges: info.ranges + 8 * nt].view(torch.int32).view(nt, 2).cpu().numpy()
+    npairs = int(fr.last_counters.n_pairs)
+    vals = st[info.pair_vals: info.pair_vals + 4 * npairs].view(torch.int32).cpu().numpy()
+    return rec, tiles, ranges, vals
+
+
+def test_slice_project_records_match_oracle():
+    G, views = ragged_scene(n=2500, seed=13)
+    fr, _, _, _ = gpu_forward(G, views)
+    rec, tiles, _, _ = read_state(fr)
+    n = G["logit"].shape[0]
+    for vi, v in enumerate(views):
+        ref = O.project_all(G, v)
+        vis_g = tiles[vi * n:(vi + 1) * n] > 0
+        vis_o = ref["visible"] == 1
+        border = ref["borderline"] == 1
+        # GPU-visible but oracle-culled only for borderline decisions
+        assert np.all(border[vis_g & ~vis_o])
+        # oracle-visible but GPU-culled: borderline, or the support disk misses the image
+        miss = ((ref["u"] + ref["radius"] < -0.4) | (ref["u"] - ref["radius"] > v["width"] - 0.6) |
+                (ref["v"] + ref["radius"] < -0.4) | (ref["v"] - ref["radius"] > v["height"] - 0.6))
+        assert np.all((border | miss)[vis_o & ~vis_g])
+        both = vis_g & vis_o
+        assert both.sum() > 50
+        r = rec[vi * n:(vi + 1) * n][both]
+        def close(a, b, rtol, atol, what):
+            err = np.abs(a - b) / (np.abs(b) * rtol + atol)
+            assert err.max() <= 1.0, f"{what}: worst {err.max():.3g}"
+        close(r[:, 0], ref["u"][both], 1e-5, 1e-3, "u")
+        close(r[:, 1], ref["v"][both], 1e-5, 1e-3, "v")
+        conic = ref["conic"][both]
+        scale = np.abs(conic).max(axis=1)
+        for k, col in enumerate((2, 3, 4)):
+            close(r[:, col], conic[:, k], 1e-4, 1e-4 * scale, f"conic{k}")
+        close(r[:, 5], ref["alpha_eff"][both], 1e-5, 1e-7, "alpha_eff")
+        col = ref["color"][both]
+        for ch, c in enumerate((6, 7, 8)):
+            close(r[:, c], col[:, ch], 1e-5, 1e-5, f"color{ch}")
+        close(r[:, 9], ref["depth"][both], 1e-6, 1e-6, "depth")
+
+
+def test_tile_lists_are_depth_ordered_and_complete():
+    G, views = ragged_scene(n=2500, seed=14)
+    fr, _, _, _ = gpu_forward(G, views)
+    rec, tiles, ranges, vals = read_state(fr)
+    n = G["logit"].shape[0]
+    tile_base = 0
+    expect = {}
+    for vi, v in enumerate(views):
+        tx_n = (v["width"] + 15) // 16
+        for g in np.nonzero(tiles[vi * n:(vi + 1) * n])[0]:
+            sid = vi * n + g
+            u, vv, rad = rec[sid, 0], rec[sid, 1], rec[sid, 10]
+            x0 = max(math.ceil(u - rad), 0) // 16
+            x1 = min(math.floor(u + rad), v["width"] - 1) // 16
+            y0 = max(math.ceil(vv - rad), 0) // 16
+            y1 = min(math.floor(vv + rad), v["height"] - 1) // 16
+            assert (x1 - x0 + 1) * (y1 - y0 + 1) == tiles[sid]
+            for ty in range(y0, y1 + 1):
+                for tx in range(x0, x1 + 1):
+                    expect.setdefault(tile_base + ty * tx_n + tx, []).append(sid)
+        tile_base += tx_n * ((v["height"] + 15) // 16)
+    assert tile_base == ranges.shape[0]
+    for t in range(ranges.shape[0]):
+        s, e = ranges[t]
+        got = list(vals[s:e]) if e > s else []
+        want = sorted(expect.get(t, []), key=lambda sid: (rec[sid, 9], sid))
+        assert got == want, f"tile {t}"
+
+
+def test_batched_equals_one_by_one():
+    G, views = ragged_scene(n=2000, seed=15)
+    _, _, imgs, Ts = gpu_forward(G, views)
+    for v, img, T in zip(views, imgs, Ts):
+        _, _, im1, T1 = gpu_forward(G, [v])
+        np.testing.assert_array_equal(img, im1[0])
+        np.testing.assert_array_equal(T, T1[0])
+
+
+def test_fp64_fallback_for_ill_conditioned_slices():
+    """Gaussians stretched along a space-time diagonal: Sigma_{xyz|t} is a tiny
+    difference of large numbers (Eq. 9); the GPU recomputes it in FP64."""
+    n = 400
+    r = np.random.default_rng(3)
+    th = r.uniform(0.6, 1.0, size=n)  # rotation in the x-t plane
+    q = np.stack([np.cos(th / 2), np.zeros(n), np.zeros(n), np.sin(th / 2)]).astype(np.float32)
+    G = I.gaussians(n, 99, 1, 1)
+    G["ql"], G["qr"] = q.copy(), q.copy()
+    G["log_s"][0] = -1.0  # long axis (mixes x and t)
+    G["log_s"][3] = -7.5  # very thin across it
+    G["mu"][3] = 0.5
+    views = [I.view((0.0, 0.0, 4.0), 96, 96, 0.5)]
+    fr, _, imgs, Ts = gpu_forward(G, views)
+    ref = O.render(G, views[0])
+    assert_image_parity(imgs[0], Ts[0], ref)
+
+
+# ---------------------------------------------------------------------------- edge cases
+def test_edge_cases_empty_culled_tiny():
+    from paper_2310_10642_gb300 import native as N
+    # no Gaussians at all
+    G = I.gaussians(0, 1, 1, 1)
+    v = I.view((0, 0, 4), 33, 17, 0.5, bg=(0.2, 0.4, 0.6))
+    fr, _, imgs, Ts = gpu_forward(G, [v])
+    assert np.allclose(imgs[0], np.array([0.2, 0.4, 0.6])[:, None, None]) and np.all(Ts[0] == 1.0)
+    # every Gaussian culled by the temporal filter
+    G = I.gaussians(500, 2, 1, 1)
+    G["mu"][3] += 50.0
+    fr, _, imgs, _ = gpu_forward(G, [v])
+    assert fr.last_counters.n_visible == 0 and np.allclose(imgs[0], np.array([0.2, 0.4, 0.6])[:, None, None])
+    # 1x1 image and a one-tile image
+    G = I.gaussians(800, 3, 2, 1)
+    for w, h in ((1, 1), (16, 16), (17, 1)):
+        vv = I.view((0.1, 0.2, 4.0), w, h, 0.5)
+        _, _, imgs, Ts = gpu_forward(G, [vv])
+        assert_image_parity(imgs[0], Ts[0], O.render(G, vv), max_flag_frac=1.0)
+
+
+def test_pair_capacity_overflow_is_reported_not_faulted():
+    from paper_2310_10642_gb300 import native as N
+    from paper_2310_10642_gb300 import render as R
+    c = I.config(0)
+    p = R.params_to_device(c["gaussians"])
+    fr = R.Frame(2000, c["views"], pair_capacity=16)
+    fr.forward(p, check=False)
+    cnt = fr.counters()
+    assert cnt.status & N.STATUS_PAIR_OVERFLOW and cnt.n_pairs > 16
+    fr.forward(p, check=True)  # grows and re-runs
+    assert not (fr.last_counters.status & N.STATUS_PAIR_OVERFLOW)
+
+
+def test_nonfinite_and_zero_quaternion_are_flagged():
+    from paper_2310_10642_gb300 import native as N
+    G = I.gaussians(300, 4, 1, 1)
+    G["mu"][0, 5] = np.nan
+    G["ql"][:, 7] = 0.0
+    v = I.view((0, 0, 4), 64, 64, 0.5)
+    fr, _, imgs, _ = gpu_forward(G, [v])
+    assert fr.last_counters.status & N.STATUS_NONFINITE
+    assert np.all(np.isfinite(imgs[0]))
+
+
+# ---------------------------------------------------------------------------- backward
+def grads_gpu(fr, p, dL_list):
+    dL = torch.cat([torch.as_tensor(d, dtype=torch.float32).reshape(-1) for d in dL_list]).cuda()
+    g = fr.backward(p, dL)
+    torch.cuda.synchronize()
+    return {k: v.double().cpu().numpy() for k, v in g.items()}
+
+
+def assert_grad_parity(gg, go, tol=GRAD_TOL):
+    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
+        a, b = gg[k], go[k]
+        nb = np.linalg.norm(b)
+        assert nb > 0, k
+        rel = np.linalg.norm(a - b) / nb
+        assert rel <= tol, f"{k}: relative error {rel:.3e}"
+
+
+def masked_dL(views, refs, seed):
+    r = np.random.default_rng(seed)
+    out = []
+    for v, ref in zip(views, refs):
+        d = r.normal(size=(3, v["height"], v["width"]))
+        d[:, ref["flags"] != 0] = 0.0
+        out.append(d)
+    return out
+
+
+def test_backward_matches_oracle():
+    G, views = ragged_scene(n=1500, seed=21)
+    fr, p, _, _ = gpu_forward(G, views)
+    refs = [O.render(G, v) for v in views]
+    dL = masked_dL(views, refs, 5)
+    gg = grads_gpu(fr, p, dL)
+    go = O.backward_views(G, views, dL)
+    assert_grad_parity(gg, go)
+
+
+def test_backward_config0():
+    c = I.config(0)
+    G, views = c["gaussians"], c["views"]
+    fr, p, _, _ = gpu_forward(G, views)
+    refs = [O.render(G, v) for v in views]
+    dL = masked_dL(views, refs, 6)
+    assert_grad_parity(grads_gpu(fr, p, dL), O.backward_views(G, views, dL))
+
+
+def test_backward_central_differences():
+    """GPU gradient vs central differences of the GPU forward on 64 random
+    parameters whose stencil changes no discrete decision (checked on the
+    oracle's per-pixel contributor counts)."""
+    G, views = ragged_scene(n=600, seed=31, L=2, K=1)
+    G["log_s"][:3] += 0.7
+    views = views[:2]
+    fr, p, _, _ = gpu_forward(G, views)
+    refs = [O.render(G, v) for v in views]
+    dL = masked_dL(views, refs, 7)
+    gg = grads_gpu(fr, p, dL)
+    w = [torch.as_tensor(d) for d in dL]
+
+    def loss(Gx):
+        _, _, imgs, _ = gpu_forward(Gx, views)
+        return sum(float((torch.as_tensor(im) * wi).sum()) for im, wi in zip(imgs, w))
+
+    rng = np.random.default_rng(8)
+    checked, tried = 0, 0
+    keys = ("mu", "log_s", "ql", "qr", "logit", "shs")
+    while checked < 64 and tried < 400:
+        tried += 1
+        key = keys[tried % len(keys)]
+        arr = G[key]
+        idx = tuple(int(rng.integers(0, s)) for s in arr.shape)
+        gi = idx[-1]
+        if abs(gg[key][idx]) < 1e-2:
+            continue  # too small to resolve against FP32 rendering noise
+        x0 = float(arr[idx])
+        h = 2e-3 * max(1.0, abs(x0))
+        Gp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G.items()}
+        Gm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G.items()}
+        Gp[key][idx] = x0 + h
+        Gm[key][idx] = x0 - h
+        # same discrete decisions on both sides of the stencil (oracle, FP64)
+        same = True
+        for v, ref in zip(views, refs):
+            a, b = O.render(Gp, v), O.render(Gm, v)
+            if not (np.array_equal(a["n_contrib"], ref["n_contrib"]) and np.array_equal(b["n_contrib"], ref["n_contrib"])):
+                same = False
+                break
+        if not same:
+            continue
+        h_eff = (np.float32(x0 + h) - np.float32(x0 - h))
+        fd = (loss(Gp) - loss(Gm)) / float(h_eff)
+        an = gg[key][idx]
+        # FP32 rendering noise over the few hundred pixels a stencil changes is ~1e-6 in the
+        # loss, i.e. ~1e-3 after division by 2h; the relative bar applies above that floor
+        assert abs(fd - an) <= GRAD_TOL * abs(an) + 2e-3, (key, idx, an, fd)
+        checked += 1
+    assert checked >= 32
+
+
+def test_autograd_function_l1_loss():
+    from paper_2310_10642_gb300 import render as R
+    G, views = ragged_scene(n=1200, seed=41, L=1, K=1)
+    p = R.params_to_device(G)
+    leaves = {k: p[k].clone().requires_grad_(True) for k in R.PARAM_KEYS}
+    params = dict(leaves, sh_degree=p["sh_degree"], n_freq=p["n_freq"], period=p["period"])
+    imgs, fr = R.render(params, views)
+    targets = [torch.as_tensor(t).cuda() for t in I.random_target(views, 77)]
+    loss = sum((im - t).abs().mean() for im, t in zip(imgs, targets))
+    loss.backward()
+    # same gradient through the oracle: dL/dimage = sign(im - t) / numel
+    refs = [O.render(G, v) for v in views]
+    dL = [np.sign(im.detach().cpu().numpy() - t.cpu().numpy()) / im.numel() for im, t in zip(imgs, targets)]
+    for d, ref in zip(dL, refs):
+        assert (ref["flags"] != 0).mean() < 0.02
+    go = O.backward_views(G, views, dL)
+    gg = {k: leaves[k].grad.double().cpu().numpy() for k in R.PARAM_KEYS}
+    # flagged pixels are not masked here (the loss is fixed); allow their share
+    for k in R.PARAM_KEYS:
+        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
+        assert rel < 2e-2, (k, rel)
