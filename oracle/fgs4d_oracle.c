@@ -42,7 +42,9 @@
  * threshold, where a single-precision evaluation may legitimately decide the
  * other way: bit 0 = the image value may differ (alpha_min skip, early
  * termination, depth order, a borderline Gaussian-level cull), bit 1 = only
- * the gradient may differ (alpha_max clamp, colour clamp, J clamp).
+ * the gradient may differ (alpha_max clamp, colour clamp, depth near-tie).  Bits 2..5 name
+ * the cause of bit 0: depth order, early termination, alpha_min skip,
+ * Gaussian-level cull.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -55,7 +57,7 @@
 /* relative margins used only for pixel flags (see header comment) */
 #define ORC_ETA_ALPHA 1e-4
 #define ORC_ETA_T 2e-3
-#define ORC_ETA_DEPTH 2e-5
+#define ORC_ETA_DEPTH 2e-6
 #define ORC_ETA_P 1e-4
 #define ORC_ETA_NEAR 1e-4
 
@@ -439,12 +441,15 @@ typedef struct {
    returns the number of contributors; writes colour, final T and flags. */
 static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const orc_options *O,
                       const orc_view *V, double px, double py, int prefilter, double *C, double *T_out,
-                      uint8_t *flag, contrib *list) {
+                      uint8_t *flag, contrib *list, uint64_t *hash) {
     double T = 1.0;
+    uint64_t hsh = 1469598103934665603ull; /* order-sensitive hash of the contributor sequence */
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0;
     uint8_t f = 0;
-    double last_rel_depth = -1.0;
+    /* previous relevant splat, for the depth-order check */
+    double last_rel_depth = -1.0, last_alpha = 0.0;
+    const double *last_color = NULL;
     for (int64_t k = 0; k < m; k++) {
         const orc_splat *s = &S[order[k]];
         const double dx = px - s->u, dy = py - s->v;
@@ -457,10 +462,20 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
         const double araw = s->alpha_eff * Gexp;
         const int relevant = araw >= O->alpha_min * (1.0 - ORC_ETA_ALPHA);
         if (relevant) {
-            if (s->borderline) f |= 1;
-            if (fabs(araw - O->alpha_min) <= ORC_ETA_ALPHA * O->alpha_min) f |= 1;
-            if (last_rel_depth >= 0.0 && fabs(s->depth - last_rel_depth) <= ORC_ETA_DEPTH * s->depth) f |= 1;
+            if (s->borderline) f |= 1 | 32;
+            if (fabs(araw - O->alpha_min) <= ORC_ETA_ALPHA * O->alpha_min) f |= 1 | 16;
+            const double a_cl = araw < O->alpha_max ? araw : O->alpha_max;
+            if (last_rel_depth >= 0.0 && fabs(s->depth - last_rel_depth) <= ORC_ETA_DEPTH * s->depth) {
+                /* swapping two blended splats changes the pixel by at most
+                   T a_1 a_2 max|c_1 - c_2|; below 1e-5 the image cannot tell */
+                double dc = 0.0;
+                for (int ch = 0; ch < 3; ch++) dc = fmax(dc, fabs(s->color[ch] - last_color[ch]));
+                f |= 2;
+                if (T * a_cl * last_alpha * dc > 1e-5) f |= 1 | 4;
+            }
             last_rel_depth = s->depth;
+            last_alpha = a_cl;
+            last_color = s->color;
         }
         if (!s->visible) continue; /* borderline-culled: flags only */
         if (power > 0.0) continue;  /* R6 */
@@ -468,7 +483,7 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
         if (alpha < O->alpha_min) continue;
         if (fabs(araw - O->alpha_max) <= ORC_ETA_ALPHA * O->alpha_max) f |= 2;
         const double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - O->T_min) <= ORC_ETA_T * O->T_min) f |= 1;
+        if (fabs(Tn - O->T_min) <= ORC_ETA_T * O->T_min) f |= 1 | 8;
         if (Tn < O->T_min) break;  /* R5 */
         for (int ch = 0; ch < 3; ch++) {
             C[ch] += s->color[ch] * alpha * T;
@@ -480,19 +495,22 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
             c->dx = dx; c->dy = dy; c->clamped = araw > O->alpha_max;
         }
         nc++;
+        hsh = hsh * 1099511628211ull + (uint64_t)(order[k] + 1);
         T = Tn;
     }
     for (int ch = 0; ch < 3; ch++) C[ch] += T * V->bg[ch];
     *T_out = T;
     if (flag) *flag = f;
+    if (hash) *hash = hsh;
     return nc;
 }
 
 /* Renders the window [x0, x0+w) x [y0, y0+h) of the view.  image is [3][h][w].
-   Returns the number of visible splats. */
+   seq_hash (optional) receives an order-sensitive hash of each pixel's
+   contributor sequence.  Returns the number of visible splats. */
 ORC_API int64_t orc_render(const orc_gaussians *G, const orc_view *V, const orc_options *O, int x0, int y0,
                            int w, int h, int prefilter, double *image, double *T_final, int32_t *n_contrib,
-                           uint8_t *flags, orc_splat *splats_out) {
+                           uint8_t *flags, orc_splat *splats_out, uint64_t *seq_hash) {
     orc_splat *S = (orc_splat *)malloc(sizeof(orc_splat) * (G->n > 0 ? G->n : 1));
     int64_t *order;
     int64_t m = sorted_candidates(G, V, O, S, &order);
@@ -502,7 +520,10 @@ ORC_API int64_t orc_render(const orc_gaussians *G, const orc_view *V, const orc_
         for (int x = 0; x < w; x++) {
             double C[3], T;
             uint8_t f;
-            int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, &f, NULL);
+            uint64_t hsh;
+            int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, &f, NULL,
+                                &hsh);
+            if (seq_hash) seq_hash[(int64_t)y * w + x] = hsh;
             for (int ch = 0; ch < 3; ch++) image[((int64_t)ch * h + y) * w + x] = C[ch];
             if (T_final) T_final[(int64_t)y * w + x] = T;
             if (n_contrib) n_contrib[(int64_t)y * w + x] = nc;
@@ -737,7 +758,8 @@ ORC_API void orc_backward(const orc_gaussians *G, const orc_view *V, const orc_o
     for (int y = 0; y < h; y++)
         for (int x = 0; x < w; x++) {
             double C[3], T;
-            int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, NULL, list);
+            int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, NULL, list,
+                                NULL);
             double dC[3];
             for (int ch = 0; ch < 3; ch++) dC[ch] = dL_dimage[((int64_t)ch * h + y) * w + x];
             /* acc = sum_{j>i} c_j alpha_j T_j + T_final bg, built back to front */

@@ -131,7 +131,7 @@ fgs4d_status make_layout(int64_t n, const ViewSet& VS, int64_t capacity, size_t 
     L->sort_vals[1] = take(s * 4);
     L->offsets = take(s * 4);
     L->scan_tmp = take((kScanBlocksMax + 32) * 4);
-    L->hist = take((256 * kSortBlocksMax + 256) * 4);
+    L->hist = take(((size_t)kMaxDigits * kSortBlocksMax + kMaxDigits) * 4);
     L->ranges = take((size_t)VS.total_tiles * 8);
     L->grad2d = take(s * 48);
     L->fixed_bytes = off;
@@ -299,8 +299,7 @@ fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view* views, int n_views, con
 
 static int pair_buffer(const Prepared& P) {
     if (P.L.capacity == 0) return 0;
-    const int bits = pair_sort_bits(P.VS.total_tiles + 1);
-    return ((bits + 7) / 8) & 1;
+    return radix_passes(pair_sort_bits(P.VS.total_tiles + 1)) & 1;
 }
 
 fgs4d_status fgs4d_render(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,

@@ -164,13 +164,20 @@ static cudaError_t device_scan(Load ld, Store stv, const uint32_t* d_n, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort of (uint32 key, uint32 value), 8-bit digits.
+// Stable LSD radix sort of (uint32 key, uint32 value) with RB-bit digits
+// (RB = 8 or 9, chosen per sort so that the passes cover the key bits with
+// as few passes as possible).  Per pass: upsweep (per-block digit counts),
+// scan (one block per digit over the blocks), downsweep (stable rank within
+// each block tile by warp match_any, reorder in shared memory, write out).
 // ---------------------------------------------------------------------------
+template <int RB>
 __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys, const uint32_t* d_n,
                                                                  uint32_t n_max, int shift, uint32_t* hist) {
-    __shared__ uint32_t s_h[kThreads / 32][256];
+    constexpr uint32_t D = 1u << RB, DPT = D / kThreads;
+    __shared__ uint32_t s_h[kThreads / 32][D];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int w = 0; w < kThreads / 32; w++) s_h[w][tid] = 0u;
+    for (int w = 0; w < kThreads / 32; w++)
+        for (uint32_t k = 0; k < DPT; k++) s_h[w][tid * DPT + k] = 0u;
     __syncthreads();
     const uint32_t n = device_count(d_n, n_max);
     uint32_t begin, end;
@@ -178,14 +185,17 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const uint32_t*
     // warp-strided so that every iteration is warp-uniform (needed by match_any)
     for (uint32_t base = begin + wid * 32; base < end; base += kThreads) {
         const uint32_t i = base + lane;
-        const uint32_t d = i < end ? (keys[i] >> shift) & 255u : 256u;
+        const uint32_t d = i < end ? (keys[i] >> shift) & (D - 1) : D;
         const uint32_t peers = __match_any_sync(kFull, d);
-        if (d < 256u && lane == __ffs(peers) - 1) s_h[wid][d] += __popc(peers);
+        if (d < D && lane == __ffs(peers) - 1) s_h[wid][d] += __popc(peers);
     }
     __syncthreads();
-    uint32_t sum = 0;
-    for (int w = 0; w < kThreads / 32; w++) sum += s_h[w][tid];
-    hist[tid * gridDim.x + blockIdx.x] = sum;
+    for (uint32_t k = 0; k < DPT; k++) {
+        const uint32_t d = tid * DPT + k;
+        uint32_t sum = 0;
+        for (int w = 0; w < kThreads / 32; w++) sum += s_h[w][d];
+        hist[d * gridDim.x + blockIdx.x] = sum;
+    }
 }
 
 // One block per digit: exclusive scan over the blocks, digit totals.
@@ -204,13 +214,15 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, int G,
     if (threadIdx.x == 0) digit_total[d] = running;
 }
 
+template <int RB>
 __global__ void __launch_bounds__(kThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const uint32_t* d_n, uint32_t n_max, int shift, const uint32_t* __restrict__ hist,
     const uint32_t* __restrict__ digit_total) {
-    __shared__ uint32_t s_global[256];
-    __shared__ uint32_t s_tile_start[256];
-    __shared__ uint32_t s_wcnt[kThreads / 32][256];
+    constexpr uint32_t D = 1u << RB, DPT = D / kThreads;
+    __shared__ uint32_t s_global[D];
+    __shared__ uint32_t s_tile_start[D];
+    __shared__ uint32_t s_wcnt[kThreads / 32][D];
     __shared__ uint32_t s_keys[kTileItems];
     __shared__ uint32_t s_vals[kTileItems];
     __shared__ uint32_t s_warp[32];
@@ -219,12 +231,25 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep_kernel(
     uint32_t begin, end;
     block_chunk(n, gridDim.x, begin, end);
     if (begin >= end) return;  // uniform across the block
-    uint32_t tot;
-    const uint32_t dstart = block_exclusive_scan(digit_total[tid], s_warp, tot);
-    s_global[tid] = dstart + hist[tid * gridDim.x + blockIdx.x];
+    {
+        // this thread owns digits tid*DPT .. tid*DPT + DPT - 1
+        uint32_t own[DPT], sum = 0;
+        for (uint32_t k = 0; k < DPT; k++) {
+            own[k] = digit_total[tid * DPT + k];
+            sum += own[k];
+        }
+        uint32_t tot;
+        uint32_t start = block_exclusive_scan(sum, s_warp, tot);
+        for (uint32_t k = 0; k < DPT; k++) {
+            const uint32_t d = tid * DPT + k;
+            s_global[d] = start + hist[d * gridDim.x + blockIdx.x];
+            start += own[k];
+        }
+    }
     const uint32_t lt = lanemask_lt();
     for (uint32_t tile = begin; tile < end; tile += kTileItems) {
-        for (int w = 0; w < kThreads / 32; w++) s_wcnt[w][tid] = 0u;
+        for (int w = 0; w < kThreads / 32; w++)
+            for (uint32_t k = 0; k < DPT; k++) s_wcnt[w][tid * DPT + k] = 0u;
         __syncthreads();
         uint32_t k[kItems], val[kItems], dig[kItems], rank[kItems];
 #pragma unroll
@@ -233,32 +258,40 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep_kernel(
             const bool valid = idx < end;
             k[i] = valid ? keys_in[idx] : 0u;
             val[i] = valid ? vals_in[idx] : 0u;
-            dig[i] = valid ? (k[i] >> shift) & 255u : 256u;
+            dig[i] = valid ? (k[i] >> shift) & (D - 1) : D;
         }
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
             const uint32_t peers = __match_any_sync(kFull, dig[i]);
-            const uint32_t base = dig[i] < 256u ? s_wcnt[wid][dig[i]] : 0u;
+            const uint32_t base = dig[i] < D ? s_wcnt[wid][dig[i]] : 0u;
             __syncwarp();
-            if (dig[i] < 256u && lane == __ffs(peers) - 1) s_wcnt[wid][dig[i]] = base + __popc(peers);
+            if (dig[i] < D && lane == __ffs(peers) - 1) s_wcnt[wid][dig[i]] = base + __popc(peers);
             __syncwarp();
             rank[i] = base + __popc(peers & lt);
         }
         __syncthreads();
-        uint32_t run = 0;
-        for (int w = 0; w < kThreads / 32; w++) {
-            const uint32_t c = s_wcnt[w][tid];
-            s_wcnt[w][tid] = run;
-            run += c;
+        uint32_t tile_cnt[DPT], sum = 0;
+        for (uint32_t kk = 0; kk < DPT; kk++) {
+            const uint32_t d = tid * DPT + kk;
+            uint32_t run = 0;
+            for (int w = 0; w < kThreads / 32; w++) {
+                const uint32_t c = s_wcnt[w][d];
+                s_wcnt[w][d] = run;
+                run += c;
+            }
+            tile_cnt[kk] = run;
+            sum += run;
         }
-        const uint32_t tile_cnt = run;
         uint32_t tile_total;
-        const uint32_t ts = block_exclusive_scan(tile_cnt, s_warp, tile_total);
-        s_tile_start[tid] = ts;
+        uint32_t ts = block_exclusive_scan(sum, s_warp, tile_total);
+        for (uint32_t kk = 0; kk < DPT; kk++) {
+            s_tile_start[tid * DPT + kk] = ts;
+            ts += tile_cnt[kk];
+        }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kItems; i++) {
-            if (dig[i] < 256u) {
+            if (dig[i] < D) {
                 const uint32_t pos = s_tile_start[dig[i]] + s_wcnt[wid][dig[i]] + rank[i];
                 s_keys[pos] = k[i];
                 s_vals[pos] = val[i];
@@ -268,26 +301,49 @@ __global__ void __launch_bounds__(kThreads) radix_downsweep_kernel(
         const uint32_t tile_n = min((uint32_t)kTileItems, end - tile);
         for (uint32_t j = tid; j < tile_n; j += kThreads) {
             const uint32_t kk = s_keys[j];
-            const uint32_t d = (kk >> shift) & 255u;
+            const uint32_t d = (kk >> shift) & (D - 1);
             const uint32_t out = s_global[d] + (j - s_tile_start[d]);
             keys_out[out] = kk;
             vals_out[out] = s_vals[j];
         }
         __syncthreads();
-        s_global[tid] += tile_cnt;
+        for (uint32_t kk = 0; kk < DPT; kk++) s_global[tid * DPT + kk] += tile_cnt[kk];
         __syncthreads();
     }
+}
+
+// Number of passes and digit width for a sort over `bits` key bits.
+static void radix_plan(int bits, int& passes, int& rb) {
+    passes = (bits + 8) / 9;  // ceil(bits / 9)
+    if (passes < 1) passes = 1;
+    rb = ((bits + passes - 1) / passes) > 8 ? 9 : 8;
+}
+
+int radix_passes(int bits) {
+    int p, rb;
+    radix_plan(bits, p, rb);
+    return p;
 }
 
 // Sorts keys[0]/vals[0] over `bits` low key bits; result in buffer (passes % 2).
 static cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], const uint32_t* d_n, uint32_t n_max, int bits,
                               uint32_t* hist, uint32_t* digit_total, int G, cudaStream_t st, int* out_buf) {
+    int passes, rb;
+    radix_plan(bits, passes, rb);
     int cur = 0;
-    for (int shift = 0; shift < bits; shift += 8) {
-        radix_upsweep_kernel<<<G, kThreads, 0, st>>>(keys[cur], d_n, n_max, shift, hist);
-        radix_scan_kernel<<<256, 1024, 0, st>>>(hist, G, digit_total);
-        radix_downsweep_kernel<<<G, kThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, n_max,
-                                                        shift, hist, digit_total);
+    for (int pass = 0; pass < passes; pass++) {
+        const int shift = pass * rb;
+        if (rb == 9) {
+            radix_upsweep_kernel<9><<<G, kThreads, 0, st>>>(keys[cur], d_n, n_max, shift, hist);
+            radix_scan_kernel<<<512, 1024, 0, st>>>(hist, G, digit_total);
+            radix_downsweep_kernel<9><<<G, kThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n,
+                                                              n_max, shift, hist, digit_total);
+        } else {
+            radix_upsweep_kernel<8><<<G, kThreads, 0, st>>>(keys[cur], d_n, n_max, shift, hist);
+            radix_scan_kernel<<<256, 1024, 0, st>>>(hist, G, digit_total);
+            radix_downsweep_kernel<8><<<G, kThreads, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n,
+                                                              n_max, shift, hist, digit_total);
+        }
         cur ^= 1;
         count_launches(3);
     }
@@ -298,45 +354,11 @@ static cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], const uint32
 // ---------------------------------------------------------------------------
 // Pair emission and tile ranges
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void emit_one(const ViewSet& VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted_splats,
-                                         const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tiles,
-                                         const SplatRecord* __restrict__ rec,
-                                         uint32_t* counters, uint32_t capacity, uint32_t* __restrict__ pair_keys,
-                                         uint32_t* __restrict__ pair_vals, uint32_t p) {
-    const uint32_t sid = sorted_splats[p];
-    const uint32_t v = sid / n_gauss;
-    const DevView& V = VS.v[v];
-    const float4 r0 = rec[sid].r0;
-    const float radius = rec[sid].r2.z;
-    const float fx0 = fmaxf(ceilf(r0.x - radius), 0.0f);
-    const float fx1 = fminf(floorf(r0.x + radius), (float)(V.width - 1));
-    const float fy0 = fmaxf(ceilf(r0.y - radius), 0.0f);
-    const float fy1 = fminf(floorf(r0.y + radius), (float)(V.height - 1));
-    const int x0 = (int)fx0 / kTile, x1 = (int)fx1 / kTile, y0 = (int)fy0 / kTile, y1 = (int)fy1 / kTile;
-    // Exactly tiles[sid] pairs are written (the count the offsets were built
-    // from); should the rect ever disagree, surplus slots go to the dump tile
-    // id VS.total_tiles, which no CTA renders.
-    const uint32_t cnt = tiles[sid];
-    const int wx = x1 - x0 + 1;
-    const uint32_t cnt_rect = (uint32_t)(wx * (y1 - y0 + 1));
-    uint32_t o = offsets[p];
-    bool overflow = false;
-    for (uint32_t k = 0; k < cnt; k++, o++) {
-        if (o >= capacity) {
-            overflow = true;
-            break;
-        }
-        uint32_t key = VS.total_tiles;
-        if (k < cnt_rect) {
-            const int ty = y0 + (int)k / wx, tx = x0 + (int)k % wx;
-            key = V.tile_base + (uint32_t)(ty * V.tiles_x + tx);
-        }
-        pair_keys[o] = key;
-        pair_vals[o] = sid;
-    }
-    if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
-}
-
+// Warp-cooperative emission: the 32 lanes take 32 consecutive depth-sorted
+// splats, then write each splat's pairs together so that stores to the pair
+// arrays are contiguous.  Exactly tiles[sid] pairs are written per splat (the
+// count the offsets were built from); should the rect ever disagree, surplus
+// slots get the dump tile id VS.total_tiles, which no CTA renders.
 __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__ ViewSet VS, uint32_t n_gauss,
                                                          const uint32_t* __restrict__ sorted_splats,
                                                          const uint32_t* __restrict__ offsets,
@@ -346,10 +368,62 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
                                                          uint32_t* __restrict__ pair_keys,
                                                          uint32_t* __restrict__ pair_vals) {
     const uint32_t n_vis = min(counters[0], n_max);
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_vis; p += gridDim.x * blockDim.x)
-        emit_one(VS, n_gauss, sorted_splats, offsets, tiles, rec, counters, capacity, pair_keys, pair_vals, p);
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
+    bool overflow = false;
+    for (uint32_t base = warp0 * 32; base < n_vis; base += n_warps * 32) {
+        const uint32_t p = base + lane;
+        uint32_t sid = 0, o = 0, cnt = 0, x0 = 0, y0 = 0, wx = 1, cnt_rect = 0, tbase = 0, tiles_x = 1;
+        if (p < n_vis) {
+            sid = sorted_splats[p];
+            const uint32_t v = sid / n_gauss;
+            const DevView& V = VS.v[v];
+            const float4 r0 = rec[sid].r0;
+            const float radius = rec[sid].r2.z;
+            const float fx0 = fmaxf(ceilf(r0.x - radius), 0.0f);
+            const float fx1 = fminf(floorf(r0.x + radius), (float)(V.width - 1));
+            const float fy0 = fmaxf(ceilf(r0.y - radius), 0.0f);
+            const float fy1 = fminf(floorf(r0.y + radius), (float)(V.height - 1));
+            const int ix0 = (int)fx0 / kTile, ix1 = (int)fx1 / kTile, iy0 = (int)fy0 / kTile, iy1 = (int)fy1 / kTile;
+            x0 = (uint32_t)ix0;
+            y0 = (uint32_t)iy0;
+            wx = (uint32_t)max(ix1 - ix0 + 1, 1);
+            cnt_rect = (ix1 >= ix0 && iy1 >= iy0) ? wx * (uint32_t)(iy1 - iy0 + 1) : 0u;
+            tbase = V.tile_base;
+            tiles_x = (uint32_t)V.tiles_x;
+            o = offsets[p];
+            cnt = tiles[sid];
+        }
+        for (int s = 0; s < 32; s++) {
+            const uint32_t s_cnt = __shfl_sync(0xffffffffu, cnt, s);
+            if (s_cnt == 0) continue;
+            const uint32_t s_sid = __shfl_sync(0xffffffffu, sid, s);
+            const uint32_t s_o = __shfl_sync(0xffffffffu, o, s);
+            const uint32_t s_x0 = __shfl_sync(0xffffffffu, x0, s);
+            const uint32_t s_y0 = __shfl_sync(0xffffffffu, y0, s);
+            const uint32_t s_wx = __shfl_sync(0xffffffffu, wx, s);
+            const uint32_t s_cr = __shfl_sync(0xffffffffu, cnt_rect, s);
+            const uint32_t s_tb = __shfl_sync(0xffffffffu, tbase, s);
+            const uint32_t s_tx = __shfl_sync(0xffffffffu, tiles_x, s);
+            for (uint32_t k = lane; k < s_cnt; k += 32) {
+                const uint32_t at = s_o + k;
+                if (at >= capacity) {
+                    overflow = true;
+                    break;
+                }
+                uint32_t key = VS.total_tiles;
+                if (k < s_cr) {
+                    const uint32_t ty = s_y0 + k / s_wx, tx = s_x0 + k % s_wx;
+                    key = s_tb + ty * s_tx + tx;
+                }
+                pair_keys[at] = key;
+                pair_vals[at] = s_sid;
+            }
+        }
+    }
+    if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
 }
-
 
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* counters,
                                                           uint32_t capacity, uint32_t total_tiles,
@@ -385,7 +459,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     uint32_t* offsets = reinterpret_cast<uint32_t*>(state + lay.offsets);
     uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(state + lay.scan_tmp);
     uint32_t* hist = reinterpret_cast<uint32_t*>(state + lay.hist);
-    uint32_t* digit_total = hist + 256 * kSortBlocksMax;
+    uint32_t* digit_total = hist + kMaxDigits * kSortBlocksMax;
     uint2* ranges = reinterpret_cast<uint2*>(state + lay.ranges);
     uint32_t* pk[2] = {reinterpret_cast<uint32_t*>(state + lay.pair_keys[0]),
                        reinterpret_cast<uint32_t*>(state + lay.pair_keys[1])};

@@ -74,7 +74,7 @@ struct StateLayout {
     size_t sort_vals[2];   // uint32[V*n]
     size_t offsets;        // uint32[V*n] pair offsets per depth-sorted splat
     size_t scan_tmp;       // uint32[kScanBlocksMax + 32]
-    size_t hist;           // uint32[256 * kSortBlocksMax + 256]
+    size_t hist;           // uint32[kMaxDigits * kSortBlocksMax + kMaxDigits]
     size_t ranges;         // uint2[total_tiles]
     size_t grad2d;         // float4[3 * V*n] per-splat 2D gradient
     size_t pair_keys[2];   // uint32[capacity] double buffer
@@ -88,6 +88,7 @@ struct StateLayout {
 
 constexpr int kScanBlocksMax = 1024;
 constexpr int kSortBlocksMax = 1024;
+constexpr int kMaxDigits = 512;  // radix digits of at most 9 bits
 
 // Splat record (FP32): 48 bytes, three 16-byte vectors.
 //   r0 = (u, v, conic_a, conic_b)   r1 = (conic_c, alpha_eff, R, G)
@@ -499,6 +500,7 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
 
 // number of radix passes etc. needed by the host to know which buffer holds the result
 int pair_sort_bits(uint32_t total_tiles);
+int radix_passes(int bits);
 
 // Host-side count of kernel launches issued by this library (all threads).
 void count_launches(unsigned k);

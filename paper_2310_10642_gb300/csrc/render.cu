@@ -125,23 +125,43 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
+// Reduce-scatter of eight per-lane values over the warp with 4+2+1+1+1
+// shuffles: afterwards lane l holds the warp total of value (l >> 2) & 7.
+__device__ __forceinline__ float warp_reduce8(const float (&v)[8], int lane) {
+    const unsigned F = 0xffffffffu;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+    float a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; i++) a[i] = (h4 ? v[i + 4] : v[i]) + __shfl_xor_sync(F, h4 ? v[i] : v[i + 4], 16);
+#pragma unroll
+    for (int i = 0; i < 2; i++) b[i] = (h3 ? a[i + 2] : a[i]) + __shfl_xor_sync(F, h3 ? a[i] : a[i + 2], 8);
+    float c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(F, h2 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(F, c, 2);
+    c += __shfl_xor_sync(F, c, 1);
+    return c;
+}
+
+constexpr int kGradStride = 12;  // floats per staged splat in the shared gradient accumulator
+
 __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
     const __grid_constant__ ViewSet VS, const DevOpts O, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const SplatRecord* __restrict__ rec, uint32_t n_splats,
-    const float* __restrict__ final_T,
-    const int32_t* __restrict__ n_last, const float* __restrict__ dL_dimage, float4* __restrict__ grad2d) {
+    const float* __restrict__ final_T, const int32_t* __restrict__ n_last, const float* __restrict__ dL_dimage,
+    float4* __restrict__ grad2d) {
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
-    __shared__ float s_c[kTilePix];
+    __shared__ float4 s_n[kTilePix];  // natural conic (a, b, c) and B
     __shared__ uint32_t s_sid[kTilePix];
+    __shared__ __align__(16) float s_g[kTilePix * kGradStride];
     __shared__ int s_max;
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
     const DevView& V = VS.v[v];
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
+    const int px = tx * kTile + (tid & (kTile - 1));
+    const int py = ty * kTile + (tid / kTile);
     const bool inside = px < V.width && py < V.height;
     const uint2 range = ranges[tile];
     const float fpx = (float)px, fpy = (float)py;
@@ -159,26 +179,31 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
     }
     // acc = sum_{j > i} c_j alpha_j T_j + T_final bg, built back to front
     float acc0 = T * V.bg[0], acc1 = T * V.bg[1], acc2 = T * V.bg[2];
-    if (threadIdx.x == 0) s_max = 0;
+    if (tid == 0) s_max = 0;
+#pragma unroll
+    for (int k = 0; k < kGradStride; k++) s_g[tid * kGradStride + k] = 0.0f;
     __syncthreads();
     atomicMax(&s_max, last);
     __syncthreads();
     const int max_last = min(s_max, (int)(range.y - range.x));
     for (int end = max_last; end > 0; end -= kTilePix) {
-        const int start = max(0, end - kTilePix);
-        const int cnt = end - start;
+        const int cnt = min(end, kTilePix);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) {
-            const uint32_t idx = range.x + (uint32_t)(end - 1 - (int)threadIdx.x);
+        if (tid < cnt) {
+            const uint32_t idx = range.x + (uint32_t)(end - 1 - tid);
             uint32_t sid = pair_vals[idx];
             if (sid >= n_splats) sid = 0;  // never produced by bin_sort; keeps the access in bounds
-            stage_record(rec[sid], s_a[threadIdx.x], s_b[threadIdx.x], s_c[threadIdx.x]);
-            s_sid[threadIdx.x] = sid;
+            const SplatRecord r = rec[sid];
+            float sc;
+            stage_record(r, s_a[tid], s_b[tid], sc);
+            s_n[tid] = make_float4(r.r0.z, r.r0.w, r.r1.x, sc);
+            s_sid[tid] = sid;
         }
         __syncthreads();
         for (int j = 0; j < cnt; j++) {
             const int pos = end - 1 - j;  // 0-based position in the tile list
-            float g_u = 0.f, g_v = 0.f, g_a = 0.f, g_b = 0.f, g_c = 0.f, g_ae = 0.f, g_r = 0.f, g_g = 0.f, g_bl = 0.f;
+            float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // u v a b c alpha_eff R G
+            float g_bl = 0.0f;
             bool contrib = false;
             if (pos < last) {
                 const float4 a = s_a[j];
@@ -191,50 +216,55 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
                     const float alpha = fminf(O.alpha_max, araw);
                     if (alpha >= O.alpha_min) {
                         contrib = true;
-                        const float om = 1.0f - alpha;
-                        const float Ti = T / om;
-                        const float cr = b.z, cg = b.w, cb = s_c[j];
-                        const float dalpha =
-                            dC0 * (cr * Ti - acc0 / om) + dC1 * (cg * Ti - acc1 / om) + dC2 * (cb * Ti - acc2 / om);
+                        const float4 nc = s_n[j];
+                        const float inv_om = 1.0f / (1.0f - alpha);
+                        const float Ti = T * inv_om;  // transmittance before this splat
+                        const float cr = b.z, cg = b.w, cb = nc.w;
+                        const float dalpha = dC0 * (cr * Ti - acc0 * inv_om) + dC1 * (cg * Ti - acc1 * inv_om) +
+                                             dC2 * (cb * Ti - acc2 * inv_om);
                         const float w = alpha * Ti;
-                        g_r = dC0 * w;
-                        g_g = dC1 * w;
+                        gv[6] = dC0 * w;
+                        gv[7] = dC1 * w;
                         g_bl = dC2 * w;
                         acc0 = fmaf(cr, w, acc0);
                         acc1 = fmaf(cg, w, acc1);
                         acc2 = fmaf(cb, w, acc2);
                         T = Ti;
                         if (!(araw > O.alpha_max)) {
-                            g_ae = dalpha * G;
+                            gv[5] = dalpha * G;
                             const float dpow = dalpha * araw;
-                            // natural conic from the pre-scaled one
-                            const float ca = a.z * (-2.0f * kLn2), cb2 = a.w * (-kLn2), cc = b.x * (-2.0f * kLn2);
-                            g_a = -0.5f * dpow * dx * dx;
-                            g_c = -0.5f * dpow * dy * dy;
-                            g_b = -dpow * dx * dy;
-                            g_u = dpow * (ca * dx + cb2 * dy);
-                            g_v = dpow * (cc * dy + cb2 * dx);
+                            const float hx = dpow * dx, hy = dpow * dy;
+                            gv[2] = -0.5f * hx * dx;
+                            gv[4] = -0.5f * hy * dy;
+                            gv[3] = -hx * dy;
+                            gv[0] = nc.x * hx + nc.y * hy;
+                            gv[1] = nc.z * hy + nc.y * hx;
                         }
                     }
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                g_u = warp_sum(g_u);
-                g_v = warp_sum(g_v);
-                g_a = warp_sum(g_a);
-                g_b = warp_sum(g_b);
-                g_c = warp_sum(g_c);
-                g_ae = warp_sum(g_ae);
-                g_r = warp_sum(g_r);
-                g_g = warp_sum(g_g);
-                g_bl = warp_sum(g_bl);
-                if ((threadIdx.x & 31) == 0) {
-                    float4* dst = grad2d + 3 * (size_t)s_sid[j];
-                    atomicAdd(dst + 0, make_float4(g_u, g_v, g_a, g_b));
-                    atomicAdd(dst + 1, make_float4(g_c, g_ae, g_r, g_g));
-                    atomicAdd(reinterpret_cast<float*>(dst + 2), g_bl);
-                }
+                const float tot = warp_reduce8(gv, lane);
+                if ((lane & 3) == 0) atomicAdd(&s_g[j * kGradStride + (lane >> 2)], tot);
+                const float tb = warp_sum(g_bl);
+                if (lane == 0) atomicAdd(&s_g[j * kGradStride + 8], tb);
             }
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            float4* sg = reinterpret_cast<float4*>(&s_g[tid * kGradStride]);
+            const float4 q0 = sg[0], q1 = sg[1];
+            const float q2 = s_g[tid * kGradStride + 8];
+            if (q0.x != 0.f || q0.y != 0.f || q0.z != 0.f || q0.w != 0.f || q1.x != 0.f || q1.y != 0.f ||
+                q1.z != 0.f || q1.w != 0.f || q2 != 0.f) {
+                float4* dst = grad2d + 3 * (size_t)s_sid[tid];
+                atomicAdd(dst + 0, q0);
+                atomicAdd(dst + 1, q1);
+                atomicAdd(reinterpret_cast<float*>(dst + 2), q2);
+            }
+            sg[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sg[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            s_g[tid * kGradStride + 8] = 0.0f;
         }
     }
 }

@@ -43,7 +43,7 @@ def gpu_forward(G, views, opts=None, shs_dtype=None, capacity=None):
     return fr, p, imgs, Ts
 
 
-def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.02):
+def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.05):
     ok = (ref["flags"] & 1) == 0
     assert 1.0 - ok.mean() <= max_flag_frac, f"too many borderline pixels: {1 - ok.mean():.4f}"
     err = np.abs(img - ref["image"])[:, ok]
@@ -289,7 +289,7 @@ def test_backward_config0():
 def test_backward_central_differences():
     """GPU gradient vs central differences of the GPU forward on 64 random
     parameters whose stencil changes no discrete decision (checked on the
-    oracle's per-pixel contributor counts)."""
+    oracle's per-pixel contributor sequences: same splats in the same order)."""
     G, views = ragged_scene(n=600, seed=31, L=2, K=1)
     G["log_s"][:3] += 0.7
     views = views[:2]
@@ -324,7 +324,7 @@ def test_backward_central_differences():
         same = True
         for v, ref in zip(views, refs):
             a, b = O.render(Gp, v), O.render(Gm, v)
-            if not (np.array_equal(a["n_contrib"], ref["n_contrib"]) and np.array_equal(b["n_contrib"], ref["n_contrib"])):
+            if not (np.array_equal(a["seq_hash"], ref["seq_hash"]) and np.array_equal(b["seq_hash"], ref["seq_hash"])):
                 same = False
                 break
         if not same:
