@@ -210,6 +210,33 @@ typedef struct {
 fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt,
                                 size_t state_bytes, fgs4d_state_layout_info *out);
 
+/* Largest n * n_views accepted by fgs4d_render_backward_noalloc. */
+#define FGS4D_NOALLOC_MAX_SPLATS 262144
+
+/* fgs4d_render_backward without caller-provided scratch.  The paper has no
+   counterpart: this is an interface for callers that cannot call cudaMalloc
+   when they run the backward pass, e.g. code whose stream is being captured
+   into a CUDA graph, real-time loops that reserve all device memory once at
+   start-up, or plugins of an engine that owns the device allocator.
+   Same arguments, results and tolerance as fgs4d_render_backward; the
+   forward state is read as input but its per-splat gradient section is not
+   used.  That scratch (48 bytes per (view, Gaussian) splat) lives instead in
+   a static device array of the library, 12 MiB, which every GPU that loads
+   the library holds until the process exits:
+   - n * n_views above FGS4D_NOALLOC_MAX_SPLATS returns FGS4D_ERR_CAPACITY
+     before anything is enqueued;
+   - the first call on a device looks up the array's device address (once per
+     device, with that device current); make that first call before any
+     stream capture;
+   - every call clears the part of the array it uses, then reuses it: calls
+     that overlap on the GPU (other streams, other threads) race on it and
+     must be serialised by the caller;
+   - nothing is allocated or freed. */
+fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
+                                           const fgs4d_options *opt, void *state, size_t state_bytes,
+                                           const float *final_T, const int32_t *n_last, const float *dL_dimage,
+                                           fgs4d_gaussian_grads *grads, fgs4d_stream stream);
+
 /* Copies the state's counters to *out (synchronises `stream`). */
 fgs4d_status fgs4d_read_counters(const void *state, fgs4d_counters *out, fgs4d_stream stream);
 

@@ -379,3 +379,81 @@ fgs4d_status fgs4d_read_counters(const void* state, fgs4d_counters* out, fgs4d_s
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// fgs4d_render_backward_noalloc: the backward pass without caller scratch.
+//
+// Some callers cannot call cudaMalloc at the moment they need the backward
+// pass: code running while its stream is being captured into a CUDA graph,
+// real-time render loops that reserve every byte of device memory once at
+// start-up and forbid later allocations, and plugins hosted by an engine
+// that owns the device allocator.  This entry point keeps its only scratch,
+// the per-splat 2D gradient (three float4 per (view, Gaussian) splat), in a
+// static device array of this library instead of the caller's state.  The
+// state from the forward pass is read as input; its gradient section is not
+// used.  The array holds FGS4D_NOALLOC_MAX_SPLATS splats (12 MiB) and every
+// GPU that loads this library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) float4 g_noalloc_grad2d[3 * (size_t)FGS4D_NOALLOC_MAX_SPLATS];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+float4* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device with that device current.  The host-side name of the array is
+// only a stand-in: kernels must get this address, never the symbol itself.
+cudaError_t noalloc_scratch(float4** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_grad2d);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<float4*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians* g, const fgs4d_view* views,
+                                                      int n_views, const fgs4d_options* opt, void* state,
+                                                      size_t state_bytes, const float* final_T,
+                                                      const int32_t* n_last, const float* dL_dimage,
+                                                      fgs4d_gaussian_grads* grads, fgs4d_stream stream) {
+    DevGauss G;
+    fgs4d_status s = check_gaussians(g, &G);
+    if (s != FGS4D_OK) return s;
+    if (!final_T || !n_last || !dL_dimage || !grads) return FGS4D_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        const void* ptrs[] = {grads->mu, grads->log_scale, grads->q_left, grads->q_right, grads->opacity_logit,
+                              grads->shs};
+        for (const void* p : ptrs)
+            if (!p || !aligned(p, 4)) return FGS4D_ERR_INVALID_ARG;
+    }
+    if (n_views >= 1 && g->n * (int64_t)n_views > (int64_t)FGS4D_NOALLOC_MAX_SPLATS) return FGS4D_ERR_CAPACITY;
+    Prepared* P = new Prepared;
+    s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK) {
+        float4* g2 = nullptr;
+        cudaError_t e = noalloc_scratch(&g2);
+        char* st = static_cast<char*>(state);
+        if (e == cudaSuccess)
+            e = launch_render_backward_into(P->VS, P->O, P->L, st, pair_buffer(*P), final_T, n_last, dL_dimage, g2,
+                                            (cudaStream_t)stream);
+        if (e == cudaSuccess)
+            e = launch_project_backward_from(G, P->VS, P->O, P->L, st, g2, *grads, (cudaStream_t)stream);
+        s = cuda_status(e);
+    }
+    delete P;
+    return s;
+}

@@ -502,6 +502,15 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
 int pair_sort_bits(uint32_t total_tiles);
 int radix_passes(int bits);
 
+// Variants of the two backward launchers that take the per-splat 2D gradient
+// buffer explicitly instead of the state's section.
+cudaError_t launch_render_backward_into(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
+                                        int pair_buf, const float* final_T, const int32_t* n_last,
+                                        const float* dL_dimage, float4* g2, cudaStream_t st);
+cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
+                                         const StateLayout& lay, char* state, const float4* g2,
+                                         const fgs4d_gaussian_grads& grads, cudaStream_t st);
+
 // Host-side count of kernel launches issued by this library (all threads).
 void count_launches(unsigned k);
 

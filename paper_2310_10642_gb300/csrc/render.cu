@@ -297,4 +297,22 @@ cudaError_t launch_render_backward(const ViewSet& VS, const DevOpts& O, const St
     return cudaGetLastError();
 }
 
+// Same as launch_render_backward, accumulating the per-splat 2D gradient into
+// g2 (zeroed here) instead of the state (used by the allocation-free
+// backward entry point).
+cudaError_t launch_render_backward_into(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
+                                        int pair_buf, const float* final_T, const int32_t* n_last,
+                                        const float* dL_dimage, float4* g2, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float4) * 3 * (size_t)lay.n_splats, st);
+    if (e != cudaSuccess) return e;
+    if (VS.total_tiles == 0) return cudaSuccess;
+    const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
+    const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
+    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    render_bwd_kernel<<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, (uint32_t)lay.n_splats, final_T,
+                                                          n_last, dL_dimage, g2);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace fgs4d

@@ -407,4 +407,19 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
     }
 }
 
+// Same as launch_project_backward, reading the per-splat 2D gradient from g2
+// instead of the state (used by the allocation-free backward entry point).
+cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
+                                         const StateLayout& lay, char* state, const float4* g2,
+                                         const fgs4d_gaussian_grads& grads, cudaStream_t st) {
+    if (G.n == 0) return cudaSuccess;
+    auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
+    switch (G.L) {
+        case 0: return launch_pb<0>(G, VS, O, tt, g2, grads, st);
+        case 1: return launch_pb<1>(G, VS, O, tt, g2, grads, st);
+        case 2: return launch_pb<2>(G, VS, O, tt, g2, grads, st);
+        default: return launch_pb<3>(G, VS, O, tt, g2, grads, st);
+    }
+}
+
 }  // namespace fgs4d

@@ -118,7 +118,8 @@ class StateLayoutInfo(ctypes.Structure):
 
 EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fgs4d_default_options", "fgs4d_state_size",
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
-           "fgs4d_state_layout", "fgs4d_read_counters"]
+           "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc"]
+NOALLOC_MAX_SPLATS = 262144
 
 
 class Fgs4dError(RuntimeError):
@@ -157,6 +158,8 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                                                 ctypes.POINTER(Options), vp, ctypes.c_size_t, vp, vp, vp,
                                                 ctypes.POINTER(GaussianGrads), vp]
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
+            L.fgs4d_render_backward_noalloc.argtypes = L.fgs4d_render_backward.argtypes
+            L.fgs4d_render_backward_noalloc.restype = ci
             L.fgs4d_state_layout.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), ctypes.c_size_t,
                                              ctypes.POINTER(StateLayoutInfo)]
             for fn in ("fgs4d_state_size", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render",
@@ -250,3 +253,12 @@ def fgs4d_state_layout(n: int, views, n_views: int, opts: Options, state_bytes: 
 
 def fgs4d_launch_count() -> int:
     return int(lib().fgs4d_launch_count())
+
+
+def fgs4d_render_backward_noalloc(g: Gaussians, views, n_views: int, opts: Options, state: int, state_bytes: int,
+                                  final_T: int, n_last: int, dL_dimage: int, grads: GaussianGrads, stream: int):
+    """Backward pass whose scratch lives in the library's static device array
+    (at most NOALLOC_MAX_SPLATS (view, Gaussian) splats); allocates nothing."""
+    _check("fgs4d_render_backward_noalloc",
+           lib().fgs4d_render_backward_noalloc(ctypes.byref(g), views, int(n_views), ctypes.byref(opts), state,
+                                               state_bytes, final_T, n_last, dL_dimage, ctypes.byref(grads), stream))
