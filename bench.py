@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shs-bf16", action="store_true", help="store 4DSH coefficients in BF16")
+    ap.add_argument("--tile", type=int, default=32, choices=[16, 32], help="screen tile side")
     return ap.parse_args()
 
 
@@ -186,6 +187,7 @@ def main():
     N.lib()
 
     G, views, opts = workload_inputs(args.n, args.views, args.scale)
+    opts = dict(opts, tile_size=args.tile)
     n = G["logit"].shape[0]
     shs_dtype = torch.bfloat16 if args.shs_bf16 else torch.float32
     p = R.params_to_device(G, shs_dtype=shs_dtype)
@@ -350,7 +352,7 @@ def main():
                    unit="Mpix/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms_step, 4),
                    higher_is_better=True, scaling="weak", vs_baseline=None,
                    dtype="f32" + ("+bf16-shs" if args.shs_bf16 else ""), data="synthetic",
-                   config=dict(WORKLOAD, n=n, views=V, l2="inputs larger than L2 (644 MB parameters)",
+                   config=dict(WORKLOAD, n=n, views=V, tile=args.tile, l2="inputs larger than L2 (644 MB parameters)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                                pixels_per_step=npix, visible_splats=nvis, pairs=npairs),
                    fwd_mpix_s=round(fwd_mpix, 3), stage_ms={k: round(v, 4) for k, v in stage_ms.items()},

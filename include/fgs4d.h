@@ -52,7 +52,7 @@ extern "C" {
 #define FGS4D_MAX_VIEWS 128   /* views per call */
 #define FGS4D_MAX_SH_DEGREE 3 /* L */
 #define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
-#define FGS4D_TILE 16         /* screen tiles are 16 x 16 pixels */
+#define FGS4D_TILE 16         /* default screen tile: 16 x 16 pixels (32 x 32 selectable) */
 
 typedef struct CUstream_st *fgs4d_stream; /* identical to cudaStream_t */
 
@@ -118,6 +118,8 @@ typedef struct {
     int record_fp16;  /* 0: FP32 splat records; 1: FP16 conic (mixed precision) */
     float schur_cond; /* 1e-3: FP64 Schur complement when min_i Sigma3_ii/Sigma_ii is below */
     float conic_cond; /* 1e-4: FP64 2x2 inversion when det/(S00*S11) is below */
+    int tile_size;    /* 16 or 32: side of the square screen tiles (binning and compositing);
+                         32 bins each splat to ~3x fewer tiles, each thread composites 2x2 pixels */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but

@@ -36,6 +36,7 @@ fgs4d_status check_options(const fgs4d_options* o) {
     if (!(o->alpha_min > 0.0f && o->alpha_min <= o->alpha_max && o->alpha_max < 1.0f)) return FGS4D_ERR_INVALID_ARG;
     if (!(o->near_z > 0.0f) || o->p_min > 1.0f || o->T_min >= 1.0f) return FGS4D_ERR_INVALID_ARG;
     if (o->record_fp16 != 0) return FGS4D_ERR_INVALID_ARG;  // mixed-precision records: not in this build
+    if (o->tile_size != 16 && o->tile_size != 32) return FGS4D_ERR_INVALID_ARG;
     return FGS4D_OK;
 }
 
@@ -51,6 +52,7 @@ DevOpts dev_options(const fgs4d_options* o) {
     d.conic_cond = o->conic_cond;
     d.ln_alpha_min = logf(o->alpha_min);
     d.record_fp16 = o->record_fp16;
+    d.tile = o->tile_size;
     return d;
 }
 
@@ -93,8 +95,8 @@ fgs4d_status make_views(const fgs4d_view* views, int n_views, const fgs4d_option
         }
         d.width = h.width;
         d.height = h.height;
-        d.tiles_x = (h.width + kTile - 1) / kTile;
-        d.tiles_y = (h.height + kTile - 1) / kTile;
+        d.tiles_x = (h.width + o->tile_size - 1) / o->tile_size;
+        d.tiles_y = (h.height + o->tile_size - 1) / o->tile_size;
         d.tile_base = (uint32_t)tiles;
         d.pix_base = (uint32_t)pix;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
@@ -243,6 +245,7 @@ void fgs4d_default_options(fgs4d_options* o) {
     o->record_fp16 = 0;
     o->schur_cond = 1e-3f;
     o->conic_cond = 1e-4f;
+    o->tile_size = FGS4D_TILE;
 }
 
 int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {

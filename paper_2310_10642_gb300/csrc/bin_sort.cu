@@ -182,13 +182,20 @@ __global__ void __launch_bounds__(kThreads) radix_upsweep_kernel(const uint32_t*
     const uint32_t n = device_count(d_n, n_max);
     uint32_t begin, end;
     block_chunk(n, gridDim.x, begin, end);
-    // warp-strided so that every iteration is warp-uniform (needed by match_any)
-    for (uint32_t base = begin + wid * 32; base < end; base += kThreads) {
-        const uint32_t i = base + lane;
-        const uint32_t d = i < end ? (keys[i] >> shift) & (D - 1) : D;
-        const uint32_t peers = __match_any_sync(kFull, d);
-        if (d < D && lane == __ffs(peers) - 1) s_h[wid][d] += __popc(peers);
+    (void)lane;
+    // 16-byte loads (chunks start at multiples of kTileItems of a 256-byte
+    // aligned array), one shared atomic per key into the warp's histogram
+    const uint32_t n4 = (end - begin) / 4;
+    const uint4* k4 = reinterpret_cast<const uint4*>(keys + begin);
+    uint32_t* h = s_h[wid];
+    for (uint32_t i = tid; i < n4; i += kThreads) {
+        const uint4 q = k4[i];
+        atomicAdd(&h[(q.x >> shift) & (D - 1)], 1u);
+        atomicAdd(&h[(q.y >> shift) & (D - 1)], 1u);
+        atomicAdd(&h[(q.z >> shift) & (D - 1)], 1u);
+        atomicAdd(&h[(q.w >> shift) & (D - 1)], 1u);
     }
+    for (uint32_t i = begin + 4 * n4 + tid; i < end; i += kThreads) atomicAdd(&h[(keys[i] >> shift) & (D - 1)], 1u);
     __syncthreads();
     for (uint32_t k = 0; k < DPT; k++) {
         const uint32_t d = tid * DPT + k;
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
                                                          const uint32_t* __restrict__ offsets,
                                                          const uint32_t* __restrict__ tiles,
                                                          const SplatRecord* __restrict__ rec, uint32_t n_max,
-                                                         uint32_t* counters, uint32_t capacity,
+                                                         uint32_t* counters, uint32_t capacity, int tile,
                                                          uint32_t* __restrict__ pair_keys,
                                                          uint32_t* __restrict__ pair_vals) {
     const uint32_t n_vis = min(counters[0], n_max);
@@ -385,7 +392,7 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             const float fx1 = fminf(floorf(r0.x + radius), (float)(V.width - 1));
             const float fy0 = fmaxf(ceilf(r0.y - radius), 0.0f);
             const float fy1 = fminf(floorf(r0.y + radius), (float)(V.height - 1));
-            const int ix0 = (int)fx0 / kTile, ix1 = (int)fx1 / kTile, iy0 = (int)fy0 / kTile, iy1 = (int)fy1 / kTile;
+            const int ix0 = (int)fx0 / tile, ix1 = (int)fx1 / tile, iy0 = (int)fy0 / tile, iy1 = (int)fy1 / tile;
             x0 = (uint32_t)ix0;
             y0 = (uint32_t)iy0;
             wx = (uint32_t)max(ix1 - ix0 + 1, 1);
@@ -447,7 +454,6 @@ int pair_sort_bits(uint32_t total_tiles) {
 
 cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int sm_count,
                             cudaStream_t st, int* out_buf) {
-    (void)O;
     const uint32_t S = (uint32_t)lay.n_splats;
     uint32_t* counters = reinterpret_cast<uint32_t*>(state + lay.counters);
     uint32_t* tiles = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
@@ -492,7 +498,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     // 4. emission
     const int stride_grid = 16 * sm_count;
     emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, S,
-                                                       counters, cap, pk[0], pv[0]);
+                                                       counters, cap, O.tile, pk[0], pv[0]);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;

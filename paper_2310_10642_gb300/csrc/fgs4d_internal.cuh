@@ -15,8 +15,7 @@
 
 namespace fgs4d {
 
-constexpr int kTile = FGS4D_TILE;              // 16x16 pixel tiles
-constexpr int kTilePix = kTile * kTile;        // 256 pixels, one per thread
+constexpr int kTilePix = 256;                  // threads per compositing CTA
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e)
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -45,6 +44,7 @@ struct DevOpts {
     float schur_cond, conic_cond;
     float ln_alpha_min;
     int record_fp16;
+    int tile;  // screen tile side: 16 or 32
 };
 
 // Gaussian parameters (SoA) as the kernels see them.
@@ -464,10 +464,10 @@ __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, co
     const float fy0 = fmaxf(ceilf(w.v - w.radius), 0.0f);
     const float fy1 = fminf(floorf(w.v + w.radius), (float)(V.height - 1));
     if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
-    w.rect[0] = (int)fx0 / kTile;
-    w.rect[1] = (int)fy0 / kTile;
-    w.rect[2] = (int)fx1 / kTile;
-    w.rect[3] = (int)fy1 / kTile;
+    w.rect[0] = (int)fx0 / O.tile;
+    w.rect[1] = (int)fy0 / O.tile;
+    w.rect[2] = (int)fx1 / O.tile;
+    w.rect[3] = (int)fy1 / O.tile;
     w.tiles = (w.rect[2] - w.rect[0] + 1) * (w.rect[3] - w.rect[1] + 1);
     return true;
 }

@@ -1,9 +1,12 @@
 // render.cu -- tile-based front-to-back compositing (Eq. 6) and its adjoint.
 //
-// One CTA of 256 threads per 16x16 tile, one pixel per thread.  The tile's
-// depth-ordered splat list is walked in batches of 256: each thread gathers
-// one splat record into shared memory, then every pixel evaluates the batch.
-// A CTA stops as soon as all its pixels have terminated (__syncthreads_count).
+// One CTA of 256 threads per screen tile.  With 16x16 tiles each thread owns
+// one pixel; with 32x32 tiles each thread owns a 2x2 block, which amortises
+// the shared-memory reads of a splat over four pixels and cuts the number of
+// (splat, tile) pairs the binning has to sort.  The tile's depth-ordered
+// splat list is walked in batches of 256: each thread gathers one splat
+// record into shared memory, then every pixel evaluates the batch.  A CTA
+// stops as soon as all its pixels have terminated (__syncthreads_count).
 //
 // Per pixel and splat (readings R4-R6):
 //   power = -1/2 (a dx^2 + c dy^2) - b dx dy, dx = x - u, dy = y - v
@@ -29,12 +32,8 @@ __device__ __forceinline__ int find_view(const ViewSet& VS, uint32_t tile) {
     return lo;
 }
 
-struct Staged {
-    float4 a;  // (u, v, A', B')  A' = -log2e/2 a, B' = -log2e b
-    float4 b;  // (C', alpha_eff, R, G)
-    float c;   // B
-};
-
+// Shared-memory form of a record: a = (u, v, A', B'), b = (C', alpha_eff, R, G),
+// c = B, with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
 __device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float& sc) {
     sa = make_float4(r.r0.x, r.r0.y, __fmul_rn(-0.5f * kLog2e, r.r0.z), __fmul_rn(-kLog2e, r.r0.w));
     sb = make_float4(__fmul_rn(-0.5f * kLog2e, r.r1.x), r.r1.y, r.r1.z, r.r1.w);
@@ -46,76 +45,117 @@ __device__ __forceinline__ float power2(float A, float B, float C, float dx, flo
     return __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(B, dx), dy)));
 }
 
+// Pixels of thread `tid` in a TS x TS tile whose top-left pixel is (x0, y0).
+template <int TS>
+struct TilePixels {
+    static constexpr int P = TS * TS / kTilePix;  // pixels per thread: 1 or 4
+    __device__ __forceinline__ static void coords(int tid, int x0, int y0, int k, int& px, int& py) {
+        if (TS == 16) {
+            px = x0 + (tid & 15);
+            py = y0 + (tid >> 4);
+        } else {  // 2x2 block per thread; a warp covers a 32x4 strip
+            px = x0 + 2 * (tid & 15) + (k & 1);
+            py = y0 + 2 * (tid >> 4) + (k >> 1);
+        }
+    }
+};
+
+template <int TS>
 __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
                                                               const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ pair_vals,
                                                               const SplatRecord* __restrict__ rec, uint32_t n_splats,
                                                               float* __restrict__ image, float* __restrict__ final_T,
                                                               int32_t* __restrict__ n_last) {
+    constexpr int P = TilePixels<TS>::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
     __shared__ float s_c[kTilePix];
+    const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
     const DevView& V = VS.v[v];
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
-    const bool inside = px < V.width && py < V.height;
     const uint2 range = ranges[tile];
-    const float fpx = (float)px, fpy = (float)py;
-    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-    int32_t last = 0;
-    bool done = !inside;
+    float fpx[P], fpy[P], T[P], C0[P], C1[P], C2[P];
+    int32_t last[P];
+    bool pdone[P], inside[P];
+    bool done = true;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        int px, py;
+        TilePixels<TS>::coords(tid, tx * TS, ty * TS, k, px, py);
+        inside[k] = px < V.width && py < V.height;
+        fpx[k] = (float)px;
+        fpy[k] = (float)py;
+        T[k] = 1.0f;
+        C0[k] = C1[k] = C2[k] = 0.0f;
+        last[k] = 0;
+        pdone[k] = !inside[k];
+        done = done && pdone[k];
+    }
     for (uint32_t base = range.x; base < range.y; base += kTilePix) {
         if (__syncthreads_count(done) == kTilePix) break;
-        const uint32_t idx = base + threadIdx.x;
+        const uint32_t idx = base + tid;
         if (idx < range.y) {
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
-                stage_record(rec[sid], s_a[threadIdx.x], s_b[threadIdx.x], s_c[threadIdx.x]);
+                stage_record(rec[sid], s_a[tid], s_b[tid], s_c[tid]);
             } else {  // never produced by bin_sort; an invisible splat keeps the access in bounds
-                s_a[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_b[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_c[threadIdx.x] = 0.f;
+                s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_c[tid] = 0.f;
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kTilePix, range.y - base);
-        if (!done) {
-            for (int j = 0; j < cnt; j++) {
-                const float4 a = s_a[j];
-                const float4 b = s_b[j];
-                const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
+        for (int j = 0; j < cnt && !done; j++) {
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+            const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
+#pragma unroll
+            for (int k = 0; k < P; k++) {
+                if (pdone[k]) continue;
+                const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
                 const float p2 = power2(a.z, a.w, b.x, dx, dy);
                 if (!(p2 <= 0.0f)) continue;
                 const float araw = __fmul_rn(b.y, ex2_approx(p2));
                 const float alpha = fminf(O.alpha_max, araw);
                 if (alpha < O.alpha_min) continue;
-                const float Tn = T * (1.0f - alpha);
+                const float Tn = T[k] * (1.0f - alpha);
                 if (Tn < O.T_min) {
-                    done = true;
-                    break;
+                    pdone[k] = true;
+                    continue;
                 }
-                const float w = alpha * T;
-                C0 = fmaf(b.z, w, C0);
-                C1 = fmaf(b.w, w, C1);
-                C2 = fmaf(s_c[j], w, C2);
-                T = Tn;
-                last = (int32_t)(base - range.x) + j + 1;
+                const float w = alpha * T[k];
+                C0[k] = fmaf(b.z, w, C0[k]);
+                C1[k] = fmaf(b.w, w, C1[k]);
+                C2[k] = fmaf(s_c[j], w, C2[k]);
+                T[k] = Tn;
+                last[k] = pos1;
+            }
+            if (P > 1) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < P; k++) all = all && pdone[k];
+                done = all;
+            } else {
+                done = pdone[0];
             }
         }
     }
-    if (inside) {
-        const size_t npix = (size_t)V.width * V.height;
-        const size_t p = (size_t)py * V.width + px;
-        float* img = image + 3 * (size_t)V.pix_base;
-        img[p] = fmaf(T, V.bg[0], C0);
-        img[npix + p] = fmaf(T, V.bg[1], C1);
-        img[2 * npix + p] = fmaf(T, V.bg[2], C2);
-        final_T[V.pix_base + p] = T;
-        n_last[V.pix_base + p] = last;
+    const size_t npix = (size_t)V.width * V.height;
+    float* img = image + 3 * (size_t)V.pix_base;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        if (!inside[k]) continue;
+        const size_t p = (size_t)fpy[k] * V.width + (size_t)fpx[k];
+        img[p] = fmaf(T[k], V.bg[0], C0[k]);
+        img[npix + p] = fmaf(T[k], V.bg[1], C1[k]);
+        img[2 * npix + p] = fmaf(T[k], V.bg[2], C2[k]);
+        final_T[V.pix_base + p] = T[k];
+        n_last[V.pix_base + p] = last[k];
     }
 }
 
@@ -143,11 +183,13 @@ __device__ __forceinline__ float warp_reduce8(const float (&v)[8], int lane) {
 
 constexpr int kGradStride = 12;  // floats per staged splat in the shared gradient accumulator
 
+template <int TS>
 __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
     const __grid_constant__ ViewSet VS, const DevOpts O, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const SplatRecord* __restrict__ rec, uint32_t n_splats,
     const float* __restrict__ final_T, const int32_t* __restrict__ n_last, const float* __restrict__ dL_dimage,
     float4* __restrict__ grad2d) {
+    constexpr int P = TilePixels<TS>::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
     __shared__ float4 s_n[kTilePix];  // natural conic (a, b, c) and B
@@ -160,30 +202,40 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
     const DevView& V = VS.v[v];
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
-    const int px = tx * kTile + (tid & (kTile - 1));
-    const int py = ty * kTile + (tid / kTile);
-    const bool inside = px < V.width && py < V.height;
     const uint2 range = ranges[tile];
-    const float fpx = (float)px, fpy = (float)py;
     const size_t npix = (size_t)V.width * V.height;
-    const size_t p = (size_t)py * V.width + px;
-    float T = 1.0f, dC0 = 0.0f, dC1 = 0.0f, dC2 = 0.0f;
-    int32_t last = 0;
-    if (inside) {
-        T = final_T[V.pix_base + p];
-        last = n_last[V.pix_base + p];
-        const float* g = dL_dimage + 3 * (size_t)V.pix_base;
-        dC0 = g[p];
-        dC1 = g[npix + p];
-        dC2 = g[2 * npix + p];
+    const float* gimg = dL_dimage + 3 * (size_t)V.pix_base;
+    float fpx[P], fpy[P], T[P], dC0[P], dC1[P], dC2[P], acc0[P], acc1[P], acc2[P];
+    int32_t last[P];
+    int my_max = 0;
+#pragma unroll
+    for (int k = 0; k < P; k++) {
+        int px, py;
+        TilePixels<TS>::coords(tid, tx * TS, ty * TS, k, px, py);
+        fpx[k] = (float)px;
+        fpy[k] = (float)py;
+        T[k] = 1.0f;
+        dC0[k] = dC1[k] = dC2[k] = 0.0f;
+        last[k] = 0;
+        if (px < V.width && py < V.height) {
+            const size_t p = (size_t)py * V.width + px;
+            T[k] = final_T[V.pix_base + p];
+            last[k] = n_last[V.pix_base + p];
+            dC0[k] = gimg[p];
+            dC1[k] = gimg[npix + p];
+            dC2[k] = gimg[2 * npix + p];
+        }
+        // acc = sum_{j > i} c_j alpha_j T_j + T_final bg, built back to front
+        acc0[k] = T[k] * V.bg[0];
+        acc1[k] = T[k] * V.bg[1];
+        acc2[k] = T[k] * V.bg[2];
+        my_max = max(my_max, last[k]);
     }
-    // acc = sum_{j > i} c_j alpha_j T_j + T_final bg, built back to front
-    float acc0 = T * V.bg[0], acc1 = T * V.bg[1], acc2 = T * V.bg[2];
     if (tid == 0) s_max = 0;
 #pragma unroll
     for (int k = 0; k < kGradStride; k++) s_g[tid * kGradStride + k] = 0.0f;
     __syncthreads();
-    atomicMax(&s_max, last);
+    atomicMax(&s_max, my_max);
     __syncthreads();
     const int max_last = min(s_max, (int)(range.y - range.x));
     for (int end = max_last; end > 0; end -= kTilePix) {
@@ -205,42 +257,42 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
             float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // u v a b c alpha_eff R G
             float g_bl = 0.0f;
             bool contrib = false;
-            if (pos < last) {
-                const float4 a = s_a[j];
-                const float4 b = s_b[j];
-                const float dx = __fsub_rn(fpx, a.x), dy = __fsub_rn(fpy, a.y);
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
+#pragma unroll
+            for (int k = 0; k < P; k++) {
+                if (pos >= last[k]) continue;
+                const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
                 const float p2 = power2(a.z, a.w, b.x, dx, dy);
-                if (p2 <= 0.0f) {
-                    const float G = ex2_approx(p2);
-                    const float araw = __fmul_rn(b.y, G);
-                    const float alpha = fminf(O.alpha_max, araw);
-                    if (alpha >= O.alpha_min) {
-                        contrib = true;
-                        const float4 nc = s_n[j];
-                        const float inv_om = 1.0f / (1.0f - alpha);
-                        const float Ti = T * inv_om;  // transmittance before this splat
-                        const float cr = b.z, cg = b.w, cb = nc.w;
-                        const float dalpha = dC0 * (cr * Ti - acc0 * inv_om) + dC1 * (cg * Ti - acc1 * inv_om) +
-                                             dC2 * (cb * Ti - acc2 * inv_om);
-                        const float w = alpha * Ti;
-                        gv[6] = dC0 * w;
-                        gv[7] = dC1 * w;
-                        g_bl = dC2 * w;
-                        acc0 = fmaf(cr, w, acc0);
-                        acc1 = fmaf(cg, w, acc1);
-                        acc2 = fmaf(cb, w, acc2);
-                        T = Ti;
-                        if (!(araw > O.alpha_max)) {
-                            gv[5] = dalpha * G;
-                            const float dpow = dalpha * araw;
-                            const float hx = dpow * dx, hy = dpow * dy;
-                            gv[2] = -0.5f * hx * dx;
-                            gv[4] = -0.5f * hy * dy;
-                            gv[3] = -hx * dy;
-                            gv[0] = nc.x * hx + nc.y * hy;
-                            gv[1] = nc.z * hy + nc.y * hx;
-                        }
-                    }
+                if (!(p2 <= 0.0f)) continue;
+                const float G = ex2_approx(p2);
+                const float araw = __fmul_rn(b.y, G);
+                const float alpha = fminf(O.alpha_max, araw);
+                if (alpha < O.alpha_min) continue;
+                contrib = true;
+                const float4 nc = s_n[j];
+                const float inv_om = 1.0f / (1.0f - alpha);
+                const float Ti = T[k] * inv_om;  // transmittance before this splat
+                const float cr = b.z, cg = b.w, cb = nc.w;
+                const float dalpha = dC0[k] * (cr * Ti - acc0[k] * inv_om) + dC1[k] * (cg * Ti - acc1[k] * inv_om) +
+                                     dC2[k] * (cb * Ti - acc2[k] * inv_om);
+                const float w = alpha * Ti;
+                gv[6] = fmaf(dC0[k], w, gv[6]);
+                gv[7] = fmaf(dC1[k], w, gv[7]);
+                g_bl = fmaf(dC2[k], w, g_bl);
+                acc0[k] = fmaf(cr, w, acc0[k]);
+                acc1[k] = fmaf(cg, w, acc1[k]);
+                acc2[k] = fmaf(cb, w, acc2[k]);
+                T[k] = Ti;
+                if (!(araw > O.alpha_max)) {
+                    gv[5] = fmaf(dalpha, G, gv[5]);
+                    const float dpow = dalpha * araw;
+                    const float hx = dpow * dx, hy = dpow * dy;
+                    gv[2] -= 0.5f * hx * dx;
+                    gv[4] -= 0.5f * hy * dy;
+                    gv[3] -= hx * dy;
+                    gv[0] += nc.x * hx + nc.y * hy;
+                    gv[1] += nc.z * hy + nc.y * hx;
                 }
             }
             if (__any_sync(0xffffffffu, contrib)) {
@@ -275,8 +327,28 @@ cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout
     const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
     const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
     const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
-    render_fwd_kernel<<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, (uint32_t)lay.n_splats, image,
-                                                          final_T, n_last);
+    const uint32_t S = (uint32_t)lay.n_splats;
+    if (O.tile == 32)
+        render_fwd_kernel<32><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
+    else
+        render_fwd_kernel<16><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_bwd_tiles(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
+                                    int pair_buf, const float* final_T, const int32_t* n_last, const float* dL_dimage,
+                                    float4* g2, cudaStream_t st) {
+    const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
+    const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
+    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    const uint32_t S = (uint32_t)lay.n_splats;
+    if (O.tile == 32)
+        render_bwd_kernel<32><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
+                                                                   dL_dimage, g2);
+    else
+        render_bwd_kernel<16><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
+                                                                   dL_dimage, g2);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -288,13 +360,7 @@ cudaError_t launch_render_backward(const ViewSet& VS, const DevOpts& O, const St
     cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float4) * 3 * (size_t)lay.n_splats, st);
     if (e != cudaSuccess) return e;
     if (VS.total_tiles == 0) return cudaSuccess;
-    const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
-    const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
-    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
-    render_bwd_kernel<<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, (uint32_t)lay.n_splats, final_T,
-                                                          n_last, dL_dimage, g2);
-    count_launches(1);
-    return cudaGetLastError();
+    return launch_bwd_tiles(VS, O, lay, state, pair_buf, final_T, n_last, dL_dimage, g2, st);
 }
 
 // Same as launch_render_backward, accumulating the per-splat 2D gradient into
@@ -306,13 +372,7 @@ cudaError_t launch_render_backward_into(const ViewSet& VS, const DevOpts& O, con
     cudaError_t e = cudaMemsetAsync(g2, 0, sizeof(float4) * 3 * (size_t)lay.n_splats, st);
     if (e != cudaSuccess) return e;
     if (VS.total_tiles == 0) return cudaSuccess;
-    const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
-    const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
-    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
-    render_bwd_kernel<<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, (uint32_t)lay.n_splats, final_T,
-                                                          n_last, dL_dimage, g2);
-    count_launches(1);
-    return cudaGetLastError();
+    return launch_bwd_tiles(VS, O, lay, state, pair_buf, final_T, n_last, dL_dimage, g2, st);
 }
 
 }  // namespace fgs4d

@@ -97,7 +97,7 @@ class Options(ctypes.Structure):
     _fields_ = [("p_min", ctypes.c_float), ("near_z", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("clamp_fov", ctypes.c_float), ("record_fp16", ctypes.c_int), ("schur_cond", ctypes.c_float),
-                ("conic_cond", ctypes.c_float)]
+                ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int)]
 
 
 class GaussianGrads(ctypes.Structure):

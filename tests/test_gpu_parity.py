@@ -53,10 +53,14 @@ def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.05):
 
 
 # ---------------------------------------------------------------------------- forward
-def test_forward_config0_full_frame():
+TILES = pytest.mark.parametrize("tile", [16, 32])
+
+
+@TILES
+def test_forward_config0_full_frame(tile):
     c = I.config(0)
     G, views = c["gaussians"], c["views"]
-    fr, _, imgs, Ts = gpu_forward(G, views)
+    fr, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
     ref = O.render(G, views[0])
     assert fr.last_counters.n_visible == ref["n_visible"]
     assert_image_parity(imgs[0], Ts[0], ref)
@@ -71,9 +75,10 @@ def ragged_scene(n=3000, seed=11, L=3, K=2):
     return G, views
 
 
-def test_forward_ragged_multiview():
+@TILES
+def test_forward_ragged_multiview(tile):
     G, views = ragged_scene()
-    _, _, imgs, Ts = gpu_forward(G, views)
+    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
     for v, img, T in zip(views, imgs, Ts):
         ref = O.render(G, v)
         assert_image_parity(img, T, ref)
@@ -139,27 +144,28 @@ def test_slice_project_records_match_oracle():
         close(r[:, 9], ref["depth"][both], 1e-6, 1e-6, "depth")
 
 
-def test_tile_lists_are_depth_ordered_and_complete():
+@TILES
+def test_tile_lists_are_depth_ordered_and_complete(tile):
     G, views = ragged_scene(n=2500, seed=14)
-    fr, _, _, _ = gpu_forward(G, views)
+    fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile))
     rec, tiles, ranges, vals = read_state(fr)
     n = G["logit"].shape[0]
     tile_base = 0
     expect = {}
     for vi, v in enumerate(views):
-        tx_n = (v["width"] + 15) // 16
+        tx_n = (v["width"] + tile - 1) // tile
         for g in np.nonzero(tiles[vi * n:(vi + 1) * n])[0]:
             sid = vi * n + g
             u, vv, rad = rec[sid, 0], rec[sid, 1], rec[sid, 10]
-            x0 = max(math.ceil(u - rad), 0) // 16
-            x1 = min(math.floor(u + rad), v["width"] - 1) // 16
-            y0 = max(math.ceil(vv - rad), 0) // 16
-            y1 = min(math.floor(vv + rad), v["height"] - 1) // 16
+            x0 = max(math.ceil(u - rad), 0) // tile
+            x1 = min(math.floor(u + rad), v["width"] - 1) // tile
+            y0 = max(math.ceil(vv - rad), 0) // tile
+            y1 = min(math.floor(vv + rad), v["height"] - 1) // tile
             assert (x1 - x0 + 1) * (y1 - y0 + 1) == tiles[sid]
             for ty in range(y0, y1 + 1):
                 for tx in range(x0, x1 + 1):
                     expect.setdefault(tile_base + ty * tx_n + tx, []).append(sid)
-        tile_base += tx_n * ((v["height"] + 15) // 16)
+        tile_base += tx_n * ((v["height"] + tile - 1) // tile)
     assert tile_base == ranges.shape[0]
     for t in range(ranges.shape[0]):
         s, e = ranges[t]
@@ -168,11 +174,12 @@ def test_tile_lists_are_depth_ordered_and_complete():
         assert got == want, f"tile {t}"
 
 
-def test_batched_equals_one_by_one():
+@TILES
+def test_batched_equals_one_by_one(tile):
     G, views = ragged_scene(n=2000, seed=15)
-    _, _, imgs, Ts = gpu_forward(G, views)
+    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
     for v, img, T in zip(views, imgs, Ts):
-        _, _, im1, T1 = gpu_forward(G, [v])
+        _, _, im1, T1 = gpu_forward(G, [v], dict(tile_size=tile))
         np.testing.assert_array_equal(img, im1[0])
         np.testing.assert_array_equal(T, T1[0])
 
@@ -208,12 +215,13 @@ def test_edge_cases_empty_culled_tiny():
     G["mu"][3] += 50.0
     fr, _, imgs, _ = gpu_forward(G, [v])
     assert fr.last_counters.n_visible == 0 and np.allclose(imgs[0], np.array([0.2, 0.4, 0.6])[:, None, None])
-    # 1x1 image and a one-tile image
+    # 1x1 image, one-tile images, one-row images, for both tile sizes
     G = I.gaussians(800, 3, 2, 1)
-    for w, h in ((1, 1), (16, 16), (17, 1)):
-        vv = I.view((0.1, 0.2, 4.0), w, h, 0.5)
-        _, _, imgs, Ts = gpu_forward(G, [vv])
-        assert_image_parity(imgs[0], Ts[0], O.render(G, vv), max_flag_frac=1.0)
+    for tile in (16, 32):
+        for w, h in ((1, 1), (16, 16), (32, 32), (17, 1), (33, 2)):
+            vv = I.view((0.1, 0.2, 4.0), w, h, 0.5)
+            _, _, imgs, Ts = gpu_forward(G, [vv], dict(tile_size=tile))
+            assert_image_parity(imgs[0], Ts[0], O.render(G, vv), max_flag_frac=1.0)
 
 
 def test_pair_capacity_overflow_is_reported_not_faulted():
@@ -267,9 +275,10 @@ def masked_dL(views, refs, seed):
     return out
 
 
-def test_backward_matches_oracle():
+@TILES
+def test_backward_matches_oracle(tile):
     G, views = ragged_scene(n=1500, seed=21)
-    fr, p, _, _ = gpu_forward(G, views)
+    fr, p, _, _ = gpu_forward(G, views, dict(tile_size=tile))
     refs = [O.render(G, v) for v in views]
     dL = masked_dL(views, refs, 5)
     gg = grads_gpu(fr, p, dL)
@@ -277,10 +286,11 @@ def test_backward_matches_oracle():
     assert_grad_parity(gg, go)
 
 
-def test_backward_config0():
+@TILES
+def test_backward_config0(tile):
     c = I.config(0)
     G, views = c["gaussians"], c["views"]
-    fr, p, _, _ = gpu_forward(G, views)
+    fr, p, _, _ = gpu_forward(G, views, dict(tile_size=tile))
     refs = [O.render(G, v) for v in views]
     dL = masked_dL(views, refs, 6)
     assert_grad_parity(grads_gpu(fr, p, dL), O.backward_views(G, views, dL))
