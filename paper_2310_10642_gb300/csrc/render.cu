@@ -3,17 +3,23 @@
 // One CTA of 256 threads per screen tile.  With 16x16 tiles each thread owns
 // one pixel; with 32x32 tiles each thread owns a 2x2 block, which amortises
 // the shared-memory reads of a splat over four pixels and cuts the number of
-// (splat, tile) pairs the binning has to sort.  The tile's depth-ordered
-// splat list is walked in batches of 256: each thread gathers one splat
-// record into shared memory, then every pixel evaluates the batch.  A CTA
-// stops as soon as all its pixels have terminated (__syncthreads_count).
+// (splat, tile) pairs the binning has to sort.  Each warp owns a compact
+// region of the tile (8x4 pixels, resp. 16x8), so that a splat whose support
+// disk misses the region is skipped by the whole warp at once.  The tile's
+// depth-ordered splat list is walked in batches of 256: each thread gathers
+// one splat record into shared memory, then every pixel evaluates the batch.
+// A CTA stops as soon as all its pixels have terminated (__syncthreads_count).
 //
 // Per pixel and splat (readings R4-R6):
 //   power = -1/2 (a dx^2 + c dy^2) - b dx dy, dx = x - u, dy = y - v
 //   skip if power > 0; alpha = min(alpha_max, alpha_eff * exp(power));
 //   skip if alpha < alpha_min; stop (splat excluded) if T (1 - alpha) < T_min;
 //   C += c alpha T; T *= 1 - alpha.  Finally C += T bg.
-// alpha_eff = sigmoid(logit) p(t) carries the marginal of Eq. 6.
+// alpha_eff = sigmoid(logit) p(t) carries the marginal of Eq. 6.  Beyond the
+// support radius r of a splat alpha < alpha_min holds by construction (the
+// radius bounds alpha_eff exp(-|d|^2 / (2 lambda_max)) with half a pixel to
+// spare), so skipping a region that lies entirely beyond r takes the same
+// decision the per-pixel test would.
 //
 // The exponent is evaluated as exp2 of a conic pre-scaled by -log2(e)/2
 // (resp. -log2(e)) with explicitly rounded operations, so the forward and the
@@ -33,11 +39,11 @@ __device__ __forceinline__ int find_view(const ViewSet& VS, uint32_t tile) {
 }
 
 // Shared-memory form of a record: a = (u, v, A', B'), b = (C', alpha_eff, R, G),
-// c = B, with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
-__device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float& sc) {
+// c = (B, radius), with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
+__device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float2& sc) {
     sa = make_float4(r.r0.x, r.r0.y, __fmul_rn(-0.5f * kLog2e, r.r0.z), __fmul_rn(-kLog2e, r.r0.w));
     sb = make_float4(__fmul_rn(-0.5f * kLog2e, r.r1.x), r.r1.y, r.r1.z, r.r1.w);
-    sc = r.r2.x;
+    sc = make_float2(r.r2.x, r.r2.z);
 }
 
 // log2 of the Gaussian factor at (dx, dy): A' dx^2 + C' dy^2 + B' dx dy
@@ -45,20 +51,35 @@ __device__ __forceinline__ float power2(float A, float B, float C, float dx, flo
     return __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(B, dx), dy)));
 }
 
-// Pixels of thread `tid` in a TS x TS tile whose top-left pixel is (x0, y0).
+// Pixel layout of a TS x TS tile: warp w owns a region of RW x RH pixels
+// (2 regions across, 4 down); lane l owns an S x S block inside it.
 template <int TS>
 struct TilePixels {
     static constexpr int P = TS * TS / kTilePix;  // pixels per thread: 1 or 4
+    static constexpr int S = TS / 16;             // block side per thread: 1 or 2
+    static constexpr int RW = TS / 2, RH = TS / 4;
+    __device__ __forceinline__ static void region(int tid, int x0, int y0, int& rx, int& ry) {
+        const int w = tid >> 5;
+        rx = x0 + (w & 1) * RW;
+        ry = y0 + (w >> 1) * RH;
+    }
     __device__ __forceinline__ static void coords(int tid, int x0, int y0, int k, int& px, int& py) {
-        if (TS == 16) {
-            px = x0 + (tid & 15);
-            py = y0 + (tid >> 4);
-        } else {  // 2x2 block per thread; a warp covers a 32x4 strip
-            px = x0 + 2 * (tid & 15) + (k & 1);
-            py = y0 + 2 * (tid >> 4) + (k >> 1);
-        }
+        int rx, ry;
+        region(tid, x0, y0, rx, ry);
+        const int l = tid & 31;
+        px = rx + S * (l & 7) + (S == 2 ? (k & 1) : 0);
+        py = ry + S * (l >> 3) + (S == 2 ? (k >> 1) : 0);
     }
 };
+
+// True when the disk of radius r around (u, v) reaches the pixel-centre box
+// [rx, rx + RW - 1] x [ry, ry + RH - 1].
+template <int RW, int RH>
+__device__ __forceinline__ bool disk_meets_region(float u, float v, float r, float rx, float ry) {
+    const float ex = fmaxf(fmaxf(rx - u, u - (rx + (float)(RW - 1))), 0.0f);
+    const float ey = fmaxf(fmaxf(ry - v, v - (ry + (float)(RH - 1))), 0.0f);
+    return ex * ex + ey * ey <= r * r;
+}
 
 template <int TS>
 __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
@@ -67,10 +88,11 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                                                               const SplatRecord* __restrict__ rec, uint32_t n_splats,
                                                               float* __restrict__ image, float* __restrict__ final_T,
                                                               int32_t* __restrict__ n_last) {
-    constexpr int P = TilePixels<TS>::P;
+    using TP = TilePixels<TS>;
+    constexpr int P = TP::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
-    __shared__ float s_c[kTilePix];
+    __shared__ float2 s_c[kTilePix];
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
@@ -78,6 +100,9 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
+    int irx, iry;
+    TP::region(tid, tx * TS, ty * TS, irx, iry);
+    const float frx = (float)irx, fry = (float)iry;
     float fpx[P], fpy[P], T[P], C0[P], C1[P], C2[P];
     int32_t last[P];
     bool pdone[P], inside[P];
@@ -85,7 +110,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
 #pragma unroll
     for (int k = 0; k < P; k++) {
         int px, py;
-        TilePixels<TS>::coords(tid, tx * TS, ty * TS, k, px, py);
+        TP::coords(tid, tx * TS, ty * TS, k, px, py);
         inside[k] = px < V.width && py < V.height;
         fpx[k] = (float)px;
         fpy[k] = (float)py;
@@ -102,16 +127,18 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
                 stage_record(rec[sid], s_a[tid], s_b[tid], s_c[tid]);
-            } else {  // never produced by bin_sort; an invisible splat keeps the access in bounds
+            } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
                 s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
                 s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_c[tid] = 0.f;
+                s_c[tid] = make_float2(0.f, -1.f);
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kTilePix, range.y - base);
         for (int j = 0; j < cnt && !done; j++) {
             const float4 a = s_a[j];
+            const float2 c = s_c[j];
+            if (!disk_meets_region<TP::RW, TP::RH>(a.x, a.y, c.y, frx, fry)) continue;  // warp-uniform
             const float4 b = s_b[j];
             const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
 #pragma unroll
@@ -131,7 +158,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                 const float w = alpha * T[k];
                 C0[k] = fmaf(b.z, w, C0[k]);
                 C1[k] = fmaf(b.w, w, C1[k]);
-                C2[k] = fmaf(s_c[j], w, C2[k]);
+                C2[k] = fmaf(c.x, w, C2[k]);
                 T[k] = Tn;
                 last[k] = pos1;
             }
@@ -184,15 +211,17 @@ __device__ __forceinline__ float warp_reduce8(const float (&v)[8], int lane) {
 constexpr int kGradStride = 12;  // floats per staged splat in the shared gradient accumulator
 
 template <int TS>
-__global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
+__global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
     const __grid_constant__ ViewSet VS, const DevOpts O, const uint2* __restrict__ ranges,
     const uint32_t* __restrict__ pair_vals, const SplatRecord* __restrict__ rec, uint32_t n_splats,
     const float* __restrict__ final_T, const int32_t* __restrict__ n_last, const float* __restrict__ dL_dimage,
     float4* __restrict__ grad2d) {
-    constexpr int P = TilePixels<TS>::P;
+    using TP = TilePixels<TS>;
+    constexpr int P = TP::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
     __shared__ float4 s_n[kTilePix];  // natural conic (a, b, c) and B
+    __shared__ float s_r[kTilePix];   // support radius
     __shared__ uint32_t s_sid[kTilePix];
     __shared__ __align__(16) float s_g[kTilePix * kGradStride];
     __shared__ int s_max;
@@ -203,15 +232,21 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
+    int irx, iry;
+    TP::region(tid, tx * TS, ty * TS, irx, iry);
+    const float frx = (float)irx, fry = (float)iry;
     const size_t npix = (size_t)V.width * V.height;
     const float* gimg = dL_dimage + 3 * (size_t)V.pix_base;
-    float fpx[P], fpy[P], T[P], dC0[P], dC1[P], dC2[P], acc0[P], acc1[P], acc2[P];
+    // Per pixel: T (recovered back to front), dL/dC, and S = dL/dC . acc where
+    // acc = sum_{j > i} c_j alpha_j T_j + T_final bg is built back to front, so
+    // that dL/dalpha_i = T_i (dL/dC . c_i) - S / (1 - alpha_i).
+    float fpx[P], fpy[P], T[P], dC0[P], dC1[P], dC2[P], Sacc[P];
     int32_t last[P];
     int my_max = 0;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         int px, py;
-        TilePixels<TS>::coords(tid, tx * TS, ty * TS, k, px, py);
+        TP::coords(tid, tx * TS, ty * TS, k, px, py);
         fpx[k] = (float)px;
         fpy[k] = (float)py;
         T[k] = 1.0f;
@@ -225,17 +260,15 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
             dC1[k] = gimg[npix + p];
             dC2[k] = gimg[2 * npix + p];
         }
-        // acc = sum_{j > i} c_j alpha_j T_j + T_final bg, built back to front
-        acc0[k] = T[k] * V.bg[0];
-        acc1[k] = T[k] * V.bg[1];
-        acc2[k] = T[k] * V.bg[2];
+        Sacc[k] = T[k] * (dC0[k] * V.bg[0] + dC1[k] * V.bg[1] + dC2[k] * V.bg[2]);
         my_max = max(my_max, last[k]);
     }
+    const int warp_last = __reduce_max_sync(0xffffffffu, my_max);  // positions >= this: nothing in this warp
     if (tid == 0) s_max = 0;
 #pragma unroll
     for (int k = 0; k < kGradStride; k++) s_g[tid * kGradStride + k] = 0.0f;
     __syncthreads();
-    atomicMax(&s_max, my_max);
+    if (lane == 0) atomicMax(&s_max, warp_last);
     __syncthreads();
     const int max_last = min(s_max, (int)(range.y - range.x));
     for (int end = max_last; end > 0; end -= kTilePix) {
@@ -246,18 +279,21 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
             uint32_t sid = pair_vals[idx];
             if (sid >= n_splats) sid = 0;  // never produced by bin_sort; keeps the access in bounds
             const SplatRecord r = rec[sid];
-            float sc;
+            float2 sc;
             stage_record(r, s_a[tid], s_b[tid], sc);
-            s_n[tid] = make_float4(r.r0.z, r.r0.w, r.r1.x, sc);
+            s_n[tid] = make_float4(r.r0.z, r.r0.w, r.r1.x, sc.x);
+            s_r[tid] = sc.y;
             s_sid[tid] = sid;
         }
         __syncthreads();
         for (int j = 0; j < cnt; j++) {
             const int pos = end - 1 - j;  // 0-based position in the tile list
+            if (pos >= warp_last) continue;  // warp-uniform
+            const float4 a = s_a[j];
+            if (!disk_meets_region<TP::RW, TP::RH>(a.x, a.y, s_r[j], frx, fry)) continue;  // warp-uniform
             float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // u v a b c alpha_eff R G
             float g_bl = 0.0f;
             bool contrib = false;
-            const float4 a = s_a[j];
             const float4 b = s_b[j];
 #pragma unroll
             for (int k = 0; k < P; k++) {
@@ -271,18 +307,15 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(
                 if (alpha < O.alpha_min) continue;
                 contrib = true;
                 const float4 nc = s_n[j];
-                const float inv_om = 1.0f / (1.0f - alpha);
+                const float inv_om = __frcp_rn(1.0f - alpha);
                 const float Ti = T[k] * inv_om;  // transmittance before this splat
-                const float cr = b.z, cg = b.w, cb = nc.w;
-                const float dalpha = dC0[k] * (cr * Ti - acc0[k] * inv_om) + dC1[k] * (cg * Ti - acc1[k] * inv_om) +
-                                     dC2[k] * (cb * Ti - acc2[k] * inv_om);
+                const float dCc = fmaf(dC0[k], b.z, fmaf(dC1[k], b.w, dC2[k] * nc.w));
+                const float dalpha = fmaf(Ti, dCc, -Sacc[k] * inv_om);
                 const float w = alpha * Ti;
                 gv[6] = fmaf(dC0[k], w, gv[6]);
                 gv[7] = fmaf(dC1[k], w, gv[7]);
                 g_bl = fmaf(dC2[k], w, g_bl);
-                acc0[k] = fmaf(cr, w, acc0[k]);
-                acc1[k] = fmaf(cg, w, acc1[k]);
-                acc2[k] = fmaf(cb, w, acc2[k]);
+                Sacc[k] = fmaf(w, dCc, Sacc[k]);
                 T[k] = Ti;
                 if (!(araw > O.alpha_max)) {
                     gv[5] = fmaf(dalpha, G, gv[5]);
