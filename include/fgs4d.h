@@ -199,7 +199,8 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians *g, const fgs4d_view *v
 /* Byte offsets of the state's sections, for inspection and tests.
    records: one per (view v, Gaussian g) at index v*n + g, record_bytes each
    (FP32 layout: float u, v, conic a, b, c, alpha_eff, R, G, B, depth,
-   radius, uint32 flags); tiles_touched: uint32 per (v, g), 0 = culled;
+   hx, hy, where outside |x - u| <= hx, |y - v| <= hy the splat's alpha is
+   below alpha_min); tiles_touched: uint32 per (v, g), 0 = culled;
    ranges: uint32 pairs [start, end) per global tile (tiles of view v follow
    those of views < v, row-major); pair_vals: uint32 splat index v*n + g per
    list entry, in the buffer that holds the sorted lists. */

@@ -387,11 +387,11 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             const uint32_t v = sid / n_gauss;
             const DevView& V = VS.v[v];
             const float4 r0 = rec[sid].r0;
-            const float radius = rec[sid].r2.z;
-            const float fx0 = fmaxf(ceilf(r0.x - radius), 0.0f);
-            const float fx1 = fminf(floorf(r0.x + radius), (float)(V.width - 1));
-            const float fy0 = fmaxf(ceilf(r0.y - radius), 0.0f);
-            const float fy1 = fminf(floorf(r0.y + radius), (float)(V.height - 1));
+            const float4 r2 = rec[sid].r2;  // (B, depth, hx, hy): support box half extents
+            const float fx0 = fmaxf(ceilf(r0.x - r2.z), 0.0f);
+            const float fx1 = fminf(floorf(r0.x + r2.z), (float)(V.width - 1));
+            const float fy0 = fmaxf(ceilf(r0.y - r2.w), 0.0f);
+            const float fy1 = fminf(floorf(r0.y + r2.w), (float)(V.height - 1));
             const int ix0 = (int)fx0 / tile, ix1 = (int)fx1 / tile, iy0 = (int)fy0 / tile, iy1 = (int)fy1 / tile;
             x0 = (uint32_t)ix0;
             y0 = (uint32_t)iy0;

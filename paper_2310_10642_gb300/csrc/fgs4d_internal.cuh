@@ -92,7 +92,7 @@ constexpr int kMaxDigits = 512;  // radix digits of at most 9 bits
 
 // Splat record (FP32): 48 bytes, three 16-byte vectors.
 //   r0 = (u, v, conic_a, conic_b)   r1 = (conic_c, alpha_eff, R, G)
-//   r2 = (B, depth, radius, flags)  flags bit ch: colour channel ch clamped
+//   r2 = (B, depth, hx, hy)         half extents of the support box
 struct __align__(16) SplatRecord {
     float4 r0, r1, r2;
 };
@@ -340,7 +340,7 @@ struct ViewGeom {
     float conic[3];  // (a, b, c)
     float u, v;
     float alpha_eff;
-    float radius;
+    float hx, hy;    // half extents of the support box (pixels)
     int rect[4];     // inclusive tile rect: x0, y0, x1, y1
     int tiles;       // number of touched tiles (0 = invisible)
 };
@@ -381,7 +381,7 @@ __device__ __forceinline__ void slice_view(const Core& c, const DevView& V, cons
     }
 }
 
-// Camera transform, Jacobian, 2D covariance, conic, radius and tile rect.
+// Camera transform, Jacobian, 2D covariance, conic, support box and tile rect.
 // Returns false when the splat is culled (near plane, alpha_eff, empty rect).
 __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, const DevOpts& O, ViewGeom& w,
                                              bool allow_f64) {
@@ -453,16 +453,17 @@ __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, co
     }
     w.alpha_eff = c.alpha * w.p;
     if (!(w.alpha_eff >= O.alpha_min)) return false;
-    // support radius: beyond it alpha_eff * G < alpha_min (plus half a pixel margin)
-    const float mid = 0.5f * (w.cov[0] + w.cov[2]);
-    const float lmax = mid + sqrtf(fmaxf(mid * mid - det, 0.0f));
-    const float lnr = fmaxf(logf(w.alpha_eff) - O.ln_alpha_min, 0.0f);
-    w.radius = sqrtf(2.0f * lnr * lmax) + 0.5f;
-    // pixels i with |i - u| <= r, clamped to the image; tiles containing them
-    const float fx0 = fmaxf(ceilf(w.u - w.radius), 0.0f);
-    const float fx1 = fminf(floorf(w.u + w.radius), (float)(V.width - 1));
-    const float fy0 = fmaxf(ceilf(w.v - w.radius), 0.0f);
-    const float fy1 = fminf(floorf(w.v + w.radius), (float)(V.height - 1));
+    // Support box: alpha_eff * G >= alpha_min needs d^T Sigma2d^-1 d <= 2 ln(alpha_eff /
+    // alpha_min) =: k, and d^T Sigma2d^-1 d >= dx^2 / Sigma2d_00 (Cauchy-Schwarz), so
+    // |dx| <= sqrt(k Sigma2d_00) and |dy| <= sqrt(k Sigma2d_11), plus half a pixel margin.
+    const float k2 = 2.0f * fmaxf(logf(w.alpha_eff) - O.ln_alpha_min, 0.0f);
+    w.hx = sqrtf(k2 * w.cov[0]) + 0.5f;
+    w.hy = sqrtf(k2 * w.cov[2]) + 0.5f;
+    // pixels i with |i - u| <= hx, j with |j - v| <= hy, clamped to the image; tiles containing them
+    const float fx0 = fmaxf(ceilf(w.u - w.hx), 0.0f);
+    const float fx1 = fminf(floorf(w.u + w.hx), (float)(V.width - 1));
+    const float fy0 = fmaxf(ceilf(w.v - w.hy), 0.0f);
+    const float fy1 = fminf(floorf(w.v + w.hy), (float)(V.height - 1));
     if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
     w.rect[0] = (int)fx0 / O.tile;
     w.rect[1] = (int)fy0 / O.tile;

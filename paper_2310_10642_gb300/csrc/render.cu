@@ -15,11 +15,11 @@
 //   skip if power > 0; alpha = min(alpha_max, alpha_eff * exp(power));
 //   skip if alpha < alpha_min; stop (splat excluded) if T (1 - alpha) < T_min;
 //   C += c alpha T; T *= 1 - alpha.  Finally C += T bg.
-// alpha_eff = sigmoid(logit) p(t) carries the marginal of Eq. 6.  Beyond the
-// support radius r of a splat alpha < alpha_min holds by construction (the
-// radius bounds alpha_eff exp(-|d|^2 / (2 lambda_max)) with half a pixel to
-// spare), so skipping a region that lies entirely beyond r takes the same
-// decision the per-pixel test would.
+// alpha_eff = sigmoid(logit) p(t) carries the marginal of Eq. 6.  Outside the
+// support box |dx| <= hx, |dy| <= hy of a splat alpha < alpha_min holds by
+// construction (the box bounds the ellipse alpha_eff G >= alpha_min with half
+// a pixel to spare), so skipping a region that lies entirely outside the box
+// takes the same decision the per-pixel test would.
 //
 // The exponent is evaluated as exp2 of a conic pre-scaled by -log2(e)/2
 // (resp. -log2(e)) with explicitly rounded operations, so the forward and the
@@ -39,11 +39,11 @@ __device__ __forceinline__ int find_view(const ViewSet& VS, uint32_t tile) {
 }
 
 // Shared-memory form of a record: a = (u, v, A', B'), b = (C', alpha_eff, R, G),
-// c = (B, radius), with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
-__device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float2& sc) {
+// c = (B, hx, hy, 0), with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
+__device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float4& sc) {
     sa = make_float4(r.r0.x, r.r0.y, __fmul_rn(-0.5f * kLog2e, r.r0.z), __fmul_rn(-kLog2e, r.r0.w));
     sb = make_float4(__fmul_rn(-0.5f * kLog2e, r.r1.x), r.r1.y, r.r1.z, r.r1.w);
-    sc = make_float2(r.r2.x, r.r2.z);
+    sc = make_float4(r.r2.x, r.r2.z, r.r2.w, 0.0f);
 }
 
 // log2 of the Gaussian factor at (dx, dy): A' dx^2 + C' dy^2 + B' dx dy
@@ -72,13 +72,11 @@ struct TilePixels {
     }
 };
 
-// True when the disk of radius r around (u, v) reaches the pixel-centre box
-// [rx, rx + RW - 1] x [ry, ry + RH - 1].
+// True when the support box [u - hx, u + hx] x [v - hy, v + hy] reaches the
+// pixel-centre box [rx, rx + RW - 1] x [ry, ry + RH - 1].
 template <int RW, int RH>
-__device__ __forceinline__ bool disk_meets_region(float u, float v, float r, float rx, float ry) {
-    const float ex = fmaxf(fmaxf(rx - u, u - (rx + (float)(RW - 1))), 0.0f);
-    const float ey = fmaxf(fmaxf(ry - v, v - (ry + (float)(RH - 1))), 0.0f);
-    return ex * ex + ey * ey <= r * r;
+__device__ __forceinline__ bool box_meets_region(float u, float v, float hx, float hy, float rx, float ry) {
+    return (u + hx >= rx) && (u - hx <= rx + (float)(RW - 1)) && (v + hy >= ry) && (v - hy <= ry + (float)(RH - 1));
 }
 
 template <int TS>
@@ -92,7 +90,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
     constexpr int P = TP::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
-    __shared__ float2 s_c[kTilePix];
+    __shared__ float4 s_c[kTilePix];
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
@@ -130,15 +128,15 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
             } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
                 s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
                 s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_c[tid] = make_float2(0.f, -1.f);
+                s_c[tid] = make_float4(0.f, -1.f, -1.f, 0.f);
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)kTilePix, range.y - base);
         for (int j = 0; j < cnt && !done; j++) {
             const float4 a = s_a[j];
-            const float2 c = s_c[j];
-            if (!disk_meets_region<TP::RW, TP::RH>(a.x, a.y, c.y, frx, fry)) continue;  // warp-uniform
+            const float4 c = s_c[j];
+            if (!box_meets_region<TP::RW, TP::RH>(a.x, a.y, c.y, c.z, frx, fry)) continue;  // warp-uniform
             const float4 b = s_b[j];
             const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
 #pragma unroll
@@ -221,7 +219,7 @@ __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
     __shared__ float4 s_n[kTilePix];  // natural conic (a, b, c) and B
-    __shared__ float s_r[kTilePix];   // support radius
+    __shared__ float2 s_r[kTilePix];  // support box half extents
     __shared__ uint32_t s_sid[kTilePix];
     __shared__ __align__(16) float s_g[kTilePix * kGradStride];
     __shared__ int s_max;
@@ -279,10 +277,10 @@ __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
             uint32_t sid = pair_vals[idx];
             if (sid >= n_splats) sid = 0;  // never produced by bin_sort; keeps the access in bounds
             const SplatRecord r = rec[sid];
-            float2 sc;
+            float4 sc;
             stage_record(r, s_a[tid], s_b[tid], sc);
             s_n[tid] = make_float4(r.r0.z, r.r0.w, r.r1.x, sc.x);
-            s_r[tid] = sc.y;
+            s_r[tid] = make_float2(sc.y, sc.z);
             s_sid[tid] = sid;
         }
         __syncthreads();
@@ -290,7 +288,8 @@ __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
             const int pos = end - 1 - j;  // 0-based position in the tile list
             if (pos >= warp_last) continue;  // warp-uniform
             const float4 a = s_a[j];
-            if (!disk_meets_region<TP::RW, TP::RH>(a.x, a.y, s_r[j], frx, fry)) continue;  // warp-uniform
+            const float2 hb = s_r[j];
+            if (!box_meets_region<TP::RW, TP::RH>(a.x, a.y, hb.x, hb.y, frx, fry)) continue;  // warp-uniform
             float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // u v a b c alpha_eff R G
             float g_bl = 0.0f;
             bool contrib = false;

@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
         for (int v = 0; v < VS.n; v++) tiles_touched[(size_t)v * n + g] = 0u;
         return;
     }
-    uint32_t n_vis = 0;
     for (int v = 0; v < VS.n; v++) {
         const DevView& V = VS.v[v];
         const size_t idx = (size_t)v * n + g;
@@ -66,24 +65,17 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
         }
         float raw[3];
         color_forward<L>(G, g, w, V, raw);
-        uint32_t flags = 0;
         float col[3];
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            const float x = raw[ch] + 0.5f;
-            flags |= (x > 0.0f) ? 0u : (1u << ch);
-            col[ch] = fmaxf(x, 0.0f);
-        }
+        for (int ch = 0; ch < 3; ch++) col[ch] = fmaxf(raw[ch] + 0.5f, 0.0f);
         SplatRecord r;
         r.r0 = make_float4(w.u, w.v, w.conic[0], w.conic[1]);
         r.r1 = make_float4(w.conic[2], w.alpha_eff, col[0], col[1]);
-        r.r2 = make_float4(col[2], w.xc[2], w.radius, __uint_as_float(flags));
+        r.r2 = make_float4(col[2], w.xc[2], w.hx, w.hy);
         rec[idx] = r;
         tiles_touched[idx] = (uint32_t)w.tiles;
         depth_key[idx] = __float_as_uint(w.xc[2]);
-        n_vis++;
     }
-    (void)n_vis;
 }
 
 // ---------------------------------------------------------------------------

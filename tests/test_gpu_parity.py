@@ -121,9 +121,13 @@ def test_slice_project_records_match_oracle():
         border = ref["borderline"] == 1
         # GPU-visible but oracle-culled only for borderline decisions
         assert np.all(border[vis_g & ~vis_o])
-        # oracle-visible but GPU-culled: borderline, or the support disk misses the image
-        miss = ((ref["u"] + ref["radius"] < -0.4) | (ref["u"] - ref["radius"] > v["width"] - 0.6) |
-                (ref["v"] + ref["radius"] < -0.4) | (ref["v"] - ref["radius"] > v["height"] - 0.6))
+        # oracle-visible but GPU-culled: borderline, or the support box (the bounding box
+        # of alpha_eff G >= alpha_min) misses the image
+        k2 = 2.0 * np.log(np.maximum(ref["alpha_eff"] * 255.0, 1.0))
+        hx = np.sqrt(k2 * ref["cov2d"][:, 0]) if n else np.zeros(0)
+        hy = np.sqrt(k2 * ref["cov2d"][:, 2]) if n else np.zeros(0)
+        miss = ((ref["u"] + hx < -0.4) | (ref["u"] - hx > v["width"] - 0.6) |
+                (ref["v"] + hy < -0.4) | (ref["v"] - hy > v["height"] - 0.6))
         assert np.all((border | miss)[vis_o & ~vis_g])
         both = vis_g & vis_o
         assert both.sum() > 50
@@ -156,11 +160,11 @@ def test_tile_lists_are_depth_ordered_and_complete(tile):
         tx_n = (v["width"] + tile - 1) // tile
         for g in np.nonzero(tiles[vi * n:(vi + 1) * n])[0]:
             sid = vi * n + g
-            u, vv, rad = rec[sid, 0], rec[sid, 1], rec[sid, 10]
-            x0 = max(math.ceil(u - rad), 0) // tile
-            x1 = min(math.floor(u + rad), v["width"] - 1) // tile
-            y0 = max(math.ceil(vv - rad), 0) // tile
-            y1 = min(math.floor(vv + rad), v["height"] - 1) // tile
+            u, vv, hx, hy = rec[sid, 0], rec[sid, 1], rec[sid, 10], rec[sid, 11]
+            x0 = max(math.ceil(u - hx), 0) // tile
+            x1 = min(math.floor(u + hx), v["width"] - 1) // tile
+            y0 = max(math.ceil(vv - hy), 0) // tile
+            y1 = min(math.floor(vv + hy), v["height"] - 1) // tile
             assert (x1 - x0 + 1) * (y1 - y0 + 1) == tiles[sid]
             for ty in range(y0, y1 + 1):
                 for tx in range(x0, x1 + 1):
