@@ -509,7 +509,7 @@ cudaError_t launch_render_backward_into(const ViewSet& VS, const DevOpts& O, con
                                         int pair_buf, const float* final_T, const int32_t* n_last,
                                         const float* dL_dimage, float4* g2, cudaStream_t st);
 cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
-                                         const StateLayout& lay, char* state, const float4* g2,
+                                         const StateLayout& lay, char* state, float4* g2,
                                          const fgs4d_gaussian_grads& grads, cudaStream_t st);
 
 // Host-side count of kernel launches issued by this library (all threads).

@@ -83,18 +83,19 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
 // ---------------------------------------------------------------------------
 constexpr int kBwdThreads = 128;
 
+// Geometry part of the adjoint.  For every visible splat it also replaces the
+// splat's 2D-gradient slot by its colour cotangent, read by sh_backward_kernel:
+//   slot[0] = (view direction d, dt),  slot[1] = (dL/draw_R, dL/draw_G, dL/draw_B, 0)
+// where dL/draw is dL/dcolour with the colour clamp max(raw + 0.5, 0) applied.
 template <int L>
-__global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
+__global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
     const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, const uint32_t* __restrict__ tiles_touched,
-    const float4* __restrict__ grad2d, const fgs4d_gaussian_grads out) {
+    float4* __restrict__ grad2d, const fgs4d_gaussian_grads out) {
     constexpr int NB = (L + 1) * (L + 1);
-    extern __shared__ float s_acc[];  // [rows][kBwdThreads]
     const int tid = threadIdx.x;
     const int g = blockIdx.x * blockDim.x + tid;
     if (g >= G.n) return;
     const size_t n = (size_t)G.n;
-    const int rows = 3 * NB * (G.K + 1);
-    for (int r = 0; r < rows; r++) s_acc[r * kBwdThreads + tid] = 0.0f;
 
     Core c;
     load_core(G, g, c);
@@ -113,7 +114,10 @@ __global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
             const DevView& V = VS.v[v];
             ViewGeom w;
             slice_view(c, V, O, G, g, w, true);
-            if (!project_view(c, V, O, w, true)) continue;
+            if (!project_view(c, V, O, w, true)) {  // cannot happen for a binned splat; keep the slot defined
+                grad2d[3 * idx + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
+            }
             const float4 q0 = grad2d[3 * idx + 0];
             const float4 q1 = grad2d[3 * idx + 1];
             const float4 q2 = grad2d[3 * idx + 2];
@@ -130,6 +134,7 @@ __global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
 #pragma unroll
             for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
             float ddt = 0.0f;
+            float graws[3];
             for (int ch = 0; ch < 3; ch++) {
                 float P[16];
 #pragma unroll
@@ -153,18 +158,16 @@ __global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
 #pragma unroll
                 for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
                 const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
+                graws[ch] = graw;
                 if (graw != 0.0f) {
 #pragma unroll
                     for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
                     ddt = fmaf(graw, Q, ddt);
-                    for (int f = 0; f <= G.K; f++) {
-                        const float cf = cospif(2.0f * (float)f * w.dt * G.inv_period);
-                        const float gc = graw * cf;
-#pragma unroll
-                        for (int j = 0; j < NB; j++) s_acc[((f * NB + j) * 3 + ch) * kBwdThreads + tid] += gc * Y[j];
-                    }
                 }
             }
+            // colour cotangent for the coefficient gradients (sh_backward_kernel)
+            grad2d[3 * idx + 0] = make_float4(d[0], d[1], d[2], w.dt);
+            grad2d[3 * idx + 1] = make_float4(graws[0], graws[1], graws[2], 0.0f);
             float gd[3];
             sh_grad(L, d[0], d[1], d[2], wsum, gd[0], gd[1], gd[2]);
             const float gdd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
@@ -336,7 +339,46 @@ __global__ void __launch_bounds__(kBwdThreads) project_backward_kernel(
     }
     out.opacity_logit[g] = glogit;
     if (out.mean2d_abs) out.mean2d_abs[g] = m2d;
-    for (int r = 0; r < rows; r++) out.shs[(size_t)r * n + g] = s_acc[r * kBwdThreads + tid];
+}
+
+// Coefficient part of the adjoint (Eq. 11): dL/dk[f][j][ch] = sum over the
+// visible views of dL/draw_ch cos(2 pi f dt / T) Y_j(d), from the colour
+// cotangents left by project_backward_kernel.  One thread per (Gaussian,
+// channel) keeps the (K+1) (L+1)^2 sums in registers; consecutive threads take
+// consecutive Gaussians, so every load and store is coalesced.
+template <int L, int K1>
+__global__ void __launch_bounds__(256) sh_backward_kernel(int n, int n_views, float inv_period,
+                                                          const uint32_t* __restrict__ tiles_touched,
+                                                          const float4* __restrict__ grad2d, float* __restrict__ gshs) {
+    constexpr int NB = (L + 1) * (L + 1);
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.y;
+    if (g >= n) return;
+    float acc[K1][NB];
+#pragma unroll
+    for (int f = 0; f < K1; f++)
+#pragma unroll
+        for (int j = 0; j < NB; j++) acc[f][j] = 0.0f;
+    for (int v = 0; v < n_views; v++) {
+        const size_t idx = (size_t)v * n + g;
+        if (tiles_touched[idx] == 0u) continue;
+        const float4 gr = grad2d[3 * idx + 1];
+        const float graw = ch == 0 ? gr.x : (ch == 1 ? gr.y : gr.z);
+        if (graw == 0.0f) continue;
+        const float4 dd = grad2d[3 * idx + 0];
+        float Y[16];
+        sh_eval(L, dd.x, dd.y, dd.z, Y);
+#pragma unroll
+        for (int f = 0; f < K1; f++) {
+            const float gc = graw * cospif(2.0f * (float)f * dd.w * inv_period);
+#pragma unroll
+            for (int j = 0; j < NB; j++) acc[f][j] = fmaf(gc, Y[j], acc[f][j]);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < K1; f++)
+#pragma unroll
+        for (int j = 0; j < NB; j++) gshs[(size_t)((f * NB + j) * 3 + ch) * n + g] = acc[f][j];
 }
 
 // ---------------------------------------------------------------------------
@@ -372,17 +414,32 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
     return cudaGetLastError();
 }
 
+template <int L, int K1>
+static void launch_sh(const DevGauss& G, int n_views, const uint32_t* tt, const float4* g2, float* gshs,
+                      cudaStream_t st) {
+    const dim3 grid((G.n + 255) / 256, 3);
+    sh_backward_kernel<L, K1><<<grid, 256, 0, st>>>(G.n, n_views, G.inv_period, tt, g2, gshs);
+}
+
+template <int L>
+static void launch_sh_k(const DevGauss& G, int n_views, const uint32_t* tt, const float4* g2, float* gshs,
+                        cudaStream_t st) {
+    switch (G.K) {
+        case 0: launch_sh<L, 1>(G, n_views, tt, g2, gshs, st); break;
+        case 1: launch_sh<L, 2>(G, n_views, tt, g2, gshs, st); break;
+        case 2: launch_sh<L, 3>(G, n_views, tt, g2, gshs, st); break;
+        case 3: launch_sh<L, 4>(G, n_views, tt, g2, gshs, st); break;
+        default: launch_sh<L, 5>(G, n_views, tt, g2, gshs, st); break;
+    }
+}
+
 template <int L>
 static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
-                            const float4* g2, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
-    const int rows = 3 * (L + 1) * (L + 1) * (G.K + 1);
-    const size_t smem = (size_t)rows * kBwdThreads * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(project_backward_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+                            float4* g2, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     const int blocks = (G.n + kBwdThreads - 1) / kBwdThreads;
-    project_backward_kernel<L><<<blocks, kBwdThreads, smem, st>>>(G, VS, O, tt, g2, grads);
-    count_launches(1);
+    project_backward_kernel<L><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, tt, g2, grads);
+    launch_sh_k<L>(G, VS.n, tt, g2, grads.shs, st);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -390,7 +447,7 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
                                     char* state, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
-    auto* g2 = reinterpret_cast<const float4*>(state + lay.grad2d);
+    auto* g2 = reinterpret_cast<float4*>(state + lay.grad2d);
     switch (G.L) {
         case 0: return launch_pb<0>(G, VS, O, tt, g2, grads, st);
         case 1: return launch_pb<1>(G, VS, O, tt, g2, grads, st);
@@ -402,7 +459,7 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
 // Same as launch_project_backward, reading the per-splat 2D gradient from g2
 // instead of the state (used by the allocation-free backward entry point).
 cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
-                                         const StateLayout& lay, char* state, const float4* g2,
+                                         const StateLayout& lay, char* state, float4* g2,
                                          const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
