@@ -224,7 +224,7 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view *views, int n_views,
    Same arguments, results and tolerance as fgs4d_render_backward; the
    forward state is read as input but its per-splat gradient section is not
    used.  That scratch (48 bytes per (view, Gaussian) splat) lives instead in
-   a static device array of the library, 12 MiB, which every GPU that loads
+   a static device array of the library, 13 MiB, which every GPU that loads
    the library holds until the process exits:
    - n * n_views above FGS4D_NOALLOC_MAX_SPLATS returns FGS4D_ERR_CAPACITY
      before anything is enqueued;

@@ -390,16 +390,20 @@ fgs4d_status fgs4d_read_counters(const void* state, fgs4d_counters* out, fgs4d_s
 // pass: code running while its stream is being captured into a CUDA graph,
 // real-time render loops that reserve every byte of device memory once at
 // start-up and forbid later allocations, and plugins hosted by an engine
-// that owns the device allocator.  This entry point keeps its only scratch,
-// the per-splat 2D gradient (three float4 per (view, Gaussian) splat), in a
-// static device array of this library instead of the caller's state.  The
-// state from the forward pass is read as input; its gradient section is not
-// used.  The array holds FGS4D_NOALLOC_MAX_SPLATS splats (12 MiB) and every
-// GPU that loads this library keeps it until the process exits.
+// that owns the device allocator.  This entry point keeps its scratch -- the
+// per-splat 2D gradient (three float4 per (view, Gaussian) splat), the list
+// of visible splats (one word per splat), its length and the scan's block
+// sums -- in a static device array of this library instead of the caller's
+// state.  The state from the forward pass is only read.  The array holds
+// FGS4D_NOALLOC_MAX_SPLATS splats (13 MiB) and every GPU that loads this
+// library keeps it until the process exits.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
-static __device__ __align__(256) float4 g_noalloc_grad2d[3 * (size_t)FGS4D_NOALLOC_MAX_SPLATS];
+constexpr size_t kNoallocGrad = 3 * (size_t)FGS4D_NOALLOC_MAX_SPLATS;   // float4: 2D gradients
+constexpr size_t kNoallocList = (size_t)FGS4D_NOALLOC_MAX_SPLATS / 4;   // float4: splat list words
+constexpr size_t kNoallocMisc = (kScanBlocksMax + 32 + 16) / 4;          // float4: scan sums, list length
+static __device__ __align__(256) float4 g_noalloc_grad2d[kNoallocGrad + kNoallocList + kNoallocMisc];
 
 namespace {
 
@@ -453,8 +457,11 @@ extern "C" fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians* g, 
         if (e == cudaSuccess)
             e = launch_render_backward_into(P->VS, P->O, P->L, st, pair_buffer(*P), final_T, n_last, dL_dimage, g2,
                                             (cudaStream_t)stream);
+        uint32_t* list = reinterpret_cast<uint32_t*>(g2 + kNoallocGrad);
+        uint32_t* misc = reinterpret_cast<uint32_t*>(g2 + kNoallocGrad + kNoallocList);
         if (e == cudaSuccess)
-            e = launch_project_backward_from(G, P->VS, P->O, P->L, st, g2, *grads, (cudaStream_t)stream);
+            e = launch_project_backward_from(G, P->VS, P->O, P->L, st, g2, list, misc + kScanBlocksMax + 32, misc,
+                                             *grads, (cudaStream_t)stream);
         s = cuda_status(e);
     }
     delete P;

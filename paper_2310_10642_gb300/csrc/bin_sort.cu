@@ -446,6 +446,29 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __rest
 
 static int grid_cap(uint32_t want, int cap) { return (int)(want < (uint32_t)cap ? (want > 0 ? want : 1) : (uint32_t)cap); }
 
+// Visible splats in Gaussian-major order (g, then view): i' = g V + v.
+struct LoadVisibleGV {
+    const uint32_t* tiles;
+    uint32_t n, V;
+    __device__ uint32_t operator()(uint32_t i) const { return tiles[(i % V) * n + i / V] > 0u ? 1u : 0u; }
+};
+struct StoreListGV {
+    uint32_t* list;
+    uint32_t n, V;
+    __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t x) const {
+        if (x) list[prefix] = (i % V) * n + i / V;  // splat id v n + g
+    }
+};
+
+cudaError_t compact_visible_gaussian_major(const uint32_t* tiles, uint32_t n, uint32_t V, uint32_t* list,
+                                           uint32_t* count, uint32_t* scan_tmp, int sm_count, cudaStream_t st) {
+    const uint32_t S = n * V;
+    if (S == 0) return cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
+    const uint32_t want = (S + kTileItems - 1) / kTileItems;
+    const int G = (int)max(1u, min(want, (uint32_t)min(kScanBlocksMax, 4 * sm_count)));
+    return device_scan(LoadVisibleGV{tiles, n, V}, StoreListGV{list, n, V}, nullptr, S, scan_tmp, count, G, st);
+}
+
 int pair_sort_bits(uint32_t total_tiles) {
     int bits = 1;
     while (bits < 32 && (1ull << bits) < (unsigned long long)total_tiles) bits++;

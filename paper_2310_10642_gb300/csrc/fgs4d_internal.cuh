@@ -509,8 +509,14 @@ cudaError_t launch_render_backward_into(const ViewSet& VS, const DevOpts& O, con
                                         int pair_buf, const float* final_T, const int32_t* n_last,
                                         const float* dL_dimage, float4* g2, cudaStream_t st);
 cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
-                                         const StateLayout& lay, char* state, float4* g2,
+                                         const StateLayout& lay, char* state, float4* g2, uint32_t* list,
+                                         uint32_t* list_count, uint32_t* scan_tmp,
                                          const fgs4d_gaussian_grads& grads, cudaStream_t st);
+
+// Gaussian-major list (g, then view) of the splats with tiles_touched > 0, as
+// splat ids v n + g; its length goes to *count.  scan_tmp: kScanBlocksMax + 32 words.
+cudaError_t compact_visible_gaussian_major(const uint32_t* tiles, uint32_t n, uint32_t V, uint32_t* list,
+                                           uint32_t* count, uint32_t* scan_tmp, int sm_count, cudaStream_t st);
 
 // Host-side count of kernel launches issued by this library (all threads).
 void count_launches(unsigned k);

@@ -11,6 +11,8 @@
 // adjoint) back to the raw parameters.  One thread owns one Gaussian, so no
 // atomics are needed; the 4DSH coefficient gradients are accumulated in
 // shared memory (one column per thread) and written once, coalesced.
+#include <algorithm>
+
 #include "fgs4d_internal.cuh"
 
 namespace fgs4d {
@@ -83,262 +85,305 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
 // ---------------------------------------------------------------------------
 constexpr int kBwdThreads = 128;
 
-// Geometry part of the adjoint.  For every visible splat it also replaces the
-// splat's 2D-gradient slot by its colour cotangent, read by sh_backward_kernel:
+// Sum of x over the caller's segment of contiguous lanes; the result is exact
+// in the segment's first lane (seg_last = last lane of the segment).
+__device__ __forceinline__ float segment_sum(float x, int lane, int seg_last) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float y = __shfl_down_sync(0xffffffffu, x, off);
+        if (lane + off <= seg_last) x += y;
+    }
+    return x;
+}
+
+// Geometry part of the adjoint, one thread per visible (Gaussian, view) splat
+// taken from a Gaussian-major list, so that lanes do not idle on views where
+// their Gaussian is invisible.  The splats of one Gaussian sit in adjacent
+// lanes; their contributions to dL/dSigma (4x4), dL/dmu, dL/dalpha are summed
+// over the segment and its first lane runs Eq. 7-8 backwards once and adds the
+// result to the (pre-zeroed) outputs.  Each splat's 2D-gradient slot is
+// replaced by its colour cotangent, read by sh_backward_kernel:
 //   slot[0] = (view direction d, dt),  slot[1] = (dL/draw_R, dL/draw_G, dL/draw_B, 0)
 // where dL/draw is dL/dcolour with the colour clamp max(raw + 0.5, 0) applied.
 template <int L>
 __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
-    const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, const uint32_t* __restrict__ tiles_touched,
-    float4* __restrict__ grad2d, const fgs4d_gaussian_grads out) {
+    const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, float4* __restrict__ grad2d,
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count, const fgs4d_gaussian_grads out) {
     constexpr int NB = (L + 1) * (L + 1);
-    const int tid = threadIdx.x;
-    const int g = blockIdx.x * blockDim.x + tid;
-    if (g >= G.n) return;
+    const uint32_t count = *list_count;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     const size_t n = (size_t)G.n;
+    for (uint32_t base = warp0 * 32; base < count; base += n_warps * 32) {  // warp-uniform
+        const uint32_t e = base + lane;
+        const bool active = e < count;
+        const uint32_t sid = active ? list[e] : 0u;
+        const int g = (int)(sid % (uint32_t)n);
+        const int v = (int)(sid / (uint32_t)n);
+        const uint32_t key = active ? (uint32_t)g : (0x80000000u | (uint32_t)lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, key);
+        const int seg_first = __ffs(peers) - 1, seg_last = 31 - __clz(peers);
 
-    Core c;
-    load_core(G, g, c);
-    float gmu[4] = {0, 0, 0, 0};
-    float GS[16];
+        float gmu[4] = {0, 0, 0, 0};
+        float GS[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) GS[i] = 0.0f;
-    float galpha = 0.0f, m2d = 0.0f;
-
-    if (c.ok) {
-        const float sig = c.S[15];
-        const float b[3] = {c.S[3], c.S[7], c.S[11]};
-        for (int v = 0; v < VS.n; v++) {
-            const size_t idx = (size_t)v * n + g;
-            if (tiles_touched[idx] == 0u) continue;
+        for (int i = 0; i < 16; i++) GS[i] = 0.0f;
+        float galpha = 0.0f, m2d = 0.0f;
+        Core c;
+        c.ok = false;
+        if (active) load_core(G, g, c);
+        if (active && c.ok) {
+            const float sig = c.S[15];
+            const float b[3] = {c.S[3], c.S[7], c.S[11]};
+            const size_t idx = sid;
             const DevView& V = VS.v[v];
             ViewGeom w;
             slice_view(c, V, O, G, g, w, true);
             if (!project_view(c, V, O, w, true)) {  // cannot happen for a binned splat; keep the slot defined
                 grad2d[3 * idx + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                continue;
-            }
-            const float4 q0 = grad2d[3 * idx + 0];
-            const float4 q1 = grad2d[3 * idx + 1];
-            const float4 q2 = grad2d[3 * idx + 2];
-            const float du = q0.x, dv = q0.y, da = q0.z, db = q0.w, dc = q1.x, dae = q1.y;
-            const float dcol[3] = {q1.z, q1.w, q2.x};
-            m2d += sqrtf(du * du + dv * dv);
+            } else {
+                const float4 q0 = grad2d[3 * idx + 0];
+                const float4 q1 = grad2d[3 * idx + 1];
+                const float4 q2 = grad2d[3 * idx + 2];
+                const float du = q0.x, dv = q0.y, da = q0.z, db = q0.w, dc = q1.x, dae = q1.y;
+                const float dcol[3] = {q1.z, q1.w, q2.x};
+                m2d += sqrtf(du * du + dv * dv);
 
-            // ---- colour (Eq. 11) ----
-            float d[3];
-            const float nrm = view_dir(w, V, d);
-            float Y[16];
-            sh_eval(L, d[0], d[1], d[2], Y);
-            float wsum[16];
-#pragma unroll
-            for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
-            float ddt = 0.0f;
-            float graws[3];
-            for (int ch = 0; ch < 3; ch++) {
-                float P[16];
-#pragma unroll
-                for (int j = 0; j < NB; j++) P[j] = 0.0f;
-                float Q = 0.0f;
-                for (int f = 0; f <= G.K; f++) {
-                    const float arg = 2.0f * (float)f * w.dt * G.inv_period;
-                    const float cf = cospif(arg);
-                    const float sf = sinpif(arg);
-                    const float om = 6.283185307179586f * (float)f * G.inv_period;
-                    float kY = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < NB; j++) {
-                        const float k = load_sh(G, (f * NB + j) * 3 + ch, g);
-                        P[j] = fmaf(cf, k, P[j]);
-                        kY = fmaf(k, Y[j], kY);
+                // ---- colour (Eq. 11) ----
+                float d[3];
+                const float nrm = view_dir(w, V, d);
+                float Y[16];
+                sh_eval(L, d[0], d[1], d[2], Y);
+                float wsum[16];
+    #pragma unroll
+                for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
+                float ddt = 0.0f;
+                float graws[3];
+                for (int ch = 0; ch < 3; ch++) {
+                    float P[16];
+    #pragma unroll
+                    for (int j = 0; j < NB; j++) P[j] = 0.0f;
+                    float Q = 0.0f;
+                    for (int f = 0; f <= G.K; f++) {
+                        const float arg = 2.0f * (float)f * w.dt * G.inv_period;
+                        const float cf = cospif(arg);
+                        const float sf = sinpif(arg);
+                        const float om = 6.283185307179586f * (float)f * G.inv_period;
+                        float kY = 0.0f;
+    #pragma unroll
+                        for (int j = 0; j < NB; j++) {
+                            const float k = load_sh(G, (f * NB + j) * 3 + ch, g);
+                            P[j] = fmaf(cf, k, P[j]);
+                            kY = fmaf(k, Y[j], kY);
+                        }
+                        Q = fmaf(-om * sf, kY, Q);
                     }
-                    Q = fmaf(-om * sf, kY, Q);
+                    float raw = 0.0f;
+    #pragma unroll
+                    for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
+                    const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
+                    graws[ch] = graw;
+                    if (graw != 0.0f) {
+    #pragma unroll
+                        for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
+                        ddt = fmaf(graw, Q, ddt);
+                    }
                 }
-                float raw = 0.0f;
-#pragma unroll
-                for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
-                const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
-                graws[ch] = graw;
-                if (graw != 0.0f) {
-#pragma unroll
-                    for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
-                    ddt = fmaf(graw, Q, ddt);
+                // colour cotangent for the coefficient gradients (sh_backward_kernel)
+                grad2d[3 * idx + 0] = make_float4(d[0], d[1], d[2], w.dt);
+                grad2d[3 * idx + 1] = make_float4(graws[0], graws[1], graws[2], 0.0f);
+                float gd[3];
+                sh_grad(L, d[0], d[1], d[2], wsum, gd[0], gd[1], gd[2]);
+                const float gdd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+                float dmu3[3];
+                const float inrm = 1.0f / nrm;
+    #pragma unroll
+                for (int i = 0; i < 3; i++) dmu3[i] = (gd[i] - gdd * d[i]) * inrm;
+
+                // ---- conic -> 2D covariance: G2 = -Q Gc Q ----
+                const float a = w.conic[0], bq = w.conic[1], cq = w.conic[2];
+                const float g00 = da, g01 = 0.5f * db, g11 = dc;
+                // QG = Q * Gc
+                const float qg00 = a * g00 + bq * g01, qg01 = a * g01 + bq * g11;
+                const float qg10 = bq * g00 + cq * g01, qg11 = bq * g01 + cq * g11;
+                const float G200 = -(qg00 * a + qg01 * bq);
+                const float G201 = -(qg00 * bq + qg01 * cq);
+                const float G211 = -(qg10 * bq + qg11 * cq);
+
+                // ---- Eq. 4: dSigma3 = T^T G2 T, dT = 2 G2 T Sigma3 ----
+                const float* T = w.T;
+                float GT[2][3];
+    #pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    GT[0][k] = G200 * T[k] + G201 * T[3 + k];
+                    GT[1][k] = G201 * T[k] + G211 * T[3 + k];
                 }
-            }
-            // colour cotangent for the coefficient gradients (sh_backward_kernel)
-            grad2d[3 * idx + 0] = make_float4(d[0], d[1], d[2], w.dt);
-            grad2d[3 * idx + 1] = make_float4(graws[0], graws[1], graws[2], 0.0f);
-            float gd[3];
-            sh_grad(L, d[0], d[1], d[2], wsum, gd[0], gd[1], gd[2]);
-            const float gdd = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
-            float dmu3[3];
-            const float inrm = 1.0f / nrm;
-#pragma unroll
-            for (int i = 0; i < 3; i++) dmu3[i] = (gd[i] - gdd * d[i]) * inrm;
+                float G3[6];  // 00 01 02 11 12 22
+                G3[0] = T[0] * GT[0][0] + T[3] * GT[1][0];
+                G3[1] = T[0] * GT[0][1] + T[3] * GT[1][1];
+                G3[2] = T[0] * GT[0][2] + T[3] * GT[1][2];
+                G3[3] = T[1] * GT[0][1] + T[4] * GT[1][1];
+                G3[4] = T[1] * GT[0][2] + T[4] * GT[1][2];
+                G3[5] = T[2] * GT[0][2] + T[5] * GT[1][2];
+                const float* S3 = w.S3;
+                float dT[2][3];
+    #pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    dT[r][0] = 2.0f * (GT[r][0] * S3[0] + GT[r][1] * S3[1] + GT[r][2] * S3[2]);
+                    dT[r][1] = 2.0f * (GT[r][0] * S3[1] + GT[r][1] * S3[3] + GT[r][2] * S3[4]);
+                    dT[r][2] = 2.0f * (GT[r][0] * S3[2] + GT[r][1] * S3[4] + GT[r][2] * S3[5]);
+                }
+                // dJ = dT W^T
+                float dJ[2][3];
+    #pragma unroll
+                for (int r = 0; r < 2; r++)
+    #pragma unroll
+                    for (int m = 0; m < 3; m++)
+                        dJ[r][m] = dT[r][0] * V.W[m * 3 + 0] + dT[r][1] * V.W[m * 3 + 1] + dT[r][2] * V.W[m * 3 + 2];
 
-            // ---- conic -> 2D covariance: G2 = -Q Gc Q ----
-            const float a = w.conic[0], bq = w.conic[1], cq = w.conic[2];
-            const float g00 = da, g01 = 0.5f * db, g11 = dc;
-            // QG = Q * Gc
-            const float qg00 = a * g00 + bq * g01, qg01 = a * g01 + bq * g11;
-            const float qg10 = bq * g00 + cq * g01, qg11 = bq * g01 + cq * g11;
-            const float G200 = -(qg00 * a + qg01 * bq);
-            const float G201 = -(qg00 * bq + qg01 * cq);
-            const float G211 = -(qg10 * bq + qg11 * cq);
+                // ---- J and the projected mean w.r.t. camera coordinates ----
+                const float X = w.xc[0], Yc = w.xc[1], Z = w.xc[2];
+                const float iz = 1.0f / Z, iz2 = iz * iz;
+                float tx = X * iz, ty = Yc * iz;
+                tx = fminf(fmaxf(tx, -V.limx), V.limx);
+                ty = fminf(fmaxf(ty, -V.limy), V.limy);
+                float dxc[3] = {0.0f, 0.0f, 0.0f};
+                dxc[2] += dJ[0][0] * (-V.fx * iz2) + dJ[1][1] * (-V.fy * iz2);
+                dxc[2] += dJ[0][2] * (V.fx * tx * iz2) + dJ[1][2] * (V.fy * ty * iz2);
+                if (!w.clx) {
+                    dxc[0] += dJ[0][2] * (-V.fx * iz2);
+                    dxc[2] += dJ[0][2] * (V.fx * X * iz2 * iz);
+                }
+                if (!w.cly) {
+                    dxc[1] += dJ[1][2] * (-V.fy * iz2);
+                    dxc[2] += dJ[1][2] * (V.fy * Yc * iz2 * iz);
+                }
+                dxc[0] += du * V.fx * iz;
+                dxc[1] += dv * V.fy * iz;
+                dxc[2] += -du * V.fx * X * iz2 - dv * V.fy * Yc * iz2;
+    #pragma unroll
+                for (int i = 0; i < 3; i++)
+                    dmu3[i] += V.W[0 * 3 + i] * dxc[0] + V.W[1 * 3 + i] * dxc[1] + V.W[2 * 3 + i] * dxc[2];
 
-            // ---- Eq. 4: dSigma3 = T^T G2 T, dT = 2 G2 T Sigma3 ----
-            const float* T = w.T;
-            float GT[2][3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                GT[0][k] = G200 * T[k] + G201 * T[3 + k];
-                GT[1][k] = G201 * T[k] + G211 * T[3 + k];
+                // ---- Eq. 9, Eq. 10 ----
+                const float dp = dae * c.alpha;
+                galpha += dae * w.p;
+                const float isig = 1.0f / sig;
+                float G3b[3];
+                G3b[0] = G3[0] * b[0] + G3[1] * b[1] + G3[2] * b[2];
+                G3b[1] = G3[1] * b[0] + G3[3] * b[1] + G3[4] * b[2];
+                G3b[2] = G3[2] * b[0] + G3[4] * b[1] + G3[5] * b[2];
+                const float mb = dmu3[0] * b[0] + dmu3[1] * b[1] + dmu3[2] * b[2];
+                const float bGb = b[0] * G3b[0] + b[1] * G3b[1] + b[2] * G3b[2];
+                const float dt = w.dt;
+                const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
+                ddt += mb * isig - dp * w.p * dt * isig;
+    #pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
+                    GS[i * 4 + 3] += 0.5f * dbi;
+                    gmu[i] += dmu3[i];
+                }
+                gmu[3] -= ddt;
+                GS[0] += G3[0];
+                GS[1] += G3[1];
+                GS[2] += G3[2];
+                GS[5] += G3[3];
+                GS[6] += G3[4];
+                GS[10] += G3[5];
+                GS[15] += dsig;
             }
-            float G3[6];  // 00 01 02 11 12 22
-            G3[0] = T[0] * GT[0][0] + T[3] * GT[1][0];
-            G3[1] = T[0] * GT[0][1] + T[3] * GT[1][1];
-            G3[2] = T[0] * GT[0][2] + T[3] * GT[1][2];
-            G3[3] = T[1] * GT[0][1] + T[4] * GT[1][1];
-            G3[4] = T[1] * GT[0][2] + T[4] * GT[1][2];
-            G3[5] = T[2] * GT[0][2] + T[5] * GT[1][2];
-            const float* S3 = w.S3;
-            float dT[2][3];
-#pragma unroll
-            for (int r = 0; r < 2; r++) {
-                dT[r][0] = 2.0f * (GT[r][0] * S3[0] + GT[r][1] * S3[1] + GT[r][2] * S3[2]);
-                dT[r][1] = 2.0f * (GT[r][0] * S3[1] + GT[r][1] * S3[3] + GT[r][2] * S3[4]);
-                dT[r][2] = 2.0f * (GT[r][0] * S3[2] + GT[r][1] * S3[4] + GT[r][2] * S3[5]);
-            }
-            // dJ = dT W^T
-            float dJ[2][3];
-#pragma unroll
-            for (int r = 0; r < 2; r++)
-#pragma unroll
-                for (int m = 0; m < 3; m++)
-                    dJ[r][m] = dT[r][0] * V.W[m * 3 + 0] + dT[r][1] * V.W[m * 3 + 1] + dT[r][2] * V.W[m * 3 + 2];
-
-            // ---- J and the projected mean w.r.t. camera coordinates ----
-            const float X = w.xc[0], Yc = w.xc[1], Z = w.xc[2];
-            const float iz = 1.0f / Z, iz2 = iz * iz;
-            float tx = X * iz, ty = Yc * iz;
-            tx = fminf(fmaxf(tx, -V.limx), V.limx);
-            ty = fminf(fmaxf(ty, -V.limy), V.limy);
-            float dxc[3] = {0.0f, 0.0f, 0.0f};
-            dxc[2] += dJ[0][0] * (-V.fx * iz2) + dJ[1][1] * (-V.fy * iz2);
-            dxc[2] += dJ[0][2] * (V.fx * tx * iz2) + dJ[1][2] * (V.fy * ty * iz2);
-            if (!w.clx) {
-                dxc[0] += dJ[0][2] * (-V.fx * iz2);
-                dxc[2] += dJ[0][2] * (V.fx * X * iz2 * iz);
-            }
-            if (!w.cly) {
-                dxc[1] += dJ[1][2] * (-V.fy * iz2);
-                dxc[2] += dJ[1][2] * (V.fy * Yc * iz2 * iz);
-            }
-            dxc[0] += du * V.fx * iz;
-            dxc[1] += dv * V.fy * iz;
-            dxc[2] += -du * V.fx * X * iz2 - dv * V.fy * Yc * iz2;
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-                dmu3[i] += V.W[0 * 3 + i] * dxc[0] + V.W[1 * 3 + i] * dxc[1] + V.W[2 * 3 + i] * dxc[2];
-
-            // ---- Eq. 9, Eq. 10 ----
-            const float dp = dae * c.alpha;
-            galpha += dae * w.p;
-            const float isig = 1.0f / sig;
-            float G3b[3];
-            G3b[0] = G3[0] * b[0] + G3[1] * b[1] + G3[2] * b[2];
-            G3b[1] = G3[1] * b[0] + G3[3] * b[1] + G3[4] * b[2];
-            G3b[2] = G3[2] * b[0] + G3[4] * b[1] + G3[5] * b[2];
-            const float mb = dmu3[0] * b[0] + dmu3[1] * b[1] + dmu3[2] * b[2];
-            const float bGb = b[0] * G3b[0] + b[1] * G3b[1] + b[2] * G3b[2];
-            const float dt = w.dt;
-            const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
-            ddt += mb * isig - dp * w.p * dt * isig;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
-                GS[i * 4 + 3] += 0.5f * dbi;
-                gmu[i] += dmu3[i];
-            }
-            gmu[3] -= ddt;
-            GS[0] += G3[0];
-            GS[1] += G3[1];
-            GS[2] += G3[2];
-            GS[5] += G3[3];
-            GS[6] += G3[4];
-            GS[10] += G3[5];
-            GS[15] += dsig;
         }
-    }
+        // ---- sum the segment (all visible views of this Gaussian in this warp) ----
+        gmu[0] = segment_sum(gmu[0], lane, seg_last);
+        gmu[1] = segment_sum(gmu[1], lane, seg_last);
+        gmu[2] = segment_sum(gmu[2], lane, seg_last);
+        gmu[3] = segment_sum(gmu[3], lane, seg_last);
+        GS[0] = segment_sum(GS[0], lane, seg_last);
+        GS[1] = segment_sum(GS[1], lane, seg_last);
+        GS[2] = segment_sum(GS[2], lane, seg_last);
+        GS[3] = segment_sum(GS[3], lane, seg_last);
+        GS[5] = segment_sum(GS[5], lane, seg_last);
+        GS[6] = segment_sum(GS[6], lane, seg_last);
+        GS[7] = segment_sum(GS[7], lane, seg_last);
+        GS[10] = segment_sum(GS[10], lane, seg_last);
+        GS[11] = segment_sum(GS[11], lane, seg_last);
+        GS[15] = segment_sum(GS[15], lane, seg_last);
+        galpha = segment_sum(galpha, lane, seg_last);
+        m2d = segment_sum(m2d, lane, seg_last);
+        if (!(active && c.ok && lane == seg_first)) continue;
 
-    // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
-    float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
-    if (c.ok) {
-        // symmetrise the accumulator (only the upper triangle was written)
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
-        float dR[16];
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                float acc = 0.0f;
-#pragma unroll
-                for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], c.M[j * 4 + k], acc);
-                const float dM = 2.0f * acc;
-                dR[i * 4 + k] = dM * c.s[k];
-                gls[k] = fmaf(dM, c.R[i * 4 + k], gls[k]);
-            }
-#pragma unroll
-        for (int k = 0; k < 4; k++) gls[k] *= c.s[k];
-        float Lm[16], Rm[16];
-        left_matrix(c.qln, Lm);
-        right_matrix(c.qrn, Rm);
-        float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                float x = 0.0f, y = 0.0f;
-#pragma unroll
+        // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
+        float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
+        if (c.ok) {
+            // symmetrise the accumulator (only the upper triangle was written)
+    #pragma unroll
+            for (int i = 0; i < 4; i++)
+    #pragma unroll
+                for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
+            float dR[16];
+    #pragma unroll
+            for (int i = 0; i < 4; i++)
+    #pragma unroll
                 for (int k = 0; k < 4; k++) {
-                    x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
-                    y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
+                    float acc = 0.0f;
+    #pragma unroll
+                    for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], c.M[j * 4 + k], acc);
+                    const float dM = 2.0f * acc;
+                    dR[i * 4 + k] = dM * c.s[k];
+                    gls[k] = fmaf(dM, c.R[i * 4 + k], gls[k]);
                 }
-                D[i * 4 + j] = x;
-                E[i * 4 + j] = y;
+    #pragma unroll
+            for (int k = 0; k < 4; k++) gls[k] *= c.s[k];
+            float Lm[16], Rm[16];
+            left_matrix(c.qln, Lm);
+            right_matrix(c.qrn, Rm);
+            float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
+    #pragma unroll
+            for (int i = 0; i < 4; i++)
+    #pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    float x = 0.0f, y = 0.0f;
+    #pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
+                        y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
+                    }
+                    D[i * 4 + j] = x;
+                    E[i * 4 + j] = y;
+                }
+            const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
+                                 -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
+            const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
+                                 -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
+            float dl = 0.0f, dr = 0.0f;
+    #pragma unroll
+            for (int i = 0; i < 4; i++) {
+                dl = fmaf(gl[i], c.qln[i], dl);
+                dr = fmaf(gr[i], c.qrn[i], dr);
             }
-        const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
-                             -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
-        const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
-                             -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
-        float dl = 0.0f, dr = 0.0f;
+    #pragma unroll
+            for (int i = 0; i < 4; i++) {
+                gql[i] = (gl[i] - dl * c.qln[i]) / c.nl;
+                gqr[i] = (gr[i] - dr * c.qrn[i]) / c.nr;
+            }
+            glogit = galpha * c.alpha * (1.0f - c.alpha);
+        } else {
+    #pragma unroll
+            for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
+        }
+        // a Gaussian whose views straddle two warps is completed by two leaders: add, do not store
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            dl = fmaf(gl[i], c.qln[i], dl);
-            dr = fmaf(gr[i], c.qrn[i], dr);
+            atomicAdd(&out.mu[i * n + g], gmu[i]);
+            atomicAdd(&out.log_scale[i * n + g], gls[i]);
+            atomicAdd(&out.q_left[i * n + g], gql[i]);
+            atomicAdd(&out.q_right[i * n + g], gqr[i]);
         }
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            gql[i] = (gl[i] - dl * c.qln[i]) / c.nl;
-            gqr[i] = (gr[i] - dr * c.qrn[i]) / c.nr;
-        }
-        glogit = galpha * c.alpha * (1.0f - c.alpha);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
+        atomicAdd(&out.opacity_logit[g], glogit);
+        if (out.mean2d_abs) atomicAdd(&out.mean2d_abs[g], m2d);
     }
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        out.mu[i * n + g] = gmu[i];
-        out.log_scale[i * n + g] = gls[i];
-        out.q_left[i * n + g] = gql[i];
-        out.q_right[i * n + g] = gqr[i];
-    }
-    out.opacity_logit[g] = glogit;
-    if (out.mean2d_abs) out.mean2d_abs[g] = m2d;
 }
 
 // Coefficient part of the adjoint (Eq. 11): dL/dk[f][j][ch] = sum over the
@@ -433,42 +478,78 @@ static void launch_sh_k(const DevGauss& G, int n_views, const uint32_t* tt, cons
     }
 }
 
+static int local_sm_count() {
+    static int count = 0;
+    if (count == 0) {
+        int dev = 0, c = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && c > 0)
+            count = c;
+        else
+            return 152;
+    }
+    return count;
+}
+
+// Adjoint of slice/project/4DSH: Gaussian-major list of the visible splats,
+// geometry kernel over that list (outputs accumulated, so cleared first),
+// then the coefficient kernel.
 template <int L>
-static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
-                            float4* g2, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
-    const int blocks = (G.n + kBwdThreads - 1) / kBwdThreads;
-    project_backward_kernel<L><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, tt, g2, grads);
+static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt, float4* g2,
+                            uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp,
+                            const fgs4d_gaussian_grads& grads, cudaStream_t st) {
+    const size_t n = (size_t)G.n;
+    cudaError_t e = cudaSuccess;
+    float* outs[5] = {grads.mu, grads.log_scale, grads.q_left, grads.q_right, grads.opacity_logit};
+    const size_t rows[5] = {4, 4, 4, 4, 1};
+    for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaMemsetAsync(outs[i], 0, rows[i] * n * sizeof(float), st);
+    if (e == cudaSuccess && grads.mean2d_abs) e = cudaMemsetAsync(grads.mean2d_abs, 0, n * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    const int sms = local_sm_count();
+    e = compact_visible_gaussian_major(tt, (uint32_t)n, (uint32_t)VS.n, list, list_count, scan_tmp, sms, st);
+    if (e != cudaSuccess) return e;
+    const uint64_t S = (uint64_t)n * VS.n;
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((S + kBwdThreads - 1) / kBwdThreads, 16ull * sms));
+    project_backward_kernel<L><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads);
     launch_sh_k<L>(G, VS.n, tt, g2, grads.shs, st);
     count_launches(2);
     return cudaGetLastError();
 }
 
+static cudaError_t launch_pb_any(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
+                                 float4* g2, uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp,
+                                 const fgs4d_gaussian_grads& grads, cudaStream_t st) {
+    switch (G.L) {
+        case 0: return launch_pb<0>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+        case 1: return launch_pb<1>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+        case 2: return launch_pb<2>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+        default: return launch_pb<3>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+    }
+}
+
+// The list of visible splats goes to the state's pair-offset section (free
+// once the tiles are binned) and its length to counters[4].
 cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const StateLayout& lay,
                                     char* state, const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
     auto* g2 = reinterpret_cast<float4*>(state + lay.grad2d);
-    switch (G.L) {
-        case 0: return launch_pb<0>(G, VS, O, tt, g2, grads, st);
-        case 1: return launch_pb<1>(G, VS, O, tt, g2, grads, st);
-        case 2: return launch_pb<2>(G, VS, O, tt, g2, grads, st);
-        default: return launch_pb<3>(G, VS, O, tt, g2, grads, st);
-    }
+    auto* list = reinterpret_cast<uint32_t*>(state + lay.offsets);
+    auto* cnt = reinterpret_cast<uint32_t*>(state + lay.counters) + 4;
+    auto* scan_tmp = reinterpret_cast<uint32_t*>(state + lay.scan_tmp);
+    return launch_pb_any(G, VS, O, tt, g2, list, cnt, scan_tmp, grads, st);
 }
 
-// Same as launch_project_backward, reading the per-splat 2D gradient from g2
-// instead of the state (used by the allocation-free backward entry point).
+// Same as launch_project_backward with the per-splat 2D gradient, the list,
+// its length and the scan scratch supplied by the caller (used by the
+// allocation-free backward entry point, which does not write the state).
 cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, const DevOpts& O,
-                                         const StateLayout& lay, char* state, float4* g2,
+                                         const StateLayout& lay, char* state, float4* g2, uint32_t* list,
+                                         uint32_t* list_count, uint32_t* scan_tmp,
                                          const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
-    switch (G.L) {
-        case 0: return launch_pb<0>(G, VS, O, tt, g2, grads, st);
-        case 1: return launch_pb<1>(G, VS, O, tt, g2, grads, st);
-        case 2: return launch_pb<2>(G, VS, O, tt, g2, grads, st);
-        default: return launch_pb<3>(G, VS, O, tt, g2, grads, st);
-    }
+    return launch_pb_any(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
 }
 
 }  // namespace fgs4d
