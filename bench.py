@@ -9,11 +9,17 @@ of 20 cameras on a forward-facing arc at 1352x1014, each at its own time out
 of 300 frames (seeded synthetic data standing in for Plenoptic-Video-like
 scenes).  The parameters (644 MB) are larger than L2, so no flush is needed.
 
+Precision (default ``mixed``): 4DSH coefficients stored in BF16 and conics
+in 16-bit records, with FP32 arithmetic and accumulation; ``--precision fp32``
+stores everything in FP32.
+
 Printed: one JSON line.  ``value`` is forward+backward Mpix/s with inputs
-resident in HBM; ``e2e`` is the same step through the C ABI with host
-buffers (parameters and dL/dimage copied in, image and gradients copied out
-inside the timed region).  ``fwd_mpix_s`` is forward only and ``single_view``
-the plain one-view-per-call FP32 path on the same GPU.
+resident in HBM, each step replayed as one CUDA graph; ``e2e`` is the same
+step through the C ABI with host buffers (parameters and dL/dimage copied in,
+image and gradients copied out inside the timed region).  ``stage_ms`` and
+``fwd_mpix_s`` come from eager launches bracketed by events; ``batched_fp32``
+is the whole batch in plain FP32 and ``single_view`` the plain FP32 path one
+view per call, both on the same GPU.
 
 ``--impl reference`` times the FP64 CPU oracle instead (a bounded crop sample
 of the same workload on the host cores).
@@ -47,7 +53,9 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="image scale (smoke runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--shs-bf16", action="store_true", help="store 4DSH coefficients in BF16")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
+                    help="mixed: BF16 4DSH coefficients + 16-bit conic records; fp32: plain FP32 storage")
+    ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly, not as a CUDA graph")
     ap.add_argument("--tile", type=int, default=32, choices=[16, 32], help="screen tile side")
     return ap.parse_args()
 
@@ -187,65 +195,108 @@ def main():
     N.lib()
 
     G, views, opts = workload_inputs(args.n, args.views, args.scale)
-    opts = dict(opts, tile_size=args.tile)
     n = G["logit"].shape[0]
-    shs_dtype = torch.bfloat16 if args.shs_bf16 else torch.float32
-    p = R.params_to_device(G, shs_dtype=shs_dtype)
-    frame = R.Frame(n, views, opts)
+    mixed = args.precision == "mixed"
+    opts_fp32 = dict(opts, tile_size=args.tile, record_fp16=0)
+    opts = dict(opts, tile_size=args.tile, record_fp16=int(mixed))
+    p32 = R.params_to_device(G)
+    p = R.params_to_device(G, shs_dtype=torch.bfloat16) if mixed else p32
     stream = torch.cuda.current_stream()
-    npix = frame.total_pixels
     gen = torch.Generator(device="cuda").manual_seed(1234)
-    dL = torch.randn(3 * npix, device="cuda", generator=gen) * (1.0 / npix)
-    grads = {k: torch.empty(p[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
-
-    # size the pair capacity once (outside the timed region), with headroom
-    frame.forward(p, check=True)
-    c = frame.last_counters
-    if c.n_pairs * 1.1 > frame.pair_capacity:
-        frame._alloc(int(c.n_pairs * 1.15) + 4096)
-        frame.forward(p, check=True)
-    counters = frame.last_counters
-
+    grads = {k: torch.empty(p32[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
     stages = ["slice_project", "bin_sort", "render", "render_backward"]
 
-    def step(events=None):
-        if events is not None:
-            events[0].record(stream)
-        frame.slice_project(p)
-        if events is not None:
-            events[1].record(stream)
-        frame.bin_sort()
-        if events is not None:
-            events[2].record(stream)
-        frame.render()
-        if events is not None:
-            events[3].record(stream)
-        frame.backward(p, dL, grads)
-        if events is not None:
-            events[4].record(stream)
+    def sized_frame(vs, o, params):
+        """Frame whose pair capacity is sized once, outside the timed region, with headroom."""
+        fr = R.Frame(n, vs, o)
+        fr.forward(params, check=True)
+        c = fr.last_counters
+        if c.n_pairs * 1.1 > fr.pair_capacity:
+            fr._alloc(int(c.n_pairs * 1.15) + 4096)
+            fr.forward(params, check=True)
+        return fr
 
+    def make_step(fr, params, dLv, events=None):
+        def step():
+            if events is not None:
+                events[0].record(stream)
+            fr.slice_project(params)
+            if events is not None:
+                events[1].record(stream)
+            fr.bin_sort()
+            if events is not None:
+                events[2].record(stream)
+            fr.render()
+            if events is not None:
+                events[3].record(stream)
+            fr.backward(params, dLv, grads)
+            if events is not None:
+                events[4].record(stream)
+        return step
+
+    def capture(step):
+        """One whole step (all four entry points) as a CUDA graph; returns (graph, launches per step)."""
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        l0 = N.fgs4d_launch_count()
+        with torch.cuda.graph(g):
+            step()
+        torch.cuda.synchronize()
+        return g, N.fgs4d_launch_count() - l0
+
+    def time_graph(g, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    frame = sized_frame(views, opts, p)
+    npix = frame.total_pixels
+    dL = torch.randn(3 * npix, device="cuda", generator=gen) * (1.0 / npix)
+    counters = frame.last_counters
+
+    # per-stage breakdown: eager launches bracketed by events (untimed for the headline)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(max(3, args.steps))]
     for _ in range(max(3, args.warmup)):
-        step()
+        make_step(frame, p, dL)()
+    for e in ev:
+        make_step(frame, p, dL, e)()
+    torch.cuda.synchronize()
+    stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, s in enumerate(stages)}
+
+    # headline: K whole steps, replayed as one CUDA graph each (or launched eagerly with --no-graph)
+    step = make_step(frame, p, dL)
+    graph, per_step = (None, 0) if args.no_graph else capture(step)
+    run = step if graph is None else graph.replay
+    for _ in range(max(3, args.warmup)):
+        run()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = N.fgs4d_launch_count()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    e_start.record(stream)
     for k in range(args.steps):
-        step(ev[k])
+        run()
+    e_end.record(stream)
     torch.cuda.synchronize()
-    launches = N.fgs4d_launch_count() - launches0
+    launches = N.fgs4d_launch_count() - launches0 + per_step * args.steps * (graph is not None)
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = ev[0][0].elapsed_time(ev[-1][4])
-    stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, s in enumerate(stages)}
+    total_ms = e_start.elapsed_time(e_end)
     t_tensor = torch.tensor([total_ms], device="cuda")
     if dist:
         dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
@@ -260,46 +311,54 @@ def main():
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     L, K = G["sh_degree"], G["n_freq"]
     C = 3 * (L + 1) ** 2 * (K + 1)
-    shs_b = 2 if args.shs_bf16 else 4
+    shs_b = 2 if mixed else 4
+    rec_b = 32 if mixed else 48   # splat record written per visible splat
+    rd_b = 32 if mixed else 36    # record bytes a tile stages per list entry
     V = len(views)
     nvis, npairs = counters.n_visible, counters.n_pairs
     alg = {
         # parameters read once + records/tile counts/depth keys written
-        "slice_project": n * (17 * 4 + C * shs_b) + nvis * 48 + V * n * 8,
+        "slice_project": n * (17 * 4 + C * shs_b) + nvis * rec_b + V * n * 8,
         # compaction (read tile counts + depth keys, write 8 B per visible splat), depth sort (4 passes x 20 B),
         # offsets scan (8 B), emission (8 B per pair), pair sort (passes x 20 B per pair), ranges (4 B per pair)
         "bin_sort": V * n * 8 + nvis * (8 + 4 * 20 + 8) + npairs * (8 + 4)
         + npairs * 20 * ((_bits(frame.layout().total_tiles) + 7) // 8),
-        # list ids + gathered records (36 B) per pair, 20 B written per pixel
-        "render": npairs * (4 + 36) + npix * 20,
+        # list ids + gathered records per pair, 20 B written per pixel
+        "render": npairs * (4 + rd_b) + npix * 20,
         # same gathers + dL/dimage, T, n_last per pixel + 48 B gradient record per visible splat (zero+atomics)
         # + per-Gaussian parameters and gradients
-        "render_backward": npairs * (4 + 36) + npix * 20 + nvis * 48 * 2 + n * 2 * (17 * 4 + C * 4),
+        "render_backward": npairs * (4 + rd_b) + npix * 20 + nvis * 48 * 2 + n * (17 * 4 + C * shs_b)
+        + n * (17 * 4 + C * 4),
     }
     dom = max(stage_ms, key=stage_ms.get)
     achieved = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
     roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=hbm, unit="GB/s", frac=round(achieved / hbm, 4),
                     traffic=None, kernel=dom, peak_source=f"{peak_kind} hbm_gbs")
 
-    # ---- single-view plain FP32 path (one view per call), same GPU
-    single = None
+    # ---- plain FP32 paths on the same GPU: the whole batch, and one view per call
+    single = batched_fp32 = None
     if rank == 0:
-        fr1 = R.Frame(n, views[:1], opts)
-        fr1.forward(p, check=True)
+        if mixed:
+            fr = sized_frame(views, opts_fp32, p32)
+            g32, _ = capture(make_step(fr, p32, dL))
+            ms32 = time_graph(g32, 3)
+            batched_fp32 = dict(mpix_s=round(npix / (ms32 * 1e-3) / 1e6, 3), ms_per_step=round(ms32, 4))
+            del g32, fr
+        fr1 = sized_frame(views[:1], opts_fp32, p32)
         dL1 = torch.randn(3 * fr1.total_pixels, device="cuda", generator=gen) * (1.0 / fr1.total_pixels)
+        step1 = make_step(fr1, p32, dL1)
         for _ in range(3):
-            fr1.forward(p, check=False)
-            fr1.backward(p, dL1, grads)
+            step1()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
+        reps = 5
         e0.record(stream)
         for _ in range(reps):
-            fr1.forward(p, check=False)
-            fr1.backward(p, dL1, grads)
+            step1()
         e1.record(stream)
         torch.cuda.synchronize()
         ms1 = e0.elapsed_time(e1) / reps
-        single = dict(mpix_s=fr1.total_pixels / (ms1 * 1e-3) / 1e6, ms_per_view=ms1)
+        single = dict(mpix_s=round(fr1.total_pixels / (ms1 * 1e-3) / 1e6, 3), ms_per_view=round(ms1, 4),
+                      path="plain FP32 records and coefficients, one view per call, eager launches")
         del fr1
 
     # ---- e2e through the C ABI with host buffers
@@ -351,12 +410,17 @@ def main():
         out = dict(metric="Mpix/s fwd+bwd (4DGS render, 1M Gaussians, 1352x1014)", value=round(value, 3),
                    unit="Mpix/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms_step, 4),
                    higher_is_better=True, scaling="weak", vs_baseline=None,
-                   dtype="f32" + ("+bf16-shs" if args.shs_bf16 else ""), data="synthetic",
-                   config=dict(WORKLOAD, n=n, views=V, tile=args.tile, l2="inputs larger than L2 (644 MB parameters)",
+                   dtype="f32", data="synthetic",
+                   config=dict(WORKLOAD, n=n, views=V, tile=args.tile, precision=(
+                       "BF16 4DSH coefficients, 16-bit Cholesky conics; FP32 arithmetic" if mixed else "FP32"),
+                       cuda_graph=graph is not None,
+                       l2="inputs larger than L2 (356 MB mixed / 644 MB FP32 parameters)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                                pixels_per_step=npix, visible_splats=nvis, pairs=npairs),
                    fwd_mpix_s=round(fwd_mpix, 3), stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
-                   single_view=single, roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk,
+                   single_view=single, batched_fp32=batched_fp32,
+                   batched_vs_single_fp32=round(value / world / single["mpix_s"], 3) if single else None,
+                   roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk,
                    gpu_launches=int(launches))
         print(json.dumps(out))
     if dist:

@@ -438,18 +438,28 @@ typedef struct {
 } contrib;
 
 /* Walks one pixel front to back.  Fills the contributor list (if given),
-   returns the number of contributors; writes colour, final T and flags. */
+   returns the number of contributors; writes colour, final T and flags.
+
+   amb (optional, two doubles) bounds how far a valid single-precision
+   evaluation may land from this result, summed over the flagged decisions:
+   amb[0] for the colour, amb[1] for the final transmittance.  cmax bounds
+   every colour component (splats and background).  A splat included or
+   skipped the other way moves the pixel by at most T a (|c| + cmax) and T by
+   T a; two adjacent splats blended in the other order move it by exactly
+   T a_1 a_2 (c_1 - c_2) and leave T unchanged; stopping one splat earlier or
+   later moves it by at most T (a (|c| + cmax) + cmax) and T by T. */
 static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const orc_options *O,
                       const orc_view *V, double px, double py, int prefilter, double *C, double *T_out,
-                      uint8_t *flag, contrib *list, uint64_t *hash) {
+                      uint8_t *flag, contrib *list, uint64_t *hash, double *amb, double cmax) {
     double T = 1.0;
     uint64_t hsh = 1469598103934665603ull; /* order-sensitive hash of the contributor sequence */
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0;
     uint8_t f = 0;
     /* previous relevant splat, for the depth-order check */
-    double last_rel_depth = -1.0, last_alpha = 0.0;
+    double last_rel_depth = -1.0, last_alpha = 0.0, last_T = 1.0;
     const double *last_color = NULL;
+    double amb_c = 0.0, amb_t = 0.0;
     for (int64_t k = 0; k < m; k++) {
         const orc_splat *s = &S[order[k]];
         const double dx = px - s->u, dy = py - s->v;
@@ -461,21 +471,29 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
         const double Gexp = exp(power);
         const double araw = s->alpha_eff * Gexp;
         const int relevant = araw >= O->alpha_min * (1.0 - ORC_ETA_ALPHA);
+        double cs = 0.0;
+        for (int ch = 0; ch < 3; ch++) cs = fmax(cs, fabs(s->color[ch]));
         if (relevant) {
-            if (s->borderline) f |= 1 | 32;
-            if (fabs(araw - O->alpha_min) <= ORC_ETA_ALPHA * O->alpha_min) f |= 1 | 16;
             const double a_cl = araw < O->alpha_max ? araw : O->alpha_max;
+            int flip = 0;
+            if (s->borderline) { f |= 1 | 32; flip = 1; }
+            if (fabs(araw - O->alpha_min) <= ORC_ETA_ALPHA * O->alpha_min) { f |= 1 | 16; flip = 1; }
+            if (flip) {
+                amb_c += T * a_cl * (cs + cmax);
+                amb_t += T * a_cl;
+            }
             if (last_rel_depth >= 0.0 && fabs(s->depth - last_rel_depth) <= ORC_ETA_DEPTH * s->depth) {
-                /* swapping two blended splats changes the pixel by at most
-                   T a_1 a_2 max|c_1 - c_2|; below 1e-5 the image cannot tell */
                 double dc = 0.0;
                 for (int ch = 0; ch < 3; ch++) dc = fmax(dc, fabs(s->color[ch] - last_color[ch]));
+                const double d = last_T * a_cl * last_alpha * dc;
                 f |= 2;
-                if (T * a_cl * last_alpha * dc > 1e-5) f |= 1 | 4;
+                if (d > 1e-5) f |= 1 | 4; /* below 1e-5 the image cannot tell */
+                amb_c += d;
             }
             last_rel_depth = s->depth;
             last_alpha = a_cl;
             last_color = s->color;
+            last_T = T;
         }
         if (!s->visible) continue; /* borderline-culled: flags only */
         if (power > 0.0) continue;  /* R6 */
@@ -483,7 +501,11 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
         if (alpha < O->alpha_min) continue;
         if (fabs(araw - O->alpha_max) <= ORC_ETA_ALPHA * O->alpha_max) f |= 2;
         const double Tn = T * (1.0 - alpha);
-        if (fabs(Tn - O->T_min) <= ORC_ETA_T * O->T_min) f |= 1 | 8;
+        if (fabs(Tn - O->T_min) <= ORC_ETA_T * O->T_min) {
+            f |= 1 | 8;
+            amb_c += T * (alpha * (cs + cmax) + cmax);
+            amb_t += T;
+        }
         if (Tn < O->T_min) break;  /* R5 */
         for (int ch = 0; ch < 3; ch++) {
             C[ch] += s->color[ch] * alpha * T;
@@ -502,18 +524,34 @@ static int pixel_walk(const orc_splat *S, const int64_t *order, int64_t m, const
     *T_out = T;
     if (flag) *flag = f;
     if (hash) *hash = hsh;
+    if (amb) {
+        amb[0] = amb_c;
+        amb[1] = amb_t;
+    }
     return nc;
+}
+
+/* largest colour component of the candidates and the background */
+static double max_color(const orc_splat *S, const int64_t *order, int64_t m, const orc_view *V) {
+    double c = 0.0;
+    for (int ch = 0; ch < 3; ch++) c = fmax(c, fabs(V->bg[ch]));
+    for (int64_t k = 0; k < m; k++)
+        for (int ch = 0; ch < 3; ch++) c = fmax(c, fabs(S[order[k]].color[ch]));
+    return c;
 }
 
 /* Renders the window [x0, x0+w) x [y0, y0+h) of the view.  image is [3][h][w].
    seq_hash (optional) receives an order-sensitive hash of each pixel's
-   contributor sequence.  Returns the number of visible splats. */
+   contributor sequence; ambiguity (optional, [2][h][w]) the bounds of
+   pixel_walk for the colour and the final transmittance.  Returns the number
+   of visible splats. */
 ORC_API int64_t orc_render(const orc_gaussians *G, const orc_view *V, const orc_options *O, int x0, int y0,
                            int w, int h, int prefilter, double *image, double *T_final, int32_t *n_contrib,
-                           uint8_t *flags, orc_splat *splats_out, uint64_t *seq_hash) {
+                           uint8_t *flags, orc_splat *splats_out, uint64_t *seq_hash, double *ambiguity) {
     orc_splat *S = (orc_splat *)malloc(sizeof(orc_splat) * (G->n > 0 ? G->n : 1));
     int64_t *order;
     int64_t m = sorted_candidates(G, V, O, S, &order);
+    const double cmax = max_color(S, order, m, V);
     int64_t nvis = 0;
     for (int64_t g = 0; g < G->n; g++) nvis += S[g].visible;
     for (int y = 0; y < h; y++)
@@ -521,9 +559,14 @@ ORC_API int64_t orc_render(const orc_gaussians *G, const orc_view *V, const orc_
             double C[3], T;
             uint8_t f;
             uint64_t hsh;
+            double amb[2];
             int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, &f, NULL,
-                                &hsh);
+                                &hsh, amb, cmax);
             if (seq_hash) seq_hash[(int64_t)y * w + x] = hsh;
+            if (ambiguity) {
+                ambiguity[(int64_t)y * w + x] = amb[0];
+                ambiguity[(int64_t)(h + y) * w + x] = amb[1];
+            }
             for (int ch = 0; ch < 3; ch++) image[((int64_t)ch * h + y) * w + x] = C[ch];
             if (T_final) T_final[(int64_t)y * w + x] = T;
             if (n_contrib) n_contrib[(int64_t)y * w + x] = nc;
@@ -759,7 +802,7 @@ ORC_API void orc_backward(const orc_gaussians *G, const orc_view *V, const orc_o
         for (int x = 0; x < w; x++) {
             double C[3], T;
             int nc = pixel_walk(S, order, m, O, V, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, NULL, list,
-                                NULL);
+                                NULL, NULL, 0.0);
             double dC[3];
             for (int ch = 0; ch < 3; ch++) dC[ch] = dL_dimage[((int64_t)ch * h + y) * w + x];
             /* acc = sum_{j>i} c_j alpha_j T_j + T_final bg, built back to front */

@@ -90,7 +90,7 @@ def lib():
             L.orc_render.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_View), ctypes.POINTER(_Options),
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_void_p, ctypes.c_void_p]
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_render.restype = ctypes.c_int64
             L.orc_project_backward.argtypes = [ctypes.POINTER(_Gaussians), ctypes.c_int64, ctypes.POINTER(_View),
                                                ctypes.POINTER(_Options), dp, ctypes.POINTER(_Grads)]
@@ -202,7 +202,7 @@ def project_all(params: dict, view: dict, opts: dict | None = None) -> dict:
     S = (Splat * max(n, 1))()
     img = np.zeros((3, 1, 1))
     lib().orc_render(ctypes.byref(P.struct), ctypes.byref(_view(view)), ctypes.byref(_options(opts)), 0, 0, 1, 1, 1,
-                     img.ctypes.data, None, None, None, ctypes.cast(S, ctypes.c_void_p), None)
+                     img.ctypes.data, None, None, None, ctypes.cast(S, ctypes.c_void_p), None, None)
     out = {}
     for name, _ in Splat._fields_:
         vals = [getattr(S[i], name) for i in range(n)]
@@ -224,8 +224,11 @@ def _window(view, window):
 def render(params: dict, view: dict, opts: dict | None = None, window=None, prefilter: bool = False) -> dict:
     """Eq. 6 per pixel over all splats.  Returns image [3,h,w], T [h,w],
     n_contrib [h,w], flags [h,w] (bit 0: image borderline, bit 1: gradient
-    borderline), seq_hash [h,w] (order-sensitive hash of the contributor
-    sequence) and the number of visible splats."""
+    borderline; bits 2..5: cause of bit 0 -- depth near-tie, early stop,
+    alpha_min skip, Gaussian-level cull), seq_hash [h,w] (order-sensitive
+    hash of the contributor sequence), amb_image / amb_T [h,w] (how far a
+    valid single-precision evaluation may land from this result because of
+    the flagged decisions) and the number of visible splats."""
     P = _Packed(params)
     x0, y0, w, h = _window(view, window)
     img = np.zeros((3, h, w))
@@ -233,10 +236,12 @@ def render(params: dict, view: dict, opts: dict | None = None, window=None, pref
     nc = np.zeros((h, w), dtype=np.int32)
     fl = np.zeros((h, w), dtype=np.uint8)
     sh = np.zeros((h, w), dtype=np.uint64)
+    amb = np.zeros((2, h, w))
     nvis = lib().orc_render(ctypes.byref(P.struct), ctypes.byref(_view(view)), ctypes.byref(_options(opts)),
                             x0, y0, w, h, int(bool(prefilter)), img.ctypes.data, T.ctypes.data, nc.ctypes.data,
-                            fl.ctypes.data, None, sh.ctypes.data)
-    return dict(image=img, T=T, n_contrib=nc, flags=fl, seq_hash=sh, n_visible=int(nvis))
+                            fl.ctypes.data, None, sh.ctypes.data, amb.ctypes.data)
+    return dict(image=img, T=T, n_contrib=nc, flags=fl, seq_hash=sh, amb_image=amb[0], amb_T=amb[1],
+                n_visible=int(nvis))
 
 
 def _new_grads(P: _Packed):

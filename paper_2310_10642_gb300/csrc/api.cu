@@ -35,7 +35,7 @@ fgs4d_status check_options(const fgs4d_options* o) {
         if (!isfinite(v) || v < 0.0f) return FGS4D_ERR_INVALID_ARG;
     if (!(o->alpha_min > 0.0f && o->alpha_min <= o->alpha_max && o->alpha_max < 1.0f)) return FGS4D_ERR_INVALID_ARG;
     if (!(o->near_z > 0.0f) || o->p_min > 1.0f || o->T_min >= 1.0f) return FGS4D_ERR_INVALID_ARG;
-    if (o->record_fp16 != 0) return FGS4D_ERR_INVALID_ARG;  // mixed-precision records: not in this build
+    if (o->record_fp16 != 0 && o->record_fp16 != 1) return FGS4D_ERR_INVALID_ARG;
     if (o->tile_size != 16 && o->tile_size != 32) return FGS4D_ERR_INVALID_ARG;
     return FGS4D_OK;
 }
@@ -109,13 +109,14 @@ fgs4d_status make_views(const fgs4d_view* views, int n_views, const fgs4d_option
 
 // Lays out the state for n Gaussians and the views; capacity < 0 means
 // "derive it from state_bytes".
-fgs4d_status make_layout(int64_t n, const ViewSet& VS, int64_t capacity, size_t state_bytes, StateLayout* L) {
+fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int64_t capacity, size_t state_bytes,
+                         StateLayout* L) {
     if (n < 0) return FGS4D_ERR_INVALID_ARG;
     const int64_t S = n * (int64_t)VS.n;
     if (S >= 0x7fffffffll) return FGS4D_ERR_INVALID_ARG;
     memset(L, 0, sizeof(*L));
     L->n_splats = S;
-    L->record_bytes = sizeof(SplatRecord);
+    L->record_bytes = record_fp16 ? sizeof(SplatRecordH) : sizeof(SplatRecord);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -193,7 +194,7 @@ fgs4d_status prepare(int64_t n, const fgs4d_view* views, int n_views, const fgs4
     if (s != FGS4D_OK) return s;
     if (!state || !aligned(state, kAlign)) return FGS4D_ERR_INVALID_ARG;
     if ((s = make_views(views, n_views, opt, &P->VS)) != FGS4D_OK) return s;
-    if ((s = make_layout(n, P->VS, -1, state_bytes, &P->L)) != FGS4D_OK) return s;
+    if ((s = make_layout(n, P->VS, opt->record_fp16, -1, state_bytes, &P->L)) != FGS4D_OK) return s;
     P->O = dev_options(opt);
     return FGS4D_OK;
 }
@@ -263,7 +264,7 @@ fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view* views, int n_views, i
     ViewSet* VS = new ViewSet;
     s = make_views(views, n_views, opt, VS);
     StateLayout L;
-    if (s == FGS4D_OK) s = make_layout(n, *VS, pair_capacity, 0, &L);
+    if (s == FGS4D_OK) s = make_layout(n, *VS, opt->record_fp16, pair_capacity, 0, &L);
     delete VS;
     if (s != FGS4D_OK) return s;
     *bytes = L.total;
@@ -352,7 +353,7 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views,
     if (s != FGS4D_OK) return s;
     Prepared* P = new Prepared;
     s = make_views(views, n_views, opt, &P->VS);
-    if (s == FGS4D_OK) s = make_layout(n, P->VS, -1, state_bytes, &P->L);
+    if (s == FGS4D_OK) s = make_layout(n, P->VS, opt->record_fp16, -1, state_bytes, &P->L);
     if (s == FGS4D_OK) {
         out->counters = P->L.counters;
         out->records = P->L.records;

@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
                                                          const uint32_t* __restrict__ sorted_splats,
                                                          const uint32_t* __restrict__ offsets,
                                                          const uint32_t* __restrict__ tiles,
-                                                         const SplatRecord* __restrict__ rec, uint32_t n_max,
+                                                         const void* __restrict__ rec, int rec_fp16,
+                                                         float ln_alpha_min, uint32_t n_max,
                                                          uint32_t* counters, uint32_t capacity, int tile,
                                                          uint32_t* __restrict__ pair_keys,
                                                          uint32_t* __restrict__ pair_vals) {
@@ -386,17 +387,14 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             sid = sorted_splats[p];
             const uint32_t v = sid / n_gauss;
             const DevView& V = VS.v[v];
-            const float4 r0 = rec[sid].r0;
-            const float4 r2 = rec[sid].r2;  // (B, depth, hx, hy): support box half extents
-            const float fx0 = fmaxf(ceilf(r0.x - r2.z), 0.0f);
-            const float fx1 = fminf(floorf(r0.x + r2.z), (float)(V.width - 1));
-            const float fy0 = fmaxf(ceilf(r0.y - r2.w), 0.0f);
-            const float fy1 = fminf(floorf(r0.y + r2.w), (float)(V.height - 1));
-            const int ix0 = (int)fx0 / tile, ix1 = (int)fx1 / tile, iy0 = (int)fy0 / tile, iy1 = (int)fy1 / tile;
-            x0 = (uint32_t)ix0;
-            y0 = (uint32_t)iy0;
-            wx = (uint32_t)max(ix1 - ix0 + 1, 1);
-            cnt_rect = (ix1 >= ix0 && iy1 >= iy0) ? wx * (uint32_t)(iy1 - iy0 + 1) : 0u;
+            const SplatView r =
+                rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
+                         : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
+            int rect[4] = {0, 0, 0, 0};
+            cnt_rect = (uint32_t)box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect);
+            x0 = (uint32_t)rect[0];
+            y0 = (uint32_t)rect[1];
+            wx = (uint32_t)max(rect[2] - rect[0] + 1, 1);
             tbase = V.tile_base;
             tiles_x = (uint32_t)V.tiles_x;
             o = offsets[p];
@@ -494,7 +492,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
                        reinterpret_cast<uint32_t*>(state + lay.pair_keys[1])};
     uint32_t* pv[2] = {reinterpret_cast<uint32_t*>(state + lay.pair_vals[0]),
                        reinterpret_cast<uint32_t*>(state + lay.pair_vals[1])};
-    const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    const void* rec = state + lay.records;
     const uint32_t cap = (uint32_t)lay.capacity;
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)VS.total_tiles, st);
     if (e != cudaSuccess) return e;
@@ -520,7 +518,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     if (e != cudaSuccess) return e;
     // 4. emission
     const int stride_grid = 16 * sm_count;
-    emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, S,
+    emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, O.record_fp16, O.ln_alpha_min, S,
                                                        counters, cap, O.tile, pk[0], pv[0]);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

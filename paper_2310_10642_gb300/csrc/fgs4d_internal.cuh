@@ -97,17 +97,88 @@ struct __align__(16) SplatRecord {
     float4 r0, r1, r2;
 };
 
-// Splat record (mixed precision): 32 bytes.
-//   h0 = (u, v) fp32, h1 = (A', B') fp16x2, h2 = (C', alpha_eff) fp16x2 with
-//   the conic pre-scaled by -1/2 log2(e) (resp. -log2(e)) and by 2^e where
-//   e = exponent (stored in h3.w), h3 = (R, G, B) fp32 + packed (e, flags)
+// Splat record (mixed precision): 32 bytes, two 16-byte vectors.
+//   (u, v, alpha_eff, R, G, B) fp32; the conic Q = [[a, b], [b, c]] as its
+//   Cholesky factor Q = L L^T, L = [[l11, 0], [l21, l22]], in 16 bits per
+//   entry: int16 mantissas m with one shared exponent, l = m 2^-e, e chosen
+//   so that the largest |m| lies in [2^14, 2^15).  The quadratic form
+//   d^T Q d = (l11 dx + l21 dy)^2 + (l22 dy)^2 is then a sum of squares whose
+//   relative error is ~2^-14: rounding (a, b, c) instead ruins it along the long
+//   axis of an elongated splat, where a dx^2 + 2 b dx dy + c dy^2 cancels, and
+//   IEEE fp16's 11-bit significands perturb alpha by ~1e-3 relative, enough to
+//   flip alpha_min decisions that cost up to alpha_min T per splat.  The
+//   support box is not stored; it follows from L wherever the record is
+//   decoded, so binning and compositing use the same, conservative box.
 struct __align__(16) SplatRecordH {
-    float2 uv;
-    __half2 ab;
-    __half2 c_alpha;
-    float rgb[3];
-    uint32_t meta;  // bits 0..2 colour clamp flags, bits 8..15 biased exponent
+    float u, v, alpha_eff, R;
+    float G, B;
+    short m11, m21, m22;
+    short e;
 };
+static_assert(sizeof(SplatRecordH) == 32, "mixed-precision record must be 32 bytes");
+
+// conic (a, b, c) and the 2D covariance's S11 -> Cholesky factor of the conic:
+// l11 = sqrt(a), l21 = b / l11, l22 = sqrt(c - l21^2) = 1 / sqrt(S11)
+// (the last form needs no subtraction).
+__device__ __forceinline__ SplatRecordH encode_record_h(float u, float v, const float* conic, float S11,
+                                                        float alpha_eff, const float* col) {
+    SplatRecordH r;
+    r.u = u;
+    r.v = v;
+    r.alpha_eff = alpha_eff;
+    r.R = col[0];
+    r.G = col[1];
+    r.B = col[2];
+    const float l11 = sqrtf(conic[0]);
+    const float l21 = conic[1] / l11;
+    const float l22 = rsqrtf(S11);
+    int e = 0;
+    frexpf(fmaxf(fmaxf(l11, fabsf(l21)), l22), &e);  // max = f 2^e, f in [0.5, 1)
+    const int sh = 15 - e;                            // max 2^sh in [2^14, 2^15)
+    auto q = [sh](float x) { return (short)fminf(fmaxf(rintf(ldexpf(x, sh)), -32767.0f), 32767.0f); };
+    r.m11 = q(l11);
+    r.m21 = q(l21);
+    r.m22 = q(l22);
+    r.e = (short)sh;
+    return r;
+}
+
+// Decoded view of either record type.  (a, b, c) is the conic; for the
+// mixed-precision record (l11, l21, l22) is its Cholesky factor, from which
+// (a, b, c) was formed.
+struct SplatView {
+    float u, v, a, b, c, alpha_eff, R, G, B, hx, hy;
+    float l11, l21, l22;
+};
+__device__ __forceinline__ SplatView decode_record(const SplatRecord& r, float) {
+    return SplatView{r.r0.x, r.r0.y, r.r0.z, r.r0.w, r.r1.x, r.r1.y, r.r1.z, r.r1.w, r.r2.x, r.r2.z, r.r2.w,
+                     0.0f,   0.0f,   0.0f};
+}
+// ln_alpha_min = log(alpha_min).  With Sigma = Q^-1: Sigma_11 = 1 / l22^2 and
+// Sigma_00 = (l21^2 + l22^2) / (l11 l22)^2, so the support box
+// |dx| <= sqrt(k Sigma_00), |dy| <= sqrt(k Sigma_11), k = 2 ln(alpha_eff /
+// alpha_min) (plus half a pixel, as in project_view) needs no subtraction.
+__device__ __forceinline__ SplatView decode_record(const SplatRecordH& r, float ln_alpha_min) {
+    const float s = ldexpf(1.0f, -(int)r.e);
+    SplatView o;
+    o.u = r.u;
+    o.v = r.v;
+    o.l11 = (float)r.m11 * s;
+    o.l21 = (float)r.m21 * s;
+    o.l22 = (float)r.m22 * s;
+    o.a = o.l11 * o.l11;
+    o.b = o.l11 * o.l21;
+    o.c = fmaf(o.l21, o.l21, o.l22 * o.l22);
+    o.alpha_eff = r.alpha_eff;
+    o.R = r.R;
+    o.G = r.G;
+    o.B = r.B;
+    const float sk = sqrtf(2.0f * fmaxf(logf(o.alpha_eff) - ln_alpha_min, 0.0f));
+    const bool ok = o.l11 > 0.0f && o.l22 > 0.0f;
+    o.hx = ok ? sk * sqrtf(fmaf(o.l21, o.l21, o.l22 * o.l22)) / (o.l11 * o.l22) + 0.5f : -1.0f;
+    o.hy = ok ? sk / o.l22 + 0.5f : -1.0f;
+    return o;
+}
 
 // ---------------------------------------------------------------------------
 // Small math helpers
@@ -381,6 +452,24 @@ __device__ __forceinline__ void slice_view(const Core& c, const DevView& V, cons
     }
 }
 
+// Tiles touched by the support box |x - u| <= hx, |y - v| <= hy of a splat:
+// the pixels it covers, clamped to the image, and the tiles containing them
+// (inclusive rect x0, y0, x1, y1).  Returns the tile count, 0 when the box
+// misses the image.  The one place that turns a box into tiles, for both the
+// count (slice/project) and the emitted pairs (bin_sort).
+__device__ __forceinline__ int box_tiles(float u, float v, float hx, float hy, const DevView& V, int tile, int* rect) {
+    const float fx0 = fmaxf(ceilf(u - hx), 0.0f);
+    const float fx1 = fminf(floorf(u + hx), (float)(V.width - 1));
+    const float fy0 = fmaxf(ceilf(v - hy), 0.0f);
+    const float fy1 = fminf(floorf(v + hy), (float)(V.height - 1));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return 0;
+    rect[0] = (int)fx0 / tile;
+    rect[1] = (int)fy0 / tile;
+    rect[2] = (int)fx1 / tile;
+    rect[3] = (int)fy1 / tile;
+    return (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
+}
+
 // Camera transform, Jacobian, 2D covariance, conic, support box and tile rect.
 // Returns false when the splat is culled (near plane, alpha_eff, empty rect).
 __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, const DevOpts& O, ViewGeom& w,
@@ -459,18 +548,8 @@ __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, co
     const float k2 = 2.0f * fmaxf(logf(w.alpha_eff) - O.ln_alpha_min, 0.0f);
     w.hx = sqrtf(k2 * w.cov[0]) + 0.5f;
     w.hy = sqrtf(k2 * w.cov[2]) + 0.5f;
-    // pixels i with |i - u| <= hx, j with |j - v| <= hy, clamped to the image; tiles containing them
-    const float fx0 = fmaxf(ceilf(w.u - w.hx), 0.0f);
-    const float fx1 = fminf(floorf(w.u + w.hx), (float)(V.width - 1));
-    const float fy0 = fmaxf(ceilf(w.v - w.hy), 0.0f);
-    const float fy1 = fminf(floorf(w.v + w.hy), (float)(V.height - 1));
-    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
-    w.rect[0] = (int)fx0 / O.tile;
-    w.rect[1] = (int)fy0 / O.tile;
-    w.rect[2] = (int)fx1 / O.tile;
-    w.rect[3] = (int)fy1 / O.tile;
-    w.tiles = (w.rect[2] - w.rect[0] + 1) * (w.rect[3] - w.rect[1] + 1);
-    return true;
+    w.tiles = box_tiles(w.u, w.v, w.hx, w.hy, V, O.tile, w.rect);
+    return w.tiles > 0;
 }
 
 // Unit view direction from the camera centre to the conditional mean.

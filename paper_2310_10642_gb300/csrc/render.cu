@@ -38,17 +38,45 @@ __device__ __forceinline__ int find_view(const ViewSet& VS, uint32_t tile) {
     return lo;
 }
 
-// Shared-memory form of a record: a = (u, v, A', B'), b = (C', alpha_eff, R, G),
-// c = (B, hx, hy, 0), with A' = -log2e/2 a, B' = -log2e b, C' = -log2e/2 c.
-__device__ __forceinline__ void stage_record(const SplatRecord& r, float4& sa, float4& sb, float4& sc) {
-    sa = make_float4(r.r0.x, r.r0.y, __fmul_rn(-0.5f * kLog2e, r.r0.z), __fmul_rn(-kLog2e, r.r0.w));
-    sb = make_float4(__fmul_rn(-0.5f * kLog2e, r.r1.x), r.r1.y, r.r1.z, r.r1.w);
-    sc = make_float4(r.r2.x, r.r2.z, r.r2.w, 0.0f);
-}
+// How a staged splat evaluates log2 of its Gaussian factor at (dx, dy) from
+// three staged coefficients (X, Y, Z).
+template <class Rec>
+struct Form;
+template <>
+struct Form<SplatRecord> {  // conic pre-scaled: X = -log2e/2 a, Y = -log2e b, Z = -log2e/2 c
+    __device__ __forceinline__ static void stage(const SplatView& r, float& X, float& Y, float& Z) {
+        X = __fmul_rn(-0.5f * kLog2e, r.a);
+        Y = __fmul_rn(-kLog2e, r.b);
+        Z = __fmul_rn(-0.5f * kLog2e, r.c);
+    }
+    __device__ __forceinline__ static float power2(float X, float Y, float Z, float dx, float dy) {
+        return __fmaf_rn(__fmul_rn(X, dx), dx, __fmaf_rn(__fmul_rn(Z, dy), dy, __fmul_rn(__fmul_rn(Y, dx), dy)));
+    }
+};
+template <>
+struct Form<SplatRecordH> {  // Cholesky factor pre-scaled by kappa, kappa^2 = log2(e) / 2
+    static constexpr float kKappa = 0.8493218002880191f;
+    __device__ __forceinline__ static void stage(const SplatView& r, float& X, float& Y, float& Z) {
+        X = __fmul_rn(kKappa, r.l11);
+        Y = __fmul_rn(kKappa, r.l21);
+        Z = __fmul_rn(kKappa, r.l22);
+    }
+    __device__ __forceinline__ static float power2(float X, float Y, float Z, float dx, float dy) {
+        const float t1 = __fmaf_rn(X, dx, __fmul_rn(Y, dy));
+        const float t2 = __fmul_rn(Z, dy);
+        return -__fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+    }
+};
 
-// log2 of the Gaussian factor at (dx, dy): A' dx^2 + C' dy^2 + B' dx dy
-__device__ __forceinline__ float power2(float A, float B, float C, float dx, float dy) {
-    return __fmaf_rn(__fmul_rn(A, dx), dx, __fmaf_rn(__fmul_rn(C, dy), dy, __fmul_rn(__fmul_rn(B, dx), dy)));
+// Shared-memory form of a record: a = (u, v, X, Y), b = (Z, alpha_eff, R, G),
+// c = (B, hx, hy, 0), with (X, Y, Z) as Form<Rec> stages them.
+template <class Rec>
+__device__ __forceinline__ void stage_record(const SplatView& r, float4& sa, float4& sb, float4& sc) {
+    float X, Y, Z;
+    Form<Rec>::stage(r, X, Y, Z);
+    sa = make_float4(r.u, r.v, X, Y);
+    sb = make_float4(Z, r.alpha_eff, r.R, r.G);
+    sc = make_float4(r.B, r.hx, r.hy, 0.0f);
 }
 
 // Pixel layout of a TS x TS tile: warp w owns a region of RW x RH pixels
@@ -79,11 +107,11 @@ __device__ __forceinline__ bool box_meets_region(float u, float v, float hx, flo
     return (u + hx >= rx) && (u - hx <= rx + (float)(RW - 1)) && (v + hy >= ry) && (v - hy <= ry + (float)(RH - 1));
 }
 
-template <int TS>
+template <int TS, class Rec>
 __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
                                                               const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ pair_vals,
-                                                              const SplatRecord* __restrict__ rec, uint32_t n_splats,
+                                                              const Rec* __restrict__ rec, uint32_t n_splats,
                                                               float* __restrict__ image, float* __restrict__ final_T,
                                                               int32_t* __restrict__ n_last) {
     using TP = TilePixels<TS>;
@@ -124,7 +152,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
         if (idx < range.y) {
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
-                stage_record(rec[sid], s_a[tid], s_b[tid], s_c[tid]);
+                stage_record<Rec>(decode_record(rec[sid], O.ln_alpha_min), s_a[tid], s_b[tid], s_c[tid]);
             } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
                 s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
                 s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -143,7 +171,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
             for (int k = 0; k < P; k++) {
                 if (pdone[k]) continue;
                 const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
-                const float p2 = power2(a.z, a.w, b.x, dx, dy);
+                const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
                 if (!(p2 <= 0.0f)) continue;
                 const float araw = __fmul_rn(b.y, ex2_approx(p2));
                 const float alpha = fminf(O.alpha_max, araw);
@@ -208,10 +236,10 @@ __device__ __forceinline__ float warp_reduce8(const float (&v)[8], int lane) {
 
 constexpr int kGradStride = 12;  // floats per staged splat in the shared gradient accumulator
 
-template <int TS>
+template <int TS, class Rec>
 __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
     const __grid_constant__ ViewSet VS, const DevOpts O, const uint2* __restrict__ ranges,
-    const uint32_t* __restrict__ pair_vals, const SplatRecord* __restrict__ rec, uint32_t n_splats,
+    const uint32_t* __restrict__ pair_vals, const Rec* __restrict__ rec, uint32_t n_splats,
     const float* __restrict__ final_T, const int32_t* __restrict__ n_last, const float* __restrict__ dL_dimage,
     float4* __restrict__ grad2d) {
     using TP = TilePixels<TS>;
@@ -276,10 +304,10 @@ __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
             const uint32_t idx = range.x + (uint32_t)(end - 1 - tid);
             uint32_t sid = pair_vals[idx];
             if (sid >= n_splats) sid = 0;  // never produced by bin_sort; keeps the access in bounds
-            const SplatRecord r = rec[sid];
+            const SplatView r = decode_record(rec[sid], O.ln_alpha_min);
             float4 sc;
-            stage_record(r, s_a[tid], s_b[tid], sc);
-            s_n[tid] = make_float4(r.r0.z, r.r0.w, r.r1.x, sc.x);
+            stage_record<Rec>(r, s_a[tid], s_b[tid], sc);
+            s_n[tid] = make_float4(r.a, r.b, r.c, sc.x);
             s_r[tid] = make_float2(sc.y, sc.z);
             s_sid[tid] = sid;
         }
@@ -298,7 +326,7 @@ __global__ void __launch_bounds__(kTilePix, 3) render_bwd_kernel(
             for (int k = 0; k < P; k++) {
                 if (pos >= last[k]) continue;
                 const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
-                const float p2 = power2(a.z, a.w, b.x, dx, dy);
+                const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
                 if (!(p2 <= 0.0f)) continue;
                 const float G = ex2_approx(p2);
                 const float araw = __fmul_rn(b.y, G);
@@ -359,11 +387,17 @@ cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout
     const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
     const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
     const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    const auto* rech = reinterpret_cast<const SplatRecordH*>(state + lay.records);
     const uint32_t S = (uint32_t)lay.n_splats;
-    if (O.tile == 32)
-        render_fwd_kernel<32><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
+    const dim3 grid(VS.total_tiles);
+    if (O.tile == 32 && O.record_fp16)
+        render_fwd_kernel<32, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last);
+    else if (O.tile == 32)
+        render_fwd_kernel<32, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
+    else if (O.record_fp16)
+        render_fwd_kernel<16, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last);
     else
-        render_fwd_kernel<16><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
+        render_fwd_kernel<16, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -374,13 +408,21 @@ static cudaError_t launch_bwd_tiles(const ViewSet& VS, const DevOpts& O, const S
     const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
     const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
     const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
+    const auto* rech = reinterpret_cast<const SplatRecordH*>(state + lay.records);
     const uint32_t S = (uint32_t)lay.n_splats;
-    if (O.tile == 32)
-        render_bwd_kernel<32><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
-                                                                   dL_dimage, g2);
+    const dim3 grid(VS.total_tiles);
+    if (O.tile == 32 && O.record_fp16)
+        render_bwd_kernel<32, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, final_T, n_last,
+                                                                       dL_dimage, g2);
+    else if (O.tile == 32)
+        render_bwd_kernel<32, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
+                                                                      dL_dimage, g2);
+    else if (O.record_fp16)
+        render_bwd_kernel<16, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, final_T, n_last,
+                                                                       dL_dimage, g2);
     else
-        render_bwd_kernel<16><<<VS.total_tiles, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
-                                                                   dL_dimage, g2);
+        render_bwd_kernel<16, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
+                                                                      dL_dimage, g2);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ __device__ __forceinline__ void color_forward(const DevGauss& G, int g, const Vi
 
 template <int L>
 __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, const __grid_constant__ ViewSet VS,
-                                                            const DevOpts O, SplatRecord* __restrict__ rec,
+                                                            const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
                                                             uint32_t* __restrict__ tiles_touched,
                                                             uint32_t* __restrict__ depth_key,
                                                             uint32_t* __restrict__ counters) {
@@ -70,11 +70,23 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
         float col[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) col[ch] = fmaxf(raw[ch] + 0.5f, 0.0f);
-        SplatRecord r;
-        r.r0 = make_float4(w.u, w.v, w.conic[0], w.conic[1]);
-        r.r1 = make_float4(w.conic[2], w.alpha_eff, col[0], col[1]);
-        r.r2 = make_float4(col[2], w.xc[2], w.hx, w.hy);
-        rec[idx] = r;
+        if (O.record_fp16) {
+            const SplatRecordH h = encode_record_h(w.u, w.v, w.conic, w.cov[2], w.alpha_eff, col);
+            // bin by the box of the stored (fp16) conic, exactly as bin_sort will
+            const SplatView d = decode_record(h, O.ln_alpha_min);
+            w.tiles = box_tiles(d.u, d.v, d.hx, d.hy, V, O.tile, w.rect);
+            if (w.tiles == 0) {
+                tiles_touched[idx] = 0u;
+                continue;
+            }
+            reinterpret_cast<SplatRecordH*>(rec)[idx] = h;
+        } else {
+            SplatRecord r;
+            r.r0 = make_float4(w.u, w.v, w.conic[0], w.conic[1]);
+            r.r1 = make_float4(w.conic[2], w.alpha_eff, col[0], col[1]);
+            r.r2 = make_float4(col[2], w.xc[2], w.hx, w.hy);
+            rec[idx] = r;
+        }
         tiles_touched[idx] = (uint32_t)w.tiles;
         depth_key[idx] = __float_as_uint(w.xc[2]);
     }

@@ -44,12 +44,19 @@ def gpu_forward(G, views, opts=None, shs_dtype=None, capacity=None):
 
 
 def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.05):
-    ok = (ref["flags"] & 1) == 0
-    assert 1.0 - ok.mean() <= max_flag_frac, f"too many borderline pixels: {1 - ok.mean():.4f}"
-    err = np.abs(img - ref["image"])[:, ok]
-    assert err.max() <= tol, f"image max-abs {err.max():.3e}"
-    errT = np.abs(Tg - ref["T"])[ok]
-    assert errT.max() <= tol, f"T max-abs {errT.max():.3e}"
+    """Every pixel within tol of the oracle, plus the oracle's ambiguity bound
+    where a discrete decision lies within rounding distance of its threshold
+    (a depth near-tie, an alpha at alpha_min, a stop at T_min, a borderline
+    cull): there single precision may validly take the other branch, and the
+    bound says how far that can move the pixel and T.  Most pixels must carry
+    no such slack, so that the check is not vacuous."""
+    slack = ref["amb_image"] > tol
+    assert slack.mean() <= max_flag_frac, f"too many ambiguous pixels: {slack.mean():.4f}"
+    err = np.abs(img - ref["image"])
+    excess = err - (tol + 1.001 * ref["amb_image"])[None]
+    assert excess.max() <= 0.0, f"image beyond tolerance + ambiguity bound by {excess.max():.3e}"
+    excessT = np.abs(Tg - ref["T"]) - (tol + 1.001 * ref["amb_T"])
+    assert excessT.max() <= 0.0, f"T beyond tolerance + ambiguity bound by {excessT.max():.3e}"
 
 
 # ---------------------------------------------------------------------------- forward
@@ -186,6 +193,61 @@ def test_batched_equals_one_by_one(tile):
         _, _, im1, T1 = gpu_forward(G, [v], dict(tile_size=tile))
         np.testing.assert_array_equal(img, im1[0])
         np.testing.assert_array_equal(T, T1[0])
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_cuda_graph_batch_of_uneven_views(mixed):
+    """The batched workload's shape at reduced size (4 timestamps x 20 arc
+    cameras at one size plus 20 views at half size, 100 views): one whole
+    forward+backward step captured as a CUDA graph.  Replays after the
+    parameters are overwritten in place equal eager launches on the new
+    parameters (images and T bit for bit, gradients up to the order of FP32
+    atomic sums), and the batch equals its views rendered one by one."""
+    from paper_2310_10642_gb300 import render as R
+    c = I.config(2, n=20000, scale=0.15)
+    G, views = c["gaussians"], c["views"]
+    assert len(views) == 100 and len({(v["width"], v["height"]) for v in views}) == 2
+    opts = dict(c["options"], tile_size=32, record_fp16=int(mixed))
+    sd = torch.bfloat16 if mixed else torch.float32
+    p = R.params_to_device(G, shs_dtype=sd)
+    fr = R.Frame(G["logit"].shape[0], views, opts)
+    fr.forward(p)
+    fr._alloc(int(fr.last_counters.n_pairs * 1.5) + 4096)
+    dL = torch.randn(3 * fr.total_pixels, device="cuda", generator=torch.Generator(device="cuda").manual_seed(5))
+    grads = {k: torch.empty(p[k].shape, device="cuda") for k in R.PARAM_KEYS}
+
+    def step():
+        fr.slice_project(p)
+        fr.bin_sort()
+        fr.render()
+        fr.backward(p, dL, grads)
+
+    step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    G2 = I.gaussians(G["logit"].shape[0], 777, G["sh_degree"], G["n_freq"])
+    G2["period"] = G["period"]
+    p2 = R.params_to_device(G2, shs_dtype=sd)
+    for k in R.PARAM_KEYS:
+        p[k].copy_(p2[k])
+    g.replay()
+    torch.cuda.synchronize()
+    assert fr.counters().status == 0
+    img_g, T_g = fr.image.clone(), fr.final_T.clone()
+    grad_g = {k: v.clone() for k, v in grads.items()}
+    step()
+    torch.cuda.synchronize()
+    assert torch.equal(img_g, fr.image) and torch.equal(T_g, fr.final_T)
+    for k in R.PARAM_KEYS:
+        rel = float((grad_g[k] - grads[k]).norm() / grads[k].norm())
+        assert rel < 1e-5, (k, rel)
+    imgs, Ts = fr.split(img_g), fr.split(T_g, 1)
+    for i in (0, 37, 79, 80, 99):
+        f1 = R.Frame(G["logit"].shape[0], [views[i]], opts)
+        f1.forward(p)
+        assert torch.equal(f1.image.view_as(imgs[i]), imgs[i]) and torch.equal(f1.final_T.view_as(Ts[i]), Ts[i])
 
 
 def test_fp64_fallback_for_ill_conditioned_slices():
@@ -374,3 +436,83 @@ def test_autograd_function_l1_loss():
     for k in R.PARAM_KEYS:
         rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
         assert rel < 2e-2, (k, rel)
+
+
+# ---------------------------------------------------------------------------- mixed precision
+MIXED_IMG_TOL = 2e-3
+MIXED_GRAD_TOL = 1e-2
+
+
+@TILES
+def test_mixed_precision_against_fp64_oracle(tile):
+    """BF16 4DSH coefficients + 16-bit block-exponent Cholesky conics in the
+    splat records, FP32 compositing.  Against the oracle fed the same
+    BF16-rounded coefficients the images stay within 1e-3 (the conics' share);
+    against the original FP32 inputs within 3e-3 on this scene, where the BF16
+    rounding of the coefficients alone moves the oracle's own image by up to
+    1.4e-3.  (The 2e-3 bar on the benchmarked workload is
+    test_full_size_workload_crops.)  The path evaluates the renderer at the
+    BF16-rounded coefficients, so its gradient is compared with the oracle's
+    gradient there: at the FP32 coefficients the colour clamp max(c + 1/2, 0)
+    switches for colours within BF16 rounding of zero."""
+    G, views = ragged_scene(n=2500, seed=51)
+    opts = dict(tile_size=tile, record_fp16=1)
+    fr, p, imgs, Ts = gpu_forward(G, views, opts, shs_dtype=torch.bfloat16)
+    G16 = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy())
+    for img, T, v in zip(imgs, Ts, views):
+        assert_image_parity(img, T, O.render(G16, v), tol=1e-3)
+    refs = [O.render(G, v) for v in views]
+    for img, T, ref in zip(imgs, Ts, refs):
+        assert_image_parity(img, T, ref, tol=3e-3)
+    refs16 = [O.render(G16, v) for v in views]
+    dL = masked_dL(views, refs16, 9)
+    gg = grads_gpu(fr, p, dL)
+    go = O.backward_views(G16, views, dL)
+    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
+        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
+        assert rel <= MIXED_GRAD_TOL, (k, rel)
+
+
+# ---------------------------------------------------------------------------- full size
+@pytest.mark.parametrize("mixed", [False, True])
+def test_full_size_workload_crops(mixed):
+    """The benchmarked workload itself (1M clustered Gaussians, 20 views at
+    1352x1014, 32x32 tiles, one launch per stage): 64x64 centre crops of three
+    views against the oracle, and the gradient of a loss on the crops."""
+    c = I.config(3)
+    G, views = c["gaussians"], c["views"]
+    opts = dict(c["options"], tile_size=32, record_fp16=int(mixed))
+    fr, p, imgs, Ts = gpu_forward(G, views, opts, shs_dtype=torch.bfloat16 if mixed else torch.float32)
+    tol = MIXED_IMG_TOL if mixed else IMG_TOL
+    crop = 64
+    picks = [0, 9, 19]
+    dL = [np.zeros((3, v["height"], v["width"])) for v in views]
+    rng = np.random.default_rng(13)
+    for vi in picks:
+        v = views[vi]
+        x0, y0 = v["width"] // 2 - crop // 2, v["height"] // 2 - crop // 2
+        ref = O.render(G, v, window=(x0, y0, crop, crop), prefilter=True)
+        sub = imgs[vi][:, y0:y0 + crop, x0:x0 + crop]
+        subT = Ts[vi][y0:y0 + crop, x0:x0 + crop]
+        # dense clustered scene: thousands of splats per pixel, so more decisions sit near thresholds
+        assert_image_parity(sub, subT, ref, tol=tol, max_flag_frac=0.25)
+        w = rng.normal(size=(3, crop, crop))
+        w[:, ref["flags"] != 0] = 0.0
+        dL[vi][:, y0:y0 + crop, x0:x0 + crop] = w
+    gg = grads_gpu(fr, p, dL)
+    # the mixed path differentiates the renderer at the BF16-rounded coefficients
+    Gref = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy()) if mixed else G
+    go = None
+    for vi in picks[:2]:
+        v = views[vi]
+        x0, y0 = v["width"] // 2 - crop // 2, v["height"] // 2 - crop // 2
+        gv = O.backward(Gref, v, dL[vi][:, y0:y0 + crop, x0:x0 + crop], window=(x0, y0, crop, crop), prefilter=True)
+        gv.pop("grad2d")
+        go = gv if go is None else {k: go[k] + gv[k] for k in go}
+    # the GPU gradient above also holds the third view's crop: recompute without it
+    dL[picks[2]][:] = 0.0
+    gg = grads_gpu(fr, p, dL)
+    gtol = MIXED_GRAD_TOL if mixed else GRAD_TOL
+    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
+        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
+        assert rel <= gtol, (k, rel)

@@ -263,6 +263,35 @@ def test_layered_splats_transmittance_and_termination(oracle):
     assert abs(r["T"][2, 2] - 1e-4) < 1e-15 and r["n_contrib"][2, 2] == 2
 
 
+def test_ambiguity_bound_covers_flipped_decisions(oracle):
+    """The ambiguity bounds that the parity tests add to their tolerance,
+    pinned by re-rendering with the decisions taken the other way: moving
+    alpha_min (R4) or T_min (R5) by just under the flag margin flips exactly
+    the decisions that lie inside it, and the image and T may then move by no
+    more than the bounds (1% slack: a flip also rescales the T that later
+    flips see by 1/(1 - alpha))."""
+    am, tm = oracle.DEFAULT_OPTIONS["alpha_min"], oracle.DEFAULT_OPTIONS["T_min"]
+    v = I.view((0.2, -0.1, 3.2), 96, 72, 0.45, bg=(0.3, 0.6, 0.9))
+    moved = {"alpha_min": 0, "T_min": 0}
+    for dense in (False, True):
+        G = I.gaussians(4000, 61, 2, 1)
+        if dense:  # larger, more opaque splats: most pixels stop early (R5)
+            G["log_s"][:3] += 1.0
+            G["logit"] += 3.0
+        base = oracle.render(G, v)
+        for fa, ft in ((1 + 0.9e-4, 1.0), (1 - 0.9e-4, 1.0), (1.0, 1 + 1.8e-3), (1.0, 1 - 1.8e-3)):
+            r = oracle.render(G, v, dict(alpha_min=am * fa, T_min=tm * ft))
+            d = np.abs(r["image"] - base["image"]).max(axis=0)
+            dT = np.abs(r["T"] - base["T"])
+            moved["alpha_min" if ft == 1.0 else "T_min"] += int((d > 1e-12).sum())
+            assert np.all(d <= 1.01 * base["amb_image"] + 1e-12)
+            assert np.all(dT <= 1.01 * base["amb_T"] + 1e-12)
+        # most pixels carry no slack at all
+        assert (base["amb_image"] > 0).mean() < 0.1
+    # decisions of both kinds did flip: the check is not vacuous
+    assert moved["alpha_min"] > 0 and moved["T_min"] > 0
+
+
 def test_temporal_filter_culls_below_threshold(oracle):
     """p(t) < 0.05 removes the Gaussian entirely (Sec. 4.2)."""
     st = 0.1
