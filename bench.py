@@ -330,10 +330,29 @@ def main():
         "render_backward": npairs * (4 + rd_b) + npix * 20 + nvis * 48 * 2 + n * (17 * 4 + C * shs_b)
         + n * (17 * 4 + C * 4),
     }
+    # compositing and its adjoint are bound by FP32 arithmetic, not bytes: their
+    # algorithmic work is FLOPs per blended (pixel, splat) pair (Eq. 6 forward:
+    # 23, adjoint: 51; FMA = 2, exp = 1), counted by fgs4d_render_stats, against
+    # the FP32 peak 152 SMs x 128 lanes x 2 x SM clock
+    work = frame.render_stats()
+    torch.cuda.synchronize()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    flops = {"render": 23 * work["blended"], "render_backward": 51 * work["blended"]}
+    stage_roof = {}
+    for st_name, ms in stage_ms.items():
+        if st_name in flops:
+            a_ = flops[st_name] / (ms * 1e-3) / 1e12
+            stage_roof[st_name] = dict(bound="alu", achieved=round(a_, 3), peak=round(fp32_peak, 1), unit="TFLOP/s",
+                                       frac=round(a_ / fp32_peak, 4))
+        else:
+            a_ = alg[st_name] / (ms * 1e-3) / 1e9
+            stage_roof[st_name] = dict(bound="hbm", achieved=round(a_, 1), peak=hbm, unit="GB/s",
+                                       frac=round(a_ / hbm, 4))
     dom = max(stage_ms, key=stage_ms.get)
-    achieved = alg[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    roofline = dict(bound="hbm", achieved=round(achieved, 1), peak=hbm, unit="GB/s", frac=round(achieved / hbm, 4),
-                    traffic=None, kernel=dom, peak_source=f"{peak_kind} hbm_gbs")
+    roofline = dict(stage_roof[dom], traffic=None, kernel=dom,
+                    peak_source=("FP32: 152 SMs x 128 lanes x 2 FLOP x max SM clock" if stage_roof[dom]["bound"] == "alu"
+                                 else f"{peak_kind} hbm_gbs"))
 
     # ---- plain FP32 paths on the same GPU: the whole batch, and one view per call
     single = batched_fp32 = None
@@ -420,7 +439,7 @@ def main():
                    fwd_mpix_s=round(fwd_mpix, 3), stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
                    single_view=single, batched_fp32=batched_fp32,
                    batched_vs_single_fp32=round(value / world / single["mpix_s"], 3) if single else None,
-                   roofline=roofline, cpu_baseline=cpu, e2e=e2e, clocks=clk,
+                   roofline=roofline, stage_roofline=stage_roof, work=work, cpu_baseline=cpu, e2e=e2e, clocks=clk,
                    gpu_launches=int(launches))
         print(json.dumps(out))
     if dist:

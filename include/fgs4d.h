@@ -187,6 +187,22 @@ fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int n_views, con
 fgs4d_status fgs4d_render(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
                           size_t state_bytes, float *image, float *final_T, int32_t *n_last, fgs4d_stream stream);
 
+/* fgs4d_render plus a count of the work its walk did; the paper has no
+   counterpart (it measures Eq. 6's cost for throughput accounting).  Writes
+   image, final_T and n_last exactly as fgs4d_render does and ADDS to
+   stats[0..3] (device, 4 uint64, 8-byte aligned, zeroed by the caller):
+     stats[0]  (pixel, splat) pairs with the pixel inside the splat's support
+               box (|x - u| <= hx, |y - v| <= hy) before the pixel stopped,
+     stats[1]  pairs blended into their pixel (alpha >= alpha_min, not stopped),
+     stats[2]  the sum of n_last over all pixels,
+     stats[3]  pairs the kernel evaluated: the pixel had not stopped and the
+               splat's box reached the group of pixels it is culled with.
+   Slower than fgs4d_render (one 64-bit atomic per warp and counter); not
+   meant for the training loop. */
+fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt,
+                                void *state, size_t state_bytes, float *image, float *final_T, int32_t *n_last,
+                                uint64_t *stats, fgs4d_stream stream);
+
 /* Adjoint of slice_project + bin_sort + render: given dL/d(image) (same
    layout as image), writes dL/d(raw parameters) summed over all views into
    grads (overwritten).  Transmittance is recomputed from final_T, not stored

@@ -319,6 +319,22 @@ fgs4d_status fgs4d_render(int64_t n, const fgs4d_view* views, int n_views, const
     return s;
 }
 
+fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt,
+                                void* state, size_t state_bytes, float* image, float* final_T, int32_t* n_last,
+                                uint64_t* stats, fgs4d_stream stream) {
+    if (!image || !final_T || !n_last || !stats) return FGS4D_ERR_INVALID_ARG;
+    if (!aligned(image, 4) || !aligned(final_T, 4) || !aligned(n_last, 4) || !aligned(stats, 8))
+        return FGS4D_ERR_INVALID_ARG;
+    Prepared* P = new Prepared;
+    fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK)
+        s = cuda_status(launch_render_stats(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), image,
+                                            final_T, n_last, reinterpret_cast<unsigned long long*>(stats),
+                                            (cudaStream_t)stream));
+    delete P;
+    return s;
+}
+
 fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* views, int n_views,
                                    const fgs4d_options* opt, void* state, size_t state_bytes, const float* final_T,
                                    const int32_t* n_last, const float* dL_dimage, fgs4d_gaussian_grads* grads,

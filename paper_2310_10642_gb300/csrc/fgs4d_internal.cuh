@@ -572,6 +572,9 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
                             cudaStream_t st, int* out_buf);
 cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
                           float* image, float* final_T, int32_t* n_last, cudaStream_t st);
+cudaError_t launch_render_stats(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
+                                int pair_buf, float* image, float* final_T, int32_t* n_last,
+                                unsigned long long* stats, cudaStream_t st);
 cudaError_t launch_render_backward(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                    int pair_buf, const float* final_T, const int32_t* n_last, const float* dL_dimage,
                                    cudaStream_t st);

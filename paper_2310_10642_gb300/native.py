@@ -118,7 +118,7 @@ class StateLayoutInfo(ctypes.Structure):
 
 EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fgs4d_default_options", "fgs4d_state_size",
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
-           "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc"]
+           "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats"]
 NOALLOC_MAX_SPLATS = 262144
 
 
@@ -157,6 +157,9 @@ def lib(path: str | None = None) -> ctypes.CDLL:
             L.fgs4d_render_backward.argtypes = [ctypes.POINTER(Gaussians), ctypes.POINTER(View), ci,
                                                 ctypes.POINTER(Options), vp, ctypes.c_size_t, vp, vp, vp,
                                                 ctypes.POINTER(GaussianGrads), vp]
+            L.fgs4d_render_stats.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), vp,
+                                             ctypes.c_size_t, vp, vp, vp, vp, vp]
+            L.fgs4d_render_stats.restype = ci
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
             L.fgs4d_render_backward_noalloc.argtypes = L.fgs4d_render_backward.argtypes
             L.fgs4d_render_backward_noalloc.restype = ci
@@ -229,6 +232,12 @@ def fgs4d_render(n: int, views, n_views: int, opts: Options, state: int, state_b
                  final_T: int, n_last: int, stream: int):
     _check("fgs4d_render", lib().fgs4d_render(int(n), views, int(n_views), ctypes.byref(opts), state, state_bytes,
                                                image, final_T, n_last, stream))
+
+
+def fgs4d_render_stats(n: int, views, n_views: int, opts: Options, state: int, state_bytes: int, image: int,
+                       final_T: int, n_last: int, stats: int, stream: int):
+    _check("fgs4d_render_stats", lib().fgs4d_render_stats(int(n), views, int(n_views), ctypes.byref(opts), state,
+                                                           state_bytes, image, final_T, n_last, stats, stream))
 
 
 def fgs4d_render_backward(g: Gaussians, views, n_views: int, opts: Options, state: int, state_bytes: int,

@@ -112,6 +112,17 @@ class Frame:
         N.fgs4d_render(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
                        self.image.data_ptr(), self.final_T.data_ptr(), self.n_last.data_ptr(), _stream(stream))
 
+    def render_stats(self, stream=None) -> dict:
+        """render() plus the work counts of its walk (one synchronisation):
+        pixel-splat pairs inside support boxes, pairs blended, sum of n_last,
+        pairs the kernel evaluated."""
+        st = torch.zeros(4, device=self.device, dtype=torch.int64)
+        N.fgs4d_render_stats(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                             self.image.data_ptr(), self.final_T.data_ptr(), self.n_last.data_ptr(), st.data_ptr(),
+                             _stream(stream))
+        box, blended, walked, evaluated = (int(x) for x in st.cpu())
+        return dict(in_box=box, blended=blended, walked=walked, evaluated=evaluated)
+
     def counters(self, stream=None) -> N.Counters:
         return N.fgs4d_read_counters(self.state.data_ptr(), _stream(stream))
 

@@ -102,3 +102,6 @@ def test_invalid_arguments_rejected_on_host(lib):
     # state smaller than the fixed part
     assert lib.fgs4d_bin_sort(10, v, 2, ctypes.byref(o), 256, 1024, None) == 2
     assert lib.fgs4d_render(10, v, 2, ctypes.byref(o), 256, 1 << 30, None, None, None, None) == 1
+    # work counters: null and misaligned stats are rejected
+    assert lib.fgs4d_render_stats(10, v, 2, ctypes.byref(o), 256, 1 << 30, 256, 512, 768, None, None) == 1
+    assert lib.fgs4d_render_stats(10, v, 2, ctypes.byref(o), 256, 1 << 30, 256, 512, 768, 1028, None) == 1

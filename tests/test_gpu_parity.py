@@ -250,6 +250,30 @@ def test_cuda_graph_batch_of_uneven_views(mixed):
         assert torch.equal(f1.image.view_as(imgs[i]), imgs[i]) and torch.equal(f1.final_T.view_as(Ts[i]), Ts[i])
 
 
+@pytest.mark.parametrize("tile,mixed", [(16, False), (32, False), (32, True)])
+def test_render_stats_count_the_walk(tile, mixed):
+    """fgs4d_render_stats: same image as fgs4d_render; its blended-pair count
+    equals the oracle's contributor count summed over the pixels (up to one
+    per flagged pixel, whose decisions may validly differ); its walk count is
+    the sum of n_last; every blended pair lies inside its splat's box."""
+    G, views = ragged_scene(n=2500, seed=17)
+    opts = dict(tile_size=tile, record_fp16=int(mixed))
+    fr, p, imgs, _ = gpu_forward(G, views, opts, shs_dtype=torch.bfloat16 if mixed else None)
+    img0, T0, last0 = fr.image.clone(), fr.final_T.clone(), fr.n_last.clone()
+    st = fr.render_stats()
+    torch.cuda.synchronize()
+    assert torch.equal(img0, fr.image) and torch.equal(T0, fr.final_T) and torch.equal(last0, fr.n_last)
+    assert st["walked"] == int(fr.n_last.sum())
+    assert st["evaluated"] >= st["in_box"] >= st["blended"] > 0
+    Gr = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy()) if mixed else G
+    refs = [O.render(Gr, v) for v in views]
+    want = sum(int(r["n_contrib"].sum()) for r in refs)
+    slack = sum(int((r["flags"] != 0).sum()) for r in refs)
+    if mixed:  # 16-bit conics move alpha by more than the FP32-sized flag margins
+        slack += int(2e-3 * want)
+    assert abs(st["blended"] - want) <= slack, (st["blended"], want, slack)
+
+
 def test_fp64_fallback_for_ill_conditioned_slices():
     """Gaussians stretched along a space-time diagonal: Sigma_{xyz|t} is a tiny
     difference of large numbers (Eq. 9); the GPU recomputes it in FP64."""
