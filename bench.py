@@ -56,7 +56,10 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
                     help="mixed: BF16 4DSH coefficients + 16-bit conic records; fp32: plain FP32 storage")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly, not as a CUDA graph")
-    ap.add_argument("--tile", type=int, default=32, choices=[16, 32], help="screen tile side")
+    ap.add_argument("--tile", default="auto", choices=["auto", "16", "32"],
+                    help="screen tile side; auto: the autotuner times both on this workload")
+    ap.add_argument("--batch-depth", default="auto", choices=["auto", "32", "64", "128", "256"],
+                    help="splat records staged per shared-memory batch; auto: picked with the tile size")
     return ap.parse_args()
 
 
@@ -116,6 +119,19 @@ def measured_peaks():
         return d, "measured"
     except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def job_throughput(pixels_per_step: int, steps: int, local_ms: float, dist=None, device="cpu") -> tuple:
+    """Whole-job Mpix/s of N replicas: every rank renders pixels_per_step per
+    step; the job takes as long as its slowest rank (max over ranks of the
+    timed region).  Returns (Mpix/s over all ranks, max ms)."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return pixels_per_step * world * steps / (ms * 1e-3) / 1e6, ms
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -180,6 +196,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     import torch
+    from paper_2310_10642_gb300 import autotune as A
     from paper_2310_10642_gb300 import native as N
     from paper_2310_10642_gb300 import render as R
 
@@ -197,10 +214,17 @@ def main():
     G, views, opts = workload_inputs(args.n, args.views, args.scale)
     n = G["logit"].shape[0]
     mixed = args.precision == "mixed"
-    opts_fp32 = dict(opts, tile_size=args.tile, record_fp16=0)
-    opts = dict(opts, tile_size=args.tile, record_fp16=int(mixed))
     p32 = R.params_to_device(G)
     p = R.params_to_device(G, shs_dtype=torch.bfloat16) if mixed else p32
+    opts = dict(opts, record_fp16=int(mixed))
+    tiles = A.TILE_SIZES if args.tile == "auto" else (int(args.tile),)
+    depths = A.BATCH_DEPTHS if args.batch_depth == "auto" else (int(args.batch_depth),)
+    tune_table = None
+    if len(tiles) * len(depths) > 1:  # launch shape from the autotuner, timed on this workload (untimed here)
+        opts, tune_table = A.tune(p, views, opts, cands=A.candidates(tiles, depths), cache=None)
+    else:
+        opts = dict(opts, tile_size=tiles[0], batch_depth=depths[0])
+    opts_fp32 = dict(opts, record_fp16=0)
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda").manual_seed(1234)
     grads = {k: torch.empty(p32[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
@@ -297,12 +321,8 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     total_ms = e_start.elapsed_time(e_end)
-    t_tensor = torch.tensor([total_ms], device="cuda")
-    if dist:
-        dist.all_reduce(t_tensor, op=dist.ReduceOp.MAX)
-    total_ms = float(t_tensor.item())
+    value, total_ms = job_throughput(npix, args.steps, total_ms, dist, device="cuda")
     ms_step = total_ms / args.steps
-    value = npix * world * args.steps / (total_ms * 1e-3) / 1e6
     fwd_ms = stage_ms["slice_project"] + stage_ms["bin_sort"] + stage_ms["render"]
     fwd_mpix = npix / (fwd_ms * 1e-3) / 1e6
 
@@ -430,7 +450,8 @@ def main():
                    unit="Mpix/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms_step, 4),
                    higher_is_better=True, scaling="weak", vs_baseline=None,
                    dtype="f32", data="synthetic",
-                   config=dict(WORKLOAD, n=n, views=V, tile=args.tile, precision=(
+                   config=dict(WORKLOAD, n=n, views=V, tile=opts["tile_size"], batch_depth=opts["batch_depth"],
+                               autotune=tune_table, precision=(
                        "BF16 4DSH coefficients, 16-bit Cholesky conics; FP32 arithmetic" if mixed else "FP32"),
                        cuda_graph=graph is not None,
                        l2="inputs larger than L2 (356 MB mixed / 644 MB FP32 parameters)",

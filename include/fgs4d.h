@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define FGS4D_ABI_VERSION 1
+#define FGS4D_ABI_VERSION 2
 #define FGS4D_MAX_VIEWS 128   /* views per call */
 #define FGS4D_MAX_SH_DEGREE 3 /* L */
 #define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
@@ -120,6 +120,8 @@ typedef struct {
     float conic_cond; /* 1e-4: FP64 2x2 inversion when det/(S00*S11) is below */
     int tile_size;    /* 16 or 32: side of the square screen tiles (binning and compositing);
                          32 bins each splat to ~3x fewer tiles, each thread composites 2x2 pixels */
+    int batch_depth;  /* 256: splat records a tile stages in shared memory per batch while
+                         compositing (32, 64, 128 or 256); results do not depend on it */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but

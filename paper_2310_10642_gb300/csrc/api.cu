@@ -37,6 +37,8 @@ fgs4d_status check_options(const fgs4d_options* o) {
     if (!(o->near_z > 0.0f) || o->p_min > 1.0f || o->T_min >= 1.0f) return FGS4D_ERR_INVALID_ARG;
     if (o->record_fp16 != 0 && o->record_fp16 != 1) return FGS4D_ERR_INVALID_ARG;
     if (o->tile_size != 16 && o->tile_size != 32) return FGS4D_ERR_INVALID_ARG;
+    if (o->batch_depth != 32 && o->batch_depth != 64 && o->batch_depth != 128 && o->batch_depth != 256)
+        return FGS4D_ERR_INVALID_ARG;
     return FGS4D_OK;
 }
 
@@ -53,6 +55,7 @@ DevOpts dev_options(const fgs4d_options* o) {
     d.ln_alpha_min = logf(o->alpha_min);
     d.record_fp16 = o->record_fp16;
     d.tile = o->tile_size;
+    d.batch = o->batch_depth;
     return d;
 }
 
@@ -247,6 +250,7 @@ void fgs4d_default_options(fgs4d_options* o) {
     o->schur_cond = 1e-3f;
     o->conic_cond = 1e-4f;
     o->tile_size = FGS4D_TILE;
+    o->batch_depth = 256;
 }
 
 int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {

@@ -44,7 +44,8 @@ struct DevOpts {
     float schur_cond, conic_cond;
     float ln_alpha_min;
     int record_fp16;
-    int tile;  // screen tile side: 16 or 32
+    int tile;   // screen tile side: 16 or 32
+    int batch;  // records staged per shared-memory batch while compositing: 32..256
 };
 
 // Gaussian parameters (SoA) as the kernels see them.

@@ -177,10 +177,11 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
         pdone[k] = !inside[k];
         done = done && pdone[k];
     }
-    for (uint32_t base = range.x; base < range.y; base += kTilePix) {
+    const int B = O.batch;  // records per batch, <= kTilePix
+    for (uint32_t base = range.x; base < range.y; base += (uint32_t)B) {
         if (__syncthreads_count(done) == kTilePix) break;
         const uint32_t idx = base + tid;
-        if (idx < range.y) {
+        if (tid < B && idx < range.y) {
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
                 stage_record<Rec>(decode_record(rec[sid], O.ln_alpha_min), s_a[tid], s_b[tid], s_c[tid]);
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
             }
         }
         __syncthreads();
-        const int cnt = (int)min((uint32_t)kTilePix, range.y - base);
+        const int cnt = (int)min((uint32_t)B, range.y - base);
         for (int j = 0; j < cnt && !done; j++) {
             const float4 a = s_a[j];
             const float4 c = s_c[j];
@@ -357,8 +358,9 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     if (lane == 0) atomicMax(&s_max, warp_last);
     __syncthreads();
     const int max_last = min(s_max, (int)(range.y - range.x));
-    for (int end = max_last; end > 0; end -= kTilePix) {
-        const int cnt = min(end, kTilePix);
+    const int B = O.batch;  // records per batch, <= kTilePix
+    for (int end = max_last; end > 0; end -= B) {
+        const int cnt = min(end, B);
         __syncthreads();
         if (tid < cnt) {
             const uint32_t idx = range.x + (uint32_t)(end - 1 - tid);

@@ -97,7 +97,7 @@ class Options(ctypes.Structure):
     _fields_ = [("p_min", ctypes.c_float), ("near_z", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("clamp_fov", ctypes.c_float), ("record_fp16", ctypes.c_int), ("schur_cond", ctypes.c_float),
-                ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int)]
+                ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int), ("batch_depth", ctypes.c_int)]
 
 
 class GaussianGrads(ctypes.Structure):
@@ -168,7 +168,7 @@ def lib(path: str | None = None) -> ctypes.CDLL:
             for fn in ("fgs4d_state_size", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render",
                        "fgs4d_render_backward", "fgs4d_read_counters", "fgs4d_state_layout"):
                 getattr(L, fn).restype = ci
-            assert L.fgs4d_abi_version() == 1, "libfgs4d ABI version mismatch"
+            assert L.fgs4d_abi_version() == 2, "libfgs4d ABI version mismatch"
             _lib = L
     return _lib
 

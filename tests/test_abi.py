@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.fgs4d_abi_version() == 1
+    assert lib.fgs4d_abi_version() == 2
     for code in range(6):
         assert len(lib.fgs4d_status_string(code)) > 0
 
@@ -55,6 +55,7 @@ def test_default_options_match_readings(lib):
     assert abs(o.p_min - 0.05) < 1e-7 and abs(o.near_z - 0.2) < 1e-7
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.alpha_max - 0.99) < 1e-7
     assert abs(o.T_min - 1e-4) < 1e-10 and abs(o.dilation - 0.3) < 1e-7
+    assert o.tile_size == 16 and o.batch_depth == 256 and o.record_fp16 == 0
 
 
 def _views(k=2, w=100, h=60):
@@ -83,7 +84,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.fgs4d_state_size(-1, v, 2, 10, ctypes.byref(o), ctypes.byref(size)) == 1
     assert lib.fgs4d_state_size(10, v, 2, -5, ctypes.byref(o), ctypes.byref(size)) == 1
     # bad options
-    for field, val in (("alpha_max", 1.5), ("alpha_min", 0.0), ("near_z", 0.0), ("T_min", float("nan"))):
+    for field, val in (("alpha_max", 1.5), ("alpha_min", 0.0), ("near_z", 0.0), ("T_min", float("nan")),
+                       ("tile_size", 8), ("batch_depth", 100), ("batch_depth", 512), ("record_fp16", 2)):
         bad = N.fgs4d_default_options()
         setattr(bad, field, val)
         assert lib.fgs4d_state_size(10, v, 2, 10, ctypes.byref(bad), ctypes.byref(size)) == 1

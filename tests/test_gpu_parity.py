@@ -274,6 +274,46 @@ def test_render_stats_count_the_walk(tile, mixed):
     assert abs(st["blended"] - want) <= slack, (st["blended"], want, slack)
 
 
+@TILES
+def test_batch_depth_does_not_change_results(tile):
+    """batch_depth only changes how many records a tile stages per batch:
+    images, T and n_last are bit-identical; gradients differ only by the
+    order of FP32 sums."""
+    from paper_2310_10642_gb300 import render as R
+    G, views = ragged_scene(n=2500, seed=19)
+    p = R.params_to_device(G)
+    dL = torch.randn(sum(3 * v["width"] * v["height"] for v in views), device="cuda",
+                     generator=torch.Generator(device="cuda").manual_seed(3))
+    out = {}
+    for B in (32, 64, 128, 256):
+        fr = R.Frame(G["logit"].shape[0], views, dict(tile_size=tile, batch_depth=B))
+        fr.forward(p)
+        g = fr.backward(p, dL)
+        torch.cuda.synchronize()
+        out[B] = (fr.image.clone(), fr.final_T.clone(), fr.n_last.clone(), {k: v.clone() for k, v in g.items()})
+    ref = out[256]
+    for B in (32, 64, 128):
+        img, T, nl, g = out[B]
+        assert torch.equal(img, ref[0]) and torch.equal(T, ref[1]) and torch.equal(nl, ref[2])
+        for k in R.PARAM_KEYS:
+            rel = float((g[k] - ref[3][k]).norm() / ref[3][k].norm())
+            assert rel < 1e-5, (B, k, rel)
+
+
+def test_autotune_returns_a_timed_candidate():
+    from paper_2310_10642_gb300 import autotune as A
+    from paper_2310_10642_gb300 import render as R
+    G, views = ragged_scene(n=2000, seed=23)
+    p = R.params_to_device(G)
+    cands = A.candidates((16, 32), (64, 256))
+    opts, table = A.tune(p, views, dict(record_fp16=0), cands=cands, reps=2, warmup=1, cache=None)
+    assert {"tile_size": opts["tile_size"], "batch_depth": opts["batch_depth"]} in cands
+    assert len(table) == 4 and all(t["ms"] > 0 for t in table)
+    assert min(t["ms"] for t in table) == [t["ms"] for t in table
+                                           if t["tile_size"] == opts["tile_size"]
+                                           and t["batch_depth"] == opts["batch_depth"]][0]
+
+
 def test_fp64_fallback_for_ill_conditioned_slices():
     """Gaussians stretched along a space-time diagonal: Sigma_{xyz|t} is a tiny
     difference of large numbers (Eq. 9); the GPU recomputes it in FP64."""
