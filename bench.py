@@ -112,6 +112,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM traffic of the dominant kernel comes from a committed ncu summary; it is
+# reported only while the kernel's sources hash to the value recorded there.
+KERNEL_SOURCES = ("paper_2310_10642_gb300/csrc/render.cu", "paper_2310_10642_gb300/csrc/fgs4d_internal.cuh")
+STAGE_PROFILE = {"render_backward_2d": "render_bwd_kernel_1M_2views_1352x1014.md",
+                 "render": "render_fwd_kernel_1M_2views_1352x1014.md"}
+
+
+def profiled_traffic(stage: str):
+    """(DRAM bytes per full-size launch, note) for a stage's kernel, or (None, why)."""
+    import hashlib
+    import re
+    name = STAGE_PROFILE.get(stage)
+    if not name:
+        return None, "no ncu summary for this kernel"
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+    except OSError:
+        return None, f"profiles/{name} missing"
+    fields = dict(re.findall(r"^\s*(sources_sha1|dram_bytes_per_launch_full_workload):\s*(\S+)\s*$", text, re.M))
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if fields.get("sources_sha1") != h.hexdigest():
+        return None, f"profiles/{name} is stale: the kernel changed since the capture"
+    if "dram_bytes_per_launch_full_workload" not in fields:
+        return None, f"profiles/{name} has no traffic line"
+    return int(fields["dram_bytes_per_launch_full_workload"]), f"profiles/{name} (2-view capture scaled to 20 views)"
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -228,7 +257,7 @@ def main():
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda").manual_seed(1234)
     grads = {k: torch.empty(p32[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
-    stages = ["slice_project", "bin_sort", "render", "render_backward"]
+    stages = ["slice_project", "bin_sort", "render", "render_backward_2d", "project_backward"]
 
     def sized_frame(vs, o, params):
         """Frame whose pair capacity is sized once, outside the timed region, with headroom."""
@@ -253,9 +282,13 @@ def main():
             fr.render()
             if events is not None:
                 events[3].record(stream)
-            fr.backward(params, dLv, grads)
-            if events is not None:
+            if events is None:
+                fr.backward(params, dLv, grads)  # both adjoint steps in one call
+            else:
+                fr.backward_2d(dLv)
                 events[4].record(stream)
+                fr.project_backward(params, grads)
+                events[5].record(stream)
         return step
 
     def capture(step):
@@ -286,7 +319,7 @@ def main():
     counters = frame.last_counters
 
     # per-stage breakdown: eager launches bracketed by events (untimed for the headline)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(max(3, args.steps))]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(max(3, args.steps))]
     for _ in range(max(3, args.warmup)):
         make_step(frame, p, dL)()
     for e in ev:
@@ -323,7 +356,7 @@ def main():
     total_ms = e_start.elapsed_time(e_end)
     value, total_ms = job_throughput(npix, args.steps, total_ms, dist, device="cuda")
     ms_step = total_ms / args.steps
-    fwd_ms = stage_ms["slice_project"] + stage_ms["bin_sort"] + stage_ms["render"]
+    fwd_ms = stage_ms["slice_project"] + stage_ms["bin_sort"] + stage_ms["render"]  # per step, eager
     fwd_mpix = npix / (fwd_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / time)
@@ -345,10 +378,11 @@ def main():
         + npairs * 20 * ((_bits(frame.layout().total_tiles) + 7) // 8),
         # list ids + gathered records per pair, 20 B written per pixel
         "render": npairs * (4 + rd_b) + npix * 20,
-        # same gathers + dL/dimage, T, n_last per pixel + 48 B gradient record per visible splat (zero+atomics)
-        # + per-Gaussian parameters and gradients
-        "render_backward": npairs * (4 + rd_b) + npix * 20 + nvis * 48 * 2 + n * (17 * 4 + C * shs_b)
-        + n * (17 * 4 + C * 4),
+        # same gathers + dL/dimage, T, n_last per pixel + 48 B gradient record per splat (zeroed) and per
+        # visible splat (atomics)
+        "render_backward_2d": npairs * (4 + rd_b) + npix * 20 + V * n * 48 + nvis * 48,
+        # visible-splat list and its 2D gradients + per-Gaussian parameters read and gradients written
+        "project_backward": nvis * (4 + 48) + n * (17 * 4 + C * shs_b) + n * (17 * 4 + C * 4),
     }
     # compositing and its adjoint are bound by FP32 arithmetic, not bytes: their
     # algorithmic work is FLOPs per blended (pixel, splat) pair (Eq. 6 forward:
@@ -358,7 +392,7 @@ def main():
     torch.cuda.synchronize()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    flops = {"render": 23 * work["blended"], "render_backward": 51 * work["blended"]}
+    flops = {"render": 23 * work["blended"], "render_backward_2d": 51 * work["blended"]}
     stage_roof = {}
     for st_name, ms in stage_ms.items():
         if st_name in flops:
@@ -370,7 +404,13 @@ def main():
             stage_roof[st_name] = dict(bound="hbm", achieved=round(a_, 1), peak=hbm, unit="GB/s",
                                        frac=round(a_ / hbm, 4))
     dom = max(stage_ms, key=stage_ms.get)
-    roofline = dict(stage_roof[dom], traffic=None, kernel=dom,
+    full_workload = (args.n is None and args.views is None and args.scale == 1.0 and mixed
+                     and opts["tile_size"] == 32 and opts["batch_depth"] == 256)
+    traffic, traffic_note = profiled_traffic(dom) if full_workload else (None, "not the profiled workload")
+    kernel_of = {"render_backward_2d": "render_bwd_kernel (stage: 2D-gradient memset + kernel)",
+                 "render": "render_fwd_kernel", "project_backward": "project_backward_kernel + sh_backward_kernel",
+                 "bin_sort": "bin_sort pipeline", "slice_project": "slice_project_kernel"}
+    roofline = dict(stage_roof[dom], traffic=traffic, traffic_source=traffic_note, kernel=kernel_of.get(dom, dom),
                     peak_source=("FP32: 152 SMs x 128 lanes x 2 FLOP x max SM clock" if stage_roof[dom]["bound"] == "alu"
                                  else f"{peak_kind} hbm_gbs"))
 

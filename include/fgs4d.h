@@ -189,6 +189,22 @@ fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int n_views, con
 fgs4d_status fgs4d_render(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
                           size_t state_bytes, float *image, float *final_T, int32_t *n_last, fgs4d_stream stream);
 
+/* The adjoint in its two steps (fgs4d_render_backward runs both):
+   fgs4d_render_backward_2d is the adjoint of Eq. 6 alone.  It writes, into the
+   state's grad2d section (zeroed first), the gradient of the loss w.r.t. each
+   splat's 2D parameters (u, v, conic a, b, c, alpha_eff, R, G, B), summed over
+   the splat's pixels.  fgs4d_project_backward then chains those through the
+   projection, the slice and the 4DSH colour (Eq. 3, 4, 7-11) to dL/d(raw
+   parameters), summed over views, into grads (overwritten); it consumes the
+   grad2d section (reuses it as scratch), so read the 2D gradients before.
+   Same arguments and errors as fgs4d_render_backward. */
+fgs4d_status fgs4d_render_backward_2d(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt,
+                                      void *state, size_t state_bytes, const float *final_T, const int32_t *n_last,
+                                      const float *dL_dimage, fgs4d_stream stream);
+fgs4d_status fgs4d_project_backward(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
+                                    const fgs4d_options *opt, void *state, size_t state_bytes,
+                                    fgs4d_gaussian_grads *grads, fgs4d_stream stream);
+
 /* fgs4d_render plus a count of the work its walk did; the paper has no
    counterpart (it measures Eq. 6's cost for throughput accounting).  Writes
    image, final_T and n_last exactly as fgs4d_render does and ADDS to
@@ -221,10 +237,12 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians *g, const fgs4d_view *v
    below alpha_min); tiles_touched: uint32 per (v, g), 0 = culled;
    ranges: uint32 pairs [start, end) per global tile (tiles of view v follow
    those of views < v, row-major); pair_vals: uint32 splat index v*n + g per
-   list entry, in the buffer that holds the sorted lists. */
+   list entry, in the buffer that holds the sorted lists; grad2d: 12 floats
+   per splat (v*n + g), the first nine dL/d(u, v, a, b, c, alpha_eff, R, G,
+   B) after fgs4d_render_backward_2d. */
 typedef struct {
     uint64_t counters, records, tiles_touched, ranges, pair_vals;
-    uint64_t record_bytes, n_splats, total_tiles, pair_capacity;
+    uint64_t record_bytes, n_splats, total_tiles, pair_capacity, grad2d;
 } fgs4d_state_layout_info;
 
 /* Fills *out for the state of (n, views, opt, state_bytes). Host only. */

@@ -339,6 +339,17 @@ fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view* views, int n_views,
     return s;
 }
 
+static fgs4d_status check_grads(const fgs4d_gaussians* g, const fgs4d_gaussian_grads* grads) {
+    if (!grads) return FGS4D_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        const void* ptrs[] = {grads->mu, grads->log_scale, grads->q_left, grads->q_right, grads->opacity_logit,
+                              grads->shs};
+        for (const void* p : ptrs)
+            if (!p || !aligned(p, 4)) return FGS4D_ERR_INVALID_ARG;
+    }
+    return FGS4D_OK;
+}
+
 fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* views, int n_views,
                                    const fgs4d_options* opt, void* state, size_t state_bytes, const float* final_T,
                                    const int32_t* n_last, const float* dL_dimage, fgs4d_gaussian_grads* grads,
@@ -346,13 +357,8 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* v
     DevGauss G;
     fgs4d_status s = check_gaussians(g, &G);
     if (s != FGS4D_OK) return s;
-    if (!final_T || !n_last || !dL_dimage || !grads) return FGS4D_ERR_INVALID_ARG;
-    if (g->n > 0) {
-        const void* ptrs[] = {grads->mu, grads->log_scale, grads->q_left, grads->q_right, grads->opacity_logit,
-                              grads->shs};
-        for (const void* p : ptrs)
-            if (!p || !aligned(p, 4)) return FGS4D_ERR_INVALID_ARG;
-    }
+    if (!final_T || !n_last || !dL_dimage) return FGS4D_ERR_INVALID_ARG;
+    if ((s = check_grads(g, grads)) != FGS4D_OK) return s;
     Prepared* P = new Prepared;
     s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK) {
@@ -362,6 +368,36 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* v
         if (e == cudaSuccess) e = launch_project_backward(G, P->VS, P->O, P->L, st, *grads, (cudaStream_t)stream);
         s = cuda_status(e);
     }
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_render_backward_2d(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt,
+                                      void* state, size_t state_bytes, const float* final_T, const int32_t* n_last,
+                                      const float* dL_dimage, fgs4d_stream stream) {
+    if (!final_T || !n_last || !dL_dimage) return FGS4D_ERR_INVALID_ARG;
+    if (!aligned(final_T, 4) || !aligned(n_last, 4) || !aligned(dL_dimage, 4)) return FGS4D_ERR_INVALID_ARG;
+    Prepared* P = new Prepared;
+    fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK)
+        s = cuda_status(launch_render_backward(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), final_T,
+                                               n_last, dL_dimage, (cudaStream_t)stream));
+    delete P;
+    return s;
+}
+
+fgs4d_status fgs4d_project_backward(const fgs4d_gaussians* g, const fgs4d_view* views, int n_views,
+                                    const fgs4d_options* opt, void* state, size_t state_bytes,
+                                    fgs4d_gaussian_grads* grads, fgs4d_stream stream) {
+    DevGauss G;
+    fgs4d_status s = check_gaussians(g, &G);
+    if (s != FGS4D_OK) return s;
+    if ((s = check_grads(g, grads)) != FGS4D_OK) return s;
+    Prepared* P = new Prepared;
+    s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK)
+        s = cuda_status(launch_project_backward(G, P->VS, P->O, P->L, static_cast<char*>(state), *grads,
+                                                (cudaStream_t)stream));
     delete P;
     return s;
 }
@@ -384,6 +420,7 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views,
         out->n_splats = (uint64_t)P->L.n_splats;
         out->total_tiles = P->VS.total_tiles;
         out->pair_capacity = (uint64_t)P->L.capacity;
+        out->grad2d = P->L.grad2d;
     }
     delete P;
     return s;

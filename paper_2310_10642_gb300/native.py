@@ -113,12 +113,14 @@ class Counters(ctypes.Structure):
 
 class StateLayoutInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("counters", "records", "tiles_touched", "ranges", "pair_vals",
-                                                "record_bytes", "n_splats", "total_tiles", "pair_capacity")]
+                                                "record_bytes", "n_splats", "total_tiles", "pair_capacity",
+                                                "grad2d")]
 
 
 EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fgs4d_default_options", "fgs4d_state_size",
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
-           "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats"]
+           "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats",
+           "fgs4d_render_backward_2d", "fgs4d_project_backward"]
 NOALLOC_MAX_SPLATS = 262144
 
 
@@ -160,13 +162,19 @@ def lib(path: str | None = None) -> ctypes.CDLL:
             L.fgs4d_render_stats.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), vp,
                                              ctypes.c_size_t, vp, vp, vp, vp, vp]
             L.fgs4d_render_stats.restype = ci
+            L.fgs4d_render_backward_2d.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), vp,
+                                                   ctypes.c_size_t, vp, vp, vp, vp]
+            L.fgs4d_project_backward.argtypes = [ctypes.POINTER(Gaussians), ctypes.POINTER(View), ci,
+                                                 ctypes.POINTER(Options), vp, ctypes.c_size_t,
+                                                 ctypes.POINTER(GaussianGrads), vp]
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
             L.fgs4d_render_backward_noalloc.argtypes = L.fgs4d_render_backward.argtypes
             L.fgs4d_render_backward_noalloc.restype = ci
             L.fgs4d_state_layout.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), ctypes.c_size_t,
                                              ctypes.POINTER(StateLayoutInfo)]
             for fn in ("fgs4d_state_size", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render",
-                       "fgs4d_render_backward", "fgs4d_read_counters", "fgs4d_state_layout"):
+                       "fgs4d_render_backward", "fgs4d_read_counters", "fgs4d_state_layout",
+                       "fgs4d_render_backward_2d", "fgs4d_project_backward"):
                 getattr(L, fn).restype = ci
             assert L.fgs4d_abi_version() == 2, "libfgs4d ABI version mismatch"
             _lib = L
@@ -232,6 +240,20 @@ def fgs4d_render(n: int, views, n_views: int, opts: Options, state: int, state_b
                  final_T: int, n_last: int, stream: int):
     _check("fgs4d_render", lib().fgs4d_render(int(n), views, int(n_views), ctypes.byref(opts), state, state_bytes,
                                                image, final_T, n_last, stream))
+
+
+def fgs4d_render_backward_2d(n: int, views, n_views: int, opts: Options, state: int, state_bytes: int,
+                             final_T: int, n_last: int, dL_dimage: int, stream: int):
+    _check("fgs4d_render_backward_2d", lib().fgs4d_render_backward_2d(int(n), views, int(n_views), ctypes.byref(opts),
+                                                                       state, state_bytes, final_T, n_last, dL_dimage,
+                                                                       stream))
+
+
+def fgs4d_project_backward(g: Gaussians, views, n_views: int, opts: Options, state: int, state_bytes: int,
+                           grads: GaussianGrads, stream: int):
+    _check("fgs4d_project_backward", lib().fgs4d_project_backward(ctypes.byref(g), views, int(n_views),
+                                                                   ctypes.byref(opts), state, state_bytes,
+                                                                   ctypes.byref(grads), stream))
 
 
 def fgs4d_render_stats(n: int, views, n_views: int, opts: Options, state: int, state_bytes: int, image: int,

@@ -144,21 +144,52 @@ class Frame:
             return self.image
         raise RuntimeError("pair capacity could not be sized")
 
-    def backward(self, params: dict, dL_dimage: torch.Tensor, grads: dict | None = None, stream=None,
-                 mean2d: bool = False) -> dict:
-        g = gaussians_struct(params)
+    def _grads(self, params: dict, grads: dict | None, mean2d: bool):
         if grads is None:
             grads = {k: torch.empty(params[k].shape, device=self.device, dtype=torch.float32) for k in PARAM_KEYS}
         if mean2d and "mean2d_abs" not in grads:
             grads["mean2d_abs"] = torch.empty(self.n, device=self.device, dtype=torch.float32)
+        gs = N.GaussianGrads(_ptr(grads["mu"]), _ptr(grads["log_s"]), _ptr(grads["ql"]), _ptr(grads["qr"]),
+                             _ptr(grads["logit"]), _ptr(grads["shs"]), _ptr(grads.get("mean2d_abs")))
+        return grads, gs
+
+    def _dL(self, dL_dimage: torch.Tensor) -> torch.Tensor:
         dL = dL_dimage.contiguous()
         if dL.dtype != torch.float32 or dL.numel() != 3 * self.total_pixels:
             raise ValueError("dL_dimage must be float32 with the image's layout")
-        gs = N.GaussianGrads(_ptr(grads["mu"]), _ptr(grads["log_s"]), _ptr(grads["ql"]), _ptr(grads["qr"]),
-                             _ptr(grads["logit"]), _ptr(grads["shs"]), _ptr(grads.get("mean2d_abs")))
+        return dL
+
+    def backward(self, params: dict, dL_dimage: torch.Tensor, grads: dict | None = None, stream=None,
+                 mean2d: bool = False) -> dict:
+        """Gradients w.r.t. the raw parameters (both adjoint steps in one call)."""
+        g = gaussians_struct(params)
+        grads, gs = self._grads(params, grads, mean2d)
+        dL = self._dL(dL_dimage)
         N.fgs4d_render_backward(g, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
                                 self.final_T.data_ptr(), self.n_last.data_ptr(), dL.data_ptr(), gs, _stream(stream))
         return grads
+
+    def backward_2d(self, dL_dimage: torch.Tensor, stream=None):
+        """Adjoint of the compositing alone: per-splat 2D gradients into the state (see grad2d())."""
+        dL = self._dL(dL_dimage)
+        N.fgs4d_render_backward_2d(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(),
+                                   self.state_bytes, self.final_T.data_ptr(), self.n_last.data_ptr(), dL.data_ptr(),
+                                   _stream(stream))
+
+    def project_backward(self, params: dict, grads: dict | None = None, stream=None, mean2d: bool = False) -> dict:
+        """Second adjoint step: the state's 2D gradients to the raw parameters."""
+        g = gaussians_struct(params)
+        grads, gs = self._grads(params, grads, mean2d)
+        N.fgs4d_project_backward(g, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes, gs,
+                                 _stream(stream))
+        return grads
+
+    def grad2d(self) -> torch.Tensor:
+        """[views, n, 9] view of the state: dL/d(u, v, a, b, c, alpha_eff, R, G, B) per splat, valid
+        between backward_2d() and project_backward() (which reuses the section)."""
+        info = self.layout()
+        g = self.state[info.grad2d: info.grad2d + 48 * self.nv * self.n].view(torch.float32)
+        return g.view(self.nv, self.n, 12)[:, :, :9]
 
     # ---------------------------------------------------------------- views of the packed outputs
     def split(self, packed: torch.Tensor, channels: int = 3) -> list:

@@ -57,6 +57,9 @@ def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.05):
     assert excess.max() <= 0.0, f"image beyond tolerance + ambiguity bound by {excess.max():.3e}"
     excessT = np.abs(Tg - ref["T"]) - (tol + 1.001 * ref["amb_T"])
     assert excessT.max() <= 0.0, f"T beyond tolerance + ambiguity bound by {excessT.max():.3e}"
+    e = err.max(axis=0)
+    return dict(max_abs=float(e.max()), max_abs_unambiguous=float(e[~slack].max()) if (~slack).any() else 0.0,
+                ambiguous_frac=float(slack.mean()))
 
 
 # ---------------------------------------------------------------------------- forward
@@ -88,7 +91,8 @@ def test_forward_ragged_multiview(tile):
     _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
     for v, img, T in zip(views, imgs, Ts):
         ref = O.render(G, v)
-        assert_image_parity(img, T, ref)
+        st = assert_image_parity(img, T, ref)
+        print(f"[parity] fp32 tile {tile} {v['width']}x{v['height']}: {st}")
 
 
 def test_forward_bf16_coefficients_are_exact_inputs():
@@ -392,6 +396,7 @@ def assert_grad_parity(gg, go, tol=GRAD_TOL):
         nb = np.linalg.norm(b)
         assert nb > 0, k
         rel = np.linalg.norm(a - b) / nb
+        print(f"[parity] gradient {k}: relative error {rel:.3e}")
         assert rel <= tol, f"{k}: relative error {rel:.3e}"
 
 
@@ -414,6 +419,36 @@ def test_backward_matches_oracle(tile):
     gg = grads_gpu(fr, p, dL)
     go = O.backward_views(G, views, dL)
     assert_grad_parity(gg, go)
+
+
+@pytest.mark.parametrize("tile,mixed", [(16, False), (32, False), (32, True)])
+def test_backward_in_two_steps(tile, mixed):
+    """fgs4d_render_backward_2d + fgs4d_project_backward equal
+    fgs4d_render_backward, and the per-splat 2D gradients of the first step
+    match the oracle's adjoint of Eq. 6 alone."""
+    G, views = ragged_scene(n=1500, seed=27)
+    sd = torch.bfloat16 if mixed else torch.float32
+    fr, p, _, _ = gpu_forward(G, views, dict(tile_size=tile, record_fp16=int(mixed)), shs_dtype=sd)
+    Gr = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy()) if mixed else G
+    refs = [O.render(Gr, v) for v in views]
+    dL = masked_dL(views, refs, 8)
+    dLt = torch.cat([torch.as_tensor(d, dtype=torch.float32).reshape(-1) for d in dL]).cuda()
+    g1 = {k: v.clone() for k, v in fr.backward(p, dLt).items()}
+    fr.backward_2d(dLt)
+    g2d = fr.grad2d().double().cpu().numpy()  # before the second step, which reuses the section
+    g2 = fr.project_backward(p)
+    torch.cuda.synchronize()
+    for k in g1:
+        rel = float((g1[k] - g2[k]).norm() / g1[k].norm())
+        assert rel < 1e-5, (k, rel)
+    tol = 1e-2 if mixed else GRAD_TOL
+    for vi, v in enumerate(views):
+        want = O.backward(Gr, v, dL[vi])["grad2d"]
+        got = g2d[vi]
+        for c, name in enumerate(("u", "v", "a", "b", "c", "alpha_eff", "R", "G", "B")):
+            nb = np.linalg.norm(want[:, c])
+            rel = np.linalg.norm(got[:, c] - want[:, c]) / nb
+            assert nb > 0 and rel <= tol, (vi, name, rel)
 
 
 @TILES
@@ -524,16 +559,19 @@ def test_mixed_precision_against_fp64_oracle(tile):
     fr, p, imgs, Ts = gpu_forward(G, views, opts, shs_dtype=torch.bfloat16)
     G16 = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy())
     for img, T, v in zip(imgs, Ts, views):
-        assert_image_parity(img, T, O.render(G16, v), tol=1e-3)
+        st = assert_image_parity(img, T, O.render(G16, v), tol=1e-3)
+        print(f"[parity] mixed tile {tile} vs oracle(BF16 coefficients): {st}")
     refs = [O.render(G, v) for v in views]
     for img, T, ref in zip(imgs, Ts, refs):
-        assert_image_parity(img, T, ref, tol=3e-3)
+        st = assert_image_parity(img, T, ref, tol=3e-3)
+        print(f"[parity] mixed tile {tile} vs oracle(FP32 coefficients): {st}")
     refs16 = [O.render(G16, v) for v in views]
     dL = masked_dL(views, refs16, 9)
     gg = grads_gpu(fr, p, dL)
     go = O.backward_views(G16, views, dL)
     for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
         rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
+        print(f"[parity] mixed tile {tile} gradient {k}: relative error {rel:.3e}")
         assert rel <= MIXED_GRAD_TOL, (k, rel)
 
 
@@ -559,7 +597,8 @@ def test_full_size_workload_crops(mixed):
         sub = imgs[vi][:, y0:y0 + crop, x0:x0 + crop]
         subT = Ts[vi][y0:y0 + crop, x0:x0 + crop]
         # dense clustered scene: thousands of splats per pixel, so more decisions sit near thresholds
-        assert_image_parity(sub, subT, ref, tol=tol, max_flag_frac=0.25)
+        st = assert_image_parity(sub, subT, ref, tol=tol, max_flag_frac=0.25)
+        print(f"[parity] full-size {'mixed' if mixed else 'fp32'} view {vi} 64x64 crop: {st}")
         w = rng.normal(size=(3, crop, crop))
         w[:, ref["flags"] != 0] = 0.0
         dL[vi][:, y0:y0 + crop, x0:x0 + crop] = w
@@ -579,4 +618,5 @@ def test_full_size_workload_crops(mixed):
     gtol = MIXED_GRAD_TOL if mixed else GRAD_TOL
     for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
         rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
+        print(f"[parity] full-size {'mixed' if mixed else 'fp32'} gradient {k}: relative error {rel:.3e}")
         assert rel <= gtol, (k, rel)
