@@ -279,6 +279,52 @@ fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians *g, const fgs4d
 /* Copies the state's counters to *out (synchronises `stream`). */
 fgs4d_status fgs4d_read_counters(const void *state, fgs4d_counters *out, fgs4d_stream stream);
 
+/* ---------------------------------------------------------------- training step
+   The steps around the rendering routine in the paper's end-to-end training
+   (Sec. 3.3), with the photometric loss it adopts from 3D Gaussian splatting
+   (Sec. 4.1 setup). */
+
+/* Bytes of device scratch fgs4d_loss_l1_dssim needs for these views (0 on bad
+   views).  Host only. */
+size_t fgs4d_loss_scratch_size(const fgs4d_view *views, int n_views);
+
+/* L = (1 - lambda) mean|x - y| + lambda (1 - mean SSIM(x, y)) over all pixels
+   and channels of the batch, and dL/dx.  x = image, y = target: device, float32,
+   the layout of fgs4d_render's image.  SSIM per channel with an 11x11 Gaussian
+   window (sigma 1.5, sum 1, zero padding), C1 = 0.01^2, C2 = 0.03^2.  Writes
+   *loss (device, one float) and dL_dimage (device, the image's layout; may not
+   alias image or target).  scratch: device, 256-byte aligned, at least
+   fgs4d_loss_scratch_size() bytes; contents undefined afterwards.
+   lambda in [0, 1] (0.2 in the paper's setting).  Argument errors on the host;
+   FGS4D_ERR_CAPACITY if scratch is too small. */
+fgs4d_status fgs4d_loss_l1_dssim(const fgs4d_view *views, int n_views, const float *image, const float *target,
+                                 float lambda, float *loss, float *dL_dimage, void *scratch, size_t scratch_bytes,
+                                 fgs4d_stream stream);
+
+/* One parameter group of fgs4d_adam_step: count float32 elements each of the
+   parameter, its first and second moment estimates (updated in place) and its
+   gradient; all device.  param_bf16 (optional, device): receives the updated
+   parameter rounded to bfloat16 (the mixed-precision renderer's copy of the
+   4DSH coefficients).  lr_index: which entry of lrs applies. */
+typedef struct {
+    float *param;
+    float *exp_avg;
+    float *exp_avg_sq;
+    const float *grad;
+    void *param_bf16;
+    int64_t count;
+    int lr_index;
+} fgs4d_adam_group;
+
+/* Adam (Kingma and Ba, with bias correction) over up to 8 groups in two
+   launches: *step (device int64) is incremented first and t = the new value
+   is used, so a captured graph advances it on every replay; lrs (device
+   floats) are read at run time for the same reason.  bias_scratch: device,
+   two floats.  p <- p - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps).
+   The paper has no optimiser of its own (it trains with Adam). */
+fgs4d_status fgs4d_adam_step(const fgs4d_adam_group *groups, int n_groups, const float *lrs, float beta1,
+                             float beta2, float eps, int64_t *step, float *bias_scratch, fgs4d_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -361,7 +361,8 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     const int B = O.batch;  // records per batch, <= kTilePix
     for (int end = max_last; end > 0; end -= B) {
         const int cnt = min(end, B);
-        __syncthreads();
+        // No barrier before staging: thread tid stages slot tid, and the
+        // flush of the previous batch touched only slot tid too (same thread).
         if (tid < cnt) {
             const uint32_t idx = range.x + (uint32_t)(end - 1 - tid);
             uint32_t sid = pair_vals[idx];

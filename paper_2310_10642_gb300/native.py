@@ -20,7 +20,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libfgs4d.so")
-SOURCES = ["api.cu", "slice_project.cu", "bin_sort.cu", "render.cu"]
+SOURCES = ["api.cu", "slice_project.cu", "bin_sort.cu", "render.cu", "train.cu"]
 HEADERS = ["fgs4d_internal.cuh"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -111,6 +111,12 @@ class Counters(ctypes.Structure):
                 ("pair_capacity", ctypes.c_uint32)]
 
 
+class AdamGroup(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_void_p), ("exp_avg", ctypes.c_void_p), ("exp_avg_sq", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("param_bf16", ctypes.c_void_p), ("count", ctypes.c_int64),
+                ("lr_index", ctypes.c_int)]
+
+
 class StateLayoutInfo(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in ("counters", "records", "tiles_touched", "ranges", "pair_vals",
                                                 "record_bytes", "n_splats", "total_tiles", "pair_capacity",
@@ -120,7 +126,8 @@ class StateLayoutInfo(ctypes.Structure):
 EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fgs4d_default_options", "fgs4d_state_size",
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
            "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats",
-           "fgs4d_render_backward_2d", "fgs4d_project_backward"]
+           "fgs4d_render_backward_2d", "fgs4d_project_backward",
+           "fgs4d_loss_scratch_size", "fgs4d_loss_l1_dssim", "fgs4d_adam_step"]
 NOALLOC_MAX_SPLATS = 262144
 
 
@@ -168,6 +175,14 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                                                  ctypes.POINTER(Options), vp, ctypes.c_size_t,
                                                  ctypes.POINTER(GaussianGrads), vp]
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
+            L.fgs4d_loss_scratch_size.argtypes = [ctypes.POINTER(View), ci]
+            L.fgs4d_loss_scratch_size.restype = ctypes.c_size_t
+            L.fgs4d_loss_l1_dssim.argtypes = [ctypes.POINTER(View), ci, vp, vp, ctypes.c_float, vp, vp, vp,
+                                              ctypes.c_size_t, vp]
+            L.fgs4d_loss_l1_dssim.restype = ci
+            L.fgs4d_adam_step.argtypes = [ctypes.POINTER(AdamGroup), ci, vp, ctypes.c_float, ctypes.c_float,
+                                          ctypes.c_float, vp, vp, vp]
+            L.fgs4d_adam_step.restype = ci
             L.fgs4d_render_backward_noalloc.argtypes = L.fgs4d_render_backward.argtypes
             L.fgs4d_render_backward_noalloc.restype = ci
             L.fgs4d_state_layout.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), ctypes.c_size_t,
@@ -254,6 +269,23 @@ def fgs4d_project_backward(g: Gaussians, views, n_views: int, opts: Options, sta
     _check("fgs4d_project_backward", lib().fgs4d_project_backward(ctypes.byref(g), views, int(n_views),
                                                                    ctypes.byref(opts), state, state_bytes,
                                                                    ctypes.byref(grads), stream))
+
+
+def fgs4d_loss_scratch_size(views, n_views: int) -> int:
+    return int(lib().fgs4d_loss_scratch_size(views, int(n_views)))
+
+
+def fgs4d_loss_l1_dssim(views, n_views: int, image: int, target: int, lam: float, loss: int, dL_dimage: int,
+                        scratch: int, scratch_bytes: int, stream: int):
+    _check("fgs4d_loss_l1_dssim", lib().fgs4d_loss_l1_dssim(views, int(n_views), image, target, float(lam), loss,
+                                                             dL_dimage, scratch, scratch_bytes, stream))
+
+
+def fgs4d_adam_step(groups: list, lrs: int, beta1: float, beta2: float, eps: float, step: int, bias: int,
+                    stream: int):
+    arr = (AdamGroup * len(groups))(*groups)
+    _check("fgs4d_adam_step", lib().fgs4d_adam_step(arr, len(groups), lrs, float(beta1), float(beta2), float(eps),
+                                                     step, bias, stream))
 
 
 def fgs4d_render_stats(n: int, views, n_views: int, opts: Options, state: int, state_bytes: int, image: int,
