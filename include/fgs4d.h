@@ -67,6 +67,16 @@ typedef enum {
 
 typedef enum { FGS4D_F32 = 0, FGS4D_BF16 = 1 } fgs4d_dtype;
 
+/* How the 4D rotation R of Sigma = R S S^T R^T is formed.
+   FGS4D_ROT_4D: R = L(q_left) R(q_right), Eq. 8 (the method).
+   FGS4D_ROT_SPATIAL: the "No-4DRot" variant of the ablation (Sec. 4.3): only
+   x, y, z rotate, R = blockdiag(R3(q_left), 1) with R3 the usual rotation
+   of a unit quaternion (w, x, y, z); Sigma is block-diagonal, so the slice
+   at t leaves the mean and the spatial covariance unchanged (no motion) and
+   p(t) depends on s_t alone.  q_right is not read (may be NULL) and its
+   gradient is zero. */
+typedef enum { FGS4D_ROT_4D = 0, FGS4D_ROT_SPATIAL = 1 } fgs4d_rotation;
+
 /* Device status bits written into the state (see fgs4d_counters.status). */
 #define FGS4D_STATUS_PAIR_OVERFLOW 1u  /* more (splat, tile) pairs than capacity */
 #define FGS4D_STATUS_NONFINITE 2u      /* a Gaussian had non-finite values or |q| ~ 0 */
@@ -95,6 +105,7 @@ typedef struct {
     int n_freq;      /* K, 0..FGS4D_MAX_FREQ */
     float period;    /* T of Eq. 11, > 0 */
     int shs_dtype;   /* fgs4d_dtype */
+    int rotation;    /* fgs4d_rotation */
 } fgs4d_gaussians;
 
 /* One camera at one time t (host memory). */
@@ -134,6 +145,8 @@ typedef struct {
     float *opacity_logit;
     float *shs;
     float *mean2d_abs; /* optional [n]: sum over views of |dL/d mu_2d| (densification signal); may be NULL */
+    float *mu_t_abs;   /* optional [n]: sum over views of |dL/d mu_t| of each view (the temporal
+                          densification signal, Sec. 3.4); may be NULL */
 } fgs4d_gaussian_grads;
 
 /* Counters read back by fgs4d_read_counters. */
@@ -204,6 +217,16 @@ fgs4d_status fgs4d_render_backward_2d(int64_t n, const fgs4d_view *views, int n_
 fgs4d_status fgs4d_project_backward(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
                                     const fgs4d_options *opt, void *state, size_t state_bytes,
                                     fgs4d_gaussian_grads *grads, fgs4d_stream stream);
+
+/* Split sampling in 4D (Sec. 3.4, densification): for j < m, new 4D means
+   out_mu[i*m + j] = mu + R diag(s) z_j of Gaussian index[j], i = x, y, z, t,
+   so that the samples follow the Gaussian's own 4D density N(mu, Sigma),
+   Sigma = R S S^T R^T (Eq. 7-8).  index: device int64 [m]; z: device float
+   [4][m], standard normal draws supplied by the caller; out_mu: device float
+   [4][m].  An out-of-range index or a Gaussian with non-finite parameters
+   yields NaN for that sample. */
+fgs4d_status fgs4d_sample_split(const fgs4d_gaussians *g, const int64_t *index, const float *z, int64_t m,
+                                float *out_mu, fgs4d_stream stream);
 
 /* fgs4d_render plus a count of the work its walk did; the paper has no
    counterpart (it measures Eq. 6's cost for throughput accounting).  Writes

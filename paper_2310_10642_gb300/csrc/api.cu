@@ -166,10 +166,12 @@ fgs4d_status check_gaussians(const fgs4d_gaussians* g, DevGauss* d) {
         return FGS4D_ERR_INVALID_ARG;
     if (!(g->period > 0.0f) || !isfinite(g->period)) return FGS4D_ERR_INVALID_ARG;
     if (g->shs_dtype != FGS4D_F32 && g->shs_dtype != FGS4D_BF16) return FGS4D_ERR_INVALID_ARG;
+    if (g->rotation != FGS4D_ROT_4D && g->rotation != FGS4D_ROT_SPATIAL) return FGS4D_ERR_INVALID_ARG;
     if (g->n > 0) {
-        const void* ptrs[] = {g->mu, g->log_scale, g->q_left, g->q_right, g->opacity_logit, g->shs};
+        const void* ptrs[] = {g->mu, g->log_scale, g->q_left, g->opacity_logit, g->shs};
         for (const void* p : ptrs)
             if (!p || !aligned(p, 16)) return FGS4D_ERR_INVALID_ARG;
+        if (g->rotation == FGS4D_ROT_4D && (!g->q_right || !aligned(g->q_right, 16))) return FGS4D_ERR_INVALID_ARG;
     }
     d->mu = g->mu;
     d->log_s = g->log_scale;
@@ -182,6 +184,7 @@ fgs4d_status check_gaussians(const fgs4d_gaussians* g, DevGauss* d) {
     d->K = g->n_freq;
     d->inv_period = 1.0f / g->period;
     d->shs_bf16 = g->shs_dtype == FGS4D_BF16;
+    d->rot3 = g->rotation == FGS4D_ROT_SPATIAL;
     return FGS4D_OK;
 }
 
@@ -321,6 +324,16 @@ fgs4d_status fgs4d_render(int64_t n, const fgs4d_view* views, int n_views, const
                                       n_last, (cudaStream_t)stream));
     delete P;
     return s;
+}
+
+fgs4d_status fgs4d_sample_split(const fgs4d_gaussians* g, const int64_t* index, const float* z, int64_t m,
+                                float* out_mu, fgs4d_stream stream) {
+    DevGauss G;
+    fgs4d_status s = check_gaussians(g, &G);
+    if (s != FGS4D_OK) return s;
+    if (m < 0 || (m > 0 && (!index || !z || !out_mu))) return FGS4D_ERR_INVALID_ARG;
+    if (!aligned(index, 8) || !aligned(z, 4) || !aligned(out_mu, 4)) return FGS4D_ERR_INVALID_ARG;
+    return cuda_status(launch_sample_split(G, index, z, m, out_mu, (cudaStream_t)stream));
 }
 
 fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt,

@@ -61,6 +61,7 @@ struct DevGauss {
     int K;
     float inv_period;
     int shs_bf16;
+    int rot3;  // No-4DRot variant: q_left rotates x, y, z only; q_right is not read
 };
 
 // ---------------------------------------------------------------------------
@@ -311,6 +312,18 @@ __device__ __forceinline__ void right_matrix(const float* q, float* R) {
     R[12] = s;  R[13] = r;  R[14] = -qq; R[15] = p;
 }
 
+// blockdiag(R3(q), 1): the rotation of x, y, z by the unit quaternion
+// q = (w, x, y, z) in the usual convention, t fixed (the No-4DRot variant).
+template <class T>
+__device__ __forceinline__ void spatial_rotation(const T* q, T* R) {
+    const T w = q[0], x = q[1], y = q[2], z = q[3];
+    const T one = T(1), two = T(2);
+    R[0] = one - two * (y * y + z * z); R[1] = two * (x * y - w * z);       R[2] = two * (x * z + w * y);       R[3] = T(0);
+    R[4] = two * (x * y + w * z);       R[5] = one - two * (x * x + z * z); R[6] = two * (y * z - w * x);       R[7] = T(0);
+    R[8] = two * (x * z - w * y);       R[9] = two * (y * z + w * x);       R[10] = one - two * (x * x + y * y); R[11] = T(0);
+    R[12] = T(0);                       R[13] = T(0);                       R[14] = T(0);                       R[15] = one;
+}
+
 __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
     const size_t n = (size_t)G.n;
     float ls[4], ql[4], qr[4];
@@ -319,7 +332,7 @@ __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
         c.mu[i] = __ldg(G.mu + i * n + g);
         ls[i] = __ldg(G.log_s + i * n + g);
         ql[i] = __ldg(G.ql + i * n + g);
-        qr[i] = __ldg(G.qr + i * n + g);
+        qr[i] = G.rot3 ? (i == 0 ? 1.0f : 0.0f) : __ldg(G.qr + i * n + g);
     }
     const float logit = __ldg(G.logit + g);
     c.alpha = 1.0f / (1.0f + expf(-logit));
@@ -336,19 +349,27 @@ __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
         c.qrn[i] = qr[i] / c.nr;
     }
     c.ok = finite && nl2 > 1e-24f && nr2 > 1e-24f;
-    float Lm[16], Rm[16];
-    left_matrix(c.qln, Lm);
-    right_matrix(c.qrn, Rm);
+    if (G.rot3) {
+        spatial_rotation(c.qln, c.R);
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+        for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            float acc = 0.0f;
+            for (int j = 0; j < 4; j++) c.M[i * 4 + j] = c.R[i * 4 + j] * c.s[j];
+    } else {
+        float Lm[16], Rm[16];
+        left_matrix(c.qln, Lm);
+        right_matrix(c.qrn, Rm);
 #pragma unroll
-            for (int k = 0; k < 4; k++) acc = fmaf(Lm[i * 4 + k], Rm[k * 4 + j], acc);
-            c.R[i * 4 + j] = acc;
-            c.M[i * 4 + j] = acc * c.s[j];
-        }
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc = fmaf(Lm[i * 4 + k], Rm[k * 4 + j], acc);
+                c.R[i * 4 + j] = acc;
+                c.M[i * 4 + j] = acc * c.s[j];
+            }
+    }
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
@@ -367,7 +388,7 @@ static __device__ __noinline__ void core_sigma_f64(const DevGauss& G, int g, dou
     double ql[4], qr[4], s[4], nl = 0.0, nr = 0.0;
     for (int i = 0; i < 4; i++) {
         ql[i] = (double)G.ql[i * n + g];
-        qr[i] = (double)G.qr[i * n + g];
+        qr[i] = G.rot3 ? (i == 0 ? 1.0 : 0.0) : (double)G.qr[i * n + g];
         s[i] = exp((double)G.log_s[i * n + g]);
         nl += ql[i] * ql[i];
         nr += qr[i] * qr[i];
@@ -378,17 +399,23 @@ static __device__ __noinline__ void core_sigma_f64(const DevGauss& G, int g, dou
         ql[i] /= nl;
         qr[i] /= nr;
     }
-    const double a = ql[0], b = ql[1], c = ql[2], d = ql[3];
-    const double Lm[16] = {a, -b, -c, -d, b, a, -d, c, c, d, a, -b, d, -c, b, a};
-    const double p = qr[0], q = qr[1], r = qr[2], t = qr[3];
-    const double Rm[16] = {p, -q, -r, -t, q, p, t, -r, r, -t, p, q, t, r, -q, p};
     double M[16];
-    for (int i = 0; i < 4; i++)
-        for (int j = 0; j < 4; j++) {
-            double acc = 0.0;
-            for (int k = 0; k < 4; k++) acc += Lm[i * 4 + k] * Rm[k * 4 + j];
-            M[i * 4 + j] = acc * s[j];
-        }
+    if (G.rot3) {
+        spatial_rotation(ql, M);
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) M[i * 4 + j] *= s[j];
+    } else {
+        const double a = ql[0], b = ql[1], c = ql[2], d = ql[3];
+        const double Lm[16] = {a, -b, -c, -d, b, a, -d, c, c, d, a, -b, d, -c, b, a};
+        const double p = qr[0], q = qr[1], r = qr[2], t = qr[3];
+        const double Rm[16] = {p, -q, -r, -t, q, p, t, -r, r, -t, p, q, t, r, -q, p};
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 4; j++) {
+                double acc = 0.0;
+                for (int k = 0; k < 4; k++) acc += Lm[i * 4 + k] * Rm[k * 4 + j];
+                M[i * 4 + j] = acc * s[j];
+            }
+    }
     for (int i = 0; i < 4; i++)
         for (int j = 0; j < 4; j++) {
             double acc = 0.0;
@@ -573,6 +600,8 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
                             cudaStream_t st, int* out_buf);
 cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
                           float* image, float* final_T, int32_t* n_last, cudaStream_t st);
+cudaError_t launch_sample_split(const DevGauss& G, const int64_t* index, const float* z, int64_t m, float* out,
+                                cudaStream_t st);
 cudaError_t launch_render_stats(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                 int pair_buf, float* image, float* final_T, int32_t* n_last,
                                 unsigned long long* stats, cudaStream_t st);

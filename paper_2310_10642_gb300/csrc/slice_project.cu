@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         float GS[16];
 #pragma unroll
         for (int i = 0; i < 16; i++) GS[i] = 0.0f;
-        float galpha = 0.0f, m2d = 0.0f;
+        float galpha = 0.0f, m2d = 0.0f, mt = 0.0f;
         Core c;
         c.ok = false;
         if (active) load_core(G, g, c);
@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 const float dt = w.dt;
                 const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
                 ddt += mb * isig - dp * w.p * dt * isig;
+                mt = fabsf(ddt);  // this view's |dL/dmu_t|
     #pragma unroll
                 for (int i = 0; i < 3; i++) {
                     const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         GS[15] = segment_sum(GS[15], lane, seg_last);
         galpha = segment_sum(galpha, lane, seg_last);
         m2d = segment_sum(m2d, lane, seg_last);
+        mt = segment_sum(mt, lane, seg_last);
         if (!(active && c.ok && lane == seg_first)) continue;
 
         // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
@@ -348,6 +350,24 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 }
     #pragma unroll
             for (int k = 0; k < 4; k++) gls[k] *= c.s[k];
+            if (G.rot3) {
+                // R = blockdiag(R3(q), 1): dL/dq through the 3x3 block, then the normalisation
+                const float w = c.qln[0], x = c.qln[1], y = c.qln[2], z = c.qln[3];
+                const float* d = dR;
+                const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[4] - x * d[6] - y * d[8] + x * d[9]);
+                const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[4] - 2.0f * x * d[5] - w * d[6] + z * d[8] +
+                                         w * d[9] - 2.0f * x * d[10]);
+                const float gy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[4] + z * d[6] - w * d[8] +
+                                         z * d[9] - 2.0f * y * d[10]);
+                const float gz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[4] - 2.0f * z * d[5] +
+                                         y * d[6] + x * d[8] + y * d[9]);
+                const float gq[4] = {gw, gx, gy, gz};
+                float dq = 0.0f;
+#pragma unroll
+                for (int i = 0; i < 4; i++) dq = fmaf(gq[i], c.qln[i], dq);
+#pragma unroll
+                for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * c.qln[i]) / c.nl;
+            } else {
             float Lm[16], Rm[16];
             left_matrix(c.qln, Lm);
             right_matrix(c.qrn, Rm);
@@ -380,6 +400,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 gql[i] = (gl[i] - dl * c.qln[i]) / c.nl;
                 gqr[i] = (gr[i] - dr * c.qrn[i]) / c.nr;
             }
+            }
             glogit = galpha * c.alpha * (1.0f - c.alpha);
         } else {
     #pragma unroll
@@ -391,10 +412,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
             atomicAdd(&out.mu[i * n + g], gmu[i]);
             atomicAdd(&out.log_scale[i * n + g], gls[i]);
             atomicAdd(&out.q_left[i * n + g], gql[i]);
-            atomicAdd(&out.q_right[i * n + g], gqr[i]);
+            if (!G.rot3) atomicAdd(&out.q_right[i * n + g], gqr[i]);
         }
         atomicAdd(&out.opacity_logit[g], glogit);
         if (out.mean2d_abs) atomicAdd(&out.mean2d_abs[g], m2d);
+        if (out.mu_t_abs) atomicAdd(&out.mu_t_abs[g], mt);
     }
 }
 
@@ -516,6 +538,7 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
     const size_t rows[5] = {4, 4, 4, 4, 1};
     for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaMemsetAsync(outs[i], 0, rows[i] * n * sizeof(float), st);
     if (e == cudaSuccess && grads.mean2d_abs) e = cudaMemsetAsync(grads.mean2d_abs, 0, n * sizeof(float), st);
+    if (e == cudaSuccess && grads.mu_t_abs) e = cudaMemsetAsync(grads.mu_t_abs, 0, n * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const int sms = local_sm_count();
     e = compact_visible_gaussian_major(tt, (uint32_t)n, (uint32_t)VS.n, list, list_count, scan_tmp, sms, st);
@@ -562,6 +585,44 @@ cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, c
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
     return launch_pb_any(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+}
+
+// Split sampling in 4D (Sec. 3.4): new means drawn from a Gaussian's own 4D
+// density, x = mu + M z with M = R diag(s) (so that M M^T = Sigma, Eq. 7-8)
+// and z ~ N(0, I) supplied by the caller.  One thread per sample; index[j]
+// names the Gaussian, z and out are [4][m].  A Gaussian with non-finite or
+// zero-norm parameters yields NaN.
+__global__ void __launch_bounds__(256) sample_split_kernel(const DevGauss G, const int64_t* __restrict__ index,
+                                                           const float* __restrict__ z, int64_t m,
+                                                           float* __restrict__ out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t gi = index[j];
+    if (gi < 0 || gi >= G.n) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) out[i * m + j] = __int_as_float(0x7fc00000);
+        return;
+    }
+    Core c;
+    load_core(G, (int)gi, c);
+    float zz[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) zz[k] = z[k * m + j];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float x = c.mu[i];
+#pragma unroll
+        for (int k = 0; k < 4; k++) x = fmaf(c.M[i * 4 + k], zz[k], x);
+        out[i * m + j] = c.ok ? x : __int_as_float(0x7fc00000);
+    }
+}
+
+cudaError_t launch_sample_split(const DevGauss& G, const int64_t* index, const float* z, int64_t m, float* out,
+                                cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    sample_split_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(G, index, z, m, out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace fgs4d

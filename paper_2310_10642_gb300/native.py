@@ -29,6 +29,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 MAX_VIEWS = 128
 TILE = 16
 F32, BF16 = 0, 1
+ROT_4D, ROT_SPATIAL = 0, 1
 STATUS_PAIR_OVERFLOW = 1
 STATUS_NONFINITE = 2
 
@@ -84,7 +85,7 @@ class Gaussians(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_void_p), ("log_scale", ctypes.c_void_p), ("q_left", ctypes.c_void_p),
                 ("q_right", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p), ("shs", ctypes.c_void_p),
                 ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int), ("n_freq", ctypes.c_int),
-                ("period", ctypes.c_float), ("shs_dtype", ctypes.c_int)]
+                ("period", ctypes.c_float), ("shs_dtype", ctypes.c_int), ("rotation", ctypes.c_int)]
 
 
 class View(ctypes.Structure):
@@ -103,7 +104,7 @@ class Options(ctypes.Structure):
 class GaussianGrads(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_void_p), ("log_scale", ctypes.c_void_p), ("q_left", ctypes.c_void_p),
                 ("q_right", ctypes.c_void_p), ("opacity_logit", ctypes.c_void_p), ("shs", ctypes.c_void_p),
-                ("mean2d_abs", ctypes.c_void_p)]
+                ("mean2d_abs", ctypes.c_void_p), ("mu_t_abs", ctypes.c_void_p)]
 
 
 class Counters(ctypes.Structure):
@@ -127,7 +128,7 @@ EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fg
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
            "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats",
            "fgs4d_render_backward_2d", "fgs4d_project_backward",
-           "fgs4d_loss_scratch_size", "fgs4d_loss_l1_dssim", "fgs4d_adam_step"]
+           "fgs4d_loss_scratch_size", "fgs4d_loss_l1_dssim", "fgs4d_adam_step", "fgs4d_sample_split"]
 NOALLOC_MAX_SPLATS = 262144
 
 
@@ -175,6 +176,8 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                                                  ctypes.POINTER(Options), vp, ctypes.c_size_t,
                                                  ctypes.POINTER(GaussianGrads), vp]
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
+            L.fgs4d_sample_split.argtypes = [ctypes.POINTER(Gaussians), vp, vp, i64, vp, vp]
+            L.fgs4d_sample_split.restype = ci
             L.fgs4d_loss_scratch_size.argtypes = [ctypes.POINTER(View), ci]
             L.fgs4d_loss_scratch_size.restype = ctypes.c_size_t
             L.fgs4d_loss_l1_dssim.argtypes = [ctypes.POINTER(View), ci, vp, vp, ctypes.c_float, vp, vp, vp,
@@ -269,6 +272,10 @@ def fgs4d_project_backward(g: Gaussians, views, n_views: int, opts: Options, sta
     _check("fgs4d_project_backward", lib().fgs4d_project_backward(ctypes.byref(g), views, int(n_views),
                                                                    ctypes.byref(opts), state, state_bytes,
                                                                    ctypes.byref(grads), stream))
+
+
+def fgs4d_sample_split(g: Gaussians, index: int, z: int, m: int, out_mu: int, stream: int):
+    _check("fgs4d_sample_split", lib().fgs4d_sample_split(ctypes.byref(g), index, z, int(m), out_mu, stream))
 
 
 def fgs4d_loss_scratch_size(views, n_views: int) -> int:

@@ -30,6 +30,8 @@ def params_to_device(params: dict, device="cuda", shs_dtype=torch.float32) -> di
         out[k] = t.to(device=device, dtype=dt).contiguous()
     for k in ("sh_degree", "n_freq", "period"):
         out[k] = params[k]
+    if "rotation" in params:
+        out["rotation"] = int(params["rotation"])
     return out
 
 
@@ -51,7 +53,8 @@ def gaussians_struct(p: dict) -> N.Gaussians:
             raise ValueError(f"{k} must be a contiguous CUDA tensor")
     n = p["logit"].shape[0]
     return N.Gaussians(_ptr(p["mu"]), _ptr(p["log_s"]), _ptr(p["ql"]), _ptr(p["qr"]), _ptr(p["logit"]),
-                       _ptr(p["shs"]), n, int(p["sh_degree"]), int(p["n_freq"]), float(p.get("period", 1.0)), dtype)
+                       _ptr(p["shs"]), n, int(p["sh_degree"]), int(p["n_freq"]), float(p.get("period", 1.0)), dtype,
+                       int(p.get("rotation", N.ROT_4D)))
 
 
 def _stream(stream=None) -> int:
@@ -145,12 +148,17 @@ class Frame:
         raise RuntimeError("pair capacity could not be sized")
 
     def _grads(self, params: dict, grads: dict | None, mean2d: bool):
+        """mean2d: also the densification signals mean2d_abs (sum over views of
+        |dL/dmu_2d|) and mu_t_abs (sum over views of |dL/dmu_t|)."""
         if grads is None:
             grads = {k: torch.empty(params[k].shape, device=self.device, dtype=torch.float32) for k in PARAM_KEYS}
-        if mean2d and "mean2d_abs" not in grads:
-            grads["mean2d_abs"] = torch.empty(self.n, device=self.device, dtype=torch.float32)
+        if mean2d:
+            for k in ("mean2d_abs", "mu_t_abs"):
+                if k not in grads:
+                    grads[k] = torch.empty(self.n, device=self.device, dtype=torch.float32)
         gs = N.GaussianGrads(_ptr(grads["mu"]), _ptr(grads["log_s"]), _ptr(grads["ql"]), _ptr(grads["qr"]),
-                             _ptr(grads["logit"]), _ptr(grads["shs"]), _ptr(grads.get("mean2d_abs")))
+                             _ptr(grads["logit"]), _ptr(grads["shs"]), _ptr(grads.get("mean2d_abs")),
+                             _ptr(grads.get("mu_t_abs")))
         return grads, gs
 
     def _dL(self, dL_dimage: torch.Tensor) -> torch.Tensor:

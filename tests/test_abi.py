@@ -99,6 +99,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.fgs4d_slice_project(ctypes.byref(g2), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     g3 = N.Gaussians(16, 32, 48, 64, 80, 96, 10, 1, 1, 0.0, 0)  # period 0
     assert lib.fgs4d_slice_project(ctypes.byref(g3), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    g5 = N.Gaussians(16, 32, 48, 64, 80, 96, 10, 1, 1, 1.0, 0, 7)  # unknown rotation mode
+    assert lib.fgs4d_slice_project(ctypes.byref(g5), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    g6 = N.Gaussians(16, 32, 48, None, 80, 96, 10, 1, 1, 1.0, 0, N.ROT_4D)  # 4D rotation needs q_right
+    assert lib.fgs4d_slice_project(ctypes.byref(g6), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     g4 = N.Gaussians(16, 32, 48, 64, 80, 97, 10, 1, 1, 1.0, 0)  # misaligned shs
     assert lib.fgs4d_slice_project(ctypes.byref(g4), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     # state smaller than the fixed part
