@@ -133,6 +133,10 @@ typedef struct {
                          32 bins each splat to ~3x fewer tiles, each thread composites 2x2 pixels */
     int batch_depth;  /* 256: splat records a tile stages in shared memory per batch while
                          compositing (32, 64, 128 or 256); results do not depend on it */
+    int aux_channels; /* 0; 1: fgs4d_slice_project also stores, per splat, its camera depth and
+                         the displacement of its projected mean from t to t + flow_dt, for
+                         fgs4d_render_aux (the state grows by 16 bytes per splat) */
+    float flow_dt;    /* 1/300: time step of the optical-flow channels (one frame of 300) */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but
@@ -227,6 +231,22 @@ fgs4d_status fgs4d_project_backward(const fgs4d_gaussians *g, const fgs4d_view *
    yields NaN for that sample. */
 fgs4d_status fgs4d_sample_split(const fgs4d_gaussians *g, const int64_t *index, const float *z, int64_t m,
                                 float *out_mu, fgs4d_stream stream);
+
+/* Depth and optical-flow maps composited like the colour (Eq. 6 with the
+   colour replaced by a per-splat value, background 0), over the lists of the
+   last fgs4d_bin_sort: aux_image (device float32, the image's layout, three
+   planes per view) receives
+     plane 0: sum_i alpha_i T_i z_i, z_i the camera depth of mu_{xyz|t};
+              divided by 1 - final_T it is the expected depth;
+     planes 1, 2: sum_i alpha_i T_i (u_i(t + flow_dt) - u_i(t)) and likewise
+              for v: the flow of the projected conditional means (Eq. 9
+              moves mu_{xyz|t} linearly in t), the motion the paper renders
+              as optical flow.
+   The state must come from fgs4d_slice_project with aux_channels = 1
+   (FGS4D_ERR_INVALID_ARG otherwise).  A second walk over the lists: it costs
+   about as much as fgs4d_render. */
+fgs4d_status fgs4d_render_aux(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
+                              size_t state_bytes, float *aux_image, fgs4d_stream stream);
 
 /* fgs4d_render plus a count of the work its walk did; the paper has no
    counterpart (it measures Eq. 6's cost for throughput accounting).  Writes

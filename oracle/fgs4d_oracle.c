@@ -578,6 +578,29 @@ ORC_API int64_t orc_render(const orc_gaussians *G, const orc_view *V, const orc_
     return nvis;
 }
 
+/* Eq. 6 with each splat's colour replaced by values[3 g + ch] and a zero
+   background: the same walk, decisions and weights alpha_i T_i as the image,
+   applied to other per-splat quantities (depth, flow).  out is [3][h][w]. */
+ORC_API void orc_render_values(const orc_gaussians *G, const orc_view *V, const orc_options *O, int x0, int y0, int w,
+                               int h, int prefilter, const double *values, double *out) {
+    orc_splat *S = (orc_splat *)malloc(sizeof(orc_splat) * (G->n > 0 ? G->n : 1));
+    int64_t *order;
+    int64_t m = sorted_candidates(G, V, O, S, &order);
+    for (int64_t g = 0; g < G->n; g++)
+        for (int ch = 0; ch < 3; ch++) S[g].color[ch] = values[3 * g + ch];
+    orc_view Vz = *V;
+    for (int ch = 0; ch < 3; ch++) Vz.bg[ch] = 0.0;
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            double C[3], T;
+            pixel_walk(S, order, m, O, &Vz, (double)(x0 + x), (double)(y0 + y), prefilter, C, &T, NULL, NULL, NULL,
+                       NULL, 0.0);
+            for (int ch = 0; ch < 3; ch++) out[((int64_t)ch * h + y) * w + x] = C[ch];
+        }
+    free(order);
+    free(S);
+}
+
 /* ------------------------------------------------------------------ */
 /* O9: hand-derived reverse mode                                        */
 /* ------------------------------------------------------------------ */

@@ -92,6 +92,9 @@ def lib():
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_render.restype = ctypes.c_int64
+            L.orc_render_values.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_View),
+                                            ctypes.POINTER(_Options), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_project_backward.argtypes = [ctypes.POINTER(_Gaussians), ctypes.c_int64, ctypes.POINTER(_View),
                                                ctypes.POINTER(_Options), dp, ctypes.POINTER(_Grads)]
             L.orc_backward.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_View), ctypes.POINTER(_Options),
@@ -242,6 +245,40 @@ def render(params: dict, view: dict, opts: dict | None = None, window=None, pref
                             fl.ctypes.data, None, sh.ctypes.data, amb.ctypes.data)
     return dict(image=img, T=T, n_contrib=nc, flags=fl, seq_hash=sh, amb_image=amb[0], amb_T=amb[1],
                 n_visible=int(nvis))
+
+
+def render_values(params: dict, view: dict, values: np.ndarray, opts: dict | None = None, window=None,
+                  prefilter: bool = False) -> np.ndarray:
+    """Eq. 6 compositing of per-Gaussian values [n, 3] (in place of the
+    colours, background 0) with the image's walk: [3, h, w]."""
+    P = _Packed(params)
+    x0, y0, w, h = _window(view, window)
+    vals = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(P.n, 3))
+    out = np.zeros((3, h, w))
+    lib().orc_render_values(ctypes.byref(P.struct), ctypes.byref(_view(view)), ctypes.byref(_options(opts)), x0, y0,
+                            w, h, int(bool(prefilter)), vals.ctypes.data, out.ctypes.data)
+    return out
+
+
+def aux_values(params: dict, view: dict, flow_dt: float, opts: dict | None = None) -> np.ndarray:
+    """Per-Gaussian [n, 3]: the camera depth of mu_{xyz|t}, and the
+    displacement (du, dv) of its projection from t to t + flow_dt, with the
+    conditional mean of Eq. 9 at t + flow_dt (0 where that mean is behind the
+    camera)."""
+    rec = project_all(params, view, opts)
+    n = len(rec["u"])
+    Vm = np.asarray(view["viewmat"], dtype=np.float64).reshape(3, 4)
+    W, tau = Vm[:, :3], Vm[:, 3]
+    out = np.zeros((n, 3))
+    for g in range(n):
+        out[g, 0] = rec["depth"][g]
+        Sigma = covariance4(params["log_s"][:, g], params["ql"][:, g], params["qr"][:, g])
+        mu3, _, _ = condition(params["mu"][:, g], Sigma, float(view["t"]) + flow_dt)
+        xc = W @ mu3 + tau
+        if xc[2] > 0:
+            out[g, 1] = view["fx"] * xc[0] / xc[2] + view["cx"] - rec["u"][g]
+            out[g, 2] = view["fy"] * xc[1] / xc[2] + view["cy"] - rec["v"][g]
+    return out
 
 
 def _new_grads(P: _Packed):

@@ -39,6 +39,8 @@ fgs4d_status check_options(const fgs4d_options* o) {
     if (o->tile_size != 16 && o->tile_size != 32) return FGS4D_ERR_INVALID_ARG;
     if (o->batch_depth != 32 && o->batch_depth != 64 && o->batch_depth != 128 && o->batch_depth != 256)
         return FGS4D_ERR_INVALID_ARG;
+    if (o->aux_channels != 0 && o->aux_channels != 1) return FGS4D_ERR_INVALID_ARG;
+    if (!isfinite(o->flow_dt)) return FGS4D_ERR_INVALID_ARG;
     return FGS4D_OK;
 }
 
@@ -56,6 +58,8 @@ DevOpts dev_options(const fgs4d_options* o) {
     d.record_fp16 = o->record_fp16;
     d.tile = o->tile_size;
     d.batch = o->batch_depth;
+    d.aux = o->aux_channels;
+    d.flow_dt = o->flow_dt;
     return d;
 }
 
@@ -112,8 +116,8 @@ fgs4d_status make_views(const fgs4d_view* views, int n_views, const fgs4d_option
 
 // Lays out the state for n Gaussians and the views; capacity < 0 means
 // "derive it from state_bytes".
-fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int64_t capacity, size_t state_bytes,
-                         StateLayout* L) {
+fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int aux, int64_t capacity,
+                         size_t state_bytes, StateLayout* L) {
     if (n < 0) return FGS4D_ERR_INVALID_ARG;
     const int64_t S = n * (int64_t)VS.n;
     if (S >= 0x7fffffffll) return FGS4D_ERR_INVALID_ARG;
@@ -140,6 +144,7 @@ fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int64_t 
     L->hist = take(((size_t)kMaxDigits * kSortBlocksMax + kMaxDigits) * 4);
     L->ranges = take((size_t)VS.total_tiles * 8);
     L->grad2d = take(s * 48);
+    L->aux = aux ? take(s * 16) : 0;
     L->fixed_bytes = off;
     if (capacity < 0) {
         if (state_bytes < L->fixed_bytes) return FGS4D_ERR_CAPACITY;
@@ -200,7 +205,8 @@ fgs4d_status prepare(int64_t n, const fgs4d_view* views, int n_views, const fgs4
     if (s != FGS4D_OK) return s;
     if (!state || !aligned(state, kAlign)) return FGS4D_ERR_INVALID_ARG;
     if ((s = make_views(views, n_views, opt, &P->VS)) != FGS4D_OK) return s;
-    if ((s = make_layout(n, P->VS, opt->record_fp16, -1, state_bytes, &P->L)) != FGS4D_OK) return s;
+    if ((s = make_layout(n, P->VS, opt->record_fp16, opt->aux_channels, -1, state_bytes, &P->L)) != FGS4D_OK)
+        return s;
     P->O = dev_options(opt);
     return FGS4D_OK;
 }
@@ -254,6 +260,8 @@ void fgs4d_default_options(fgs4d_options* o) {
     o->conic_cond = 1e-4f;
     o->tile_size = FGS4D_TILE;
     o->batch_depth = 256;
+    o->aux_channels = 0;
+    o->flow_dt = 1.0f / 300.0f;
 }
 
 int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {
@@ -271,7 +279,7 @@ fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view* views, int n_views, i
     ViewSet* VS = new ViewSet;
     s = make_views(views, n_views, opt, VS);
     StateLayout L;
-    if (s == FGS4D_OK) s = make_layout(n, *VS, opt->record_fp16, pair_capacity, 0, &L);
+    if (s == FGS4D_OK) s = make_layout(n, *VS, opt->record_fp16, opt->aux_channels, pair_capacity, 0, &L);
     delete VS;
     if (s != FGS4D_OK) return s;
     *bytes = L.total;
@@ -334,6 +342,18 @@ fgs4d_status fgs4d_sample_split(const fgs4d_gaussians* g, const int64_t* index, 
     if (m < 0 || (m > 0 && (!index || !z || !out_mu))) return FGS4D_ERR_INVALID_ARG;
     if (!aligned(index, 8) || !aligned(z, 4) || !aligned(out_mu, 4)) return FGS4D_ERR_INVALID_ARG;
     return cuda_status(launch_sample_split(G, index, z, m, out_mu, (cudaStream_t)stream));
+}
+
+fgs4d_status fgs4d_render_aux(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
+                              size_t state_bytes, float* aux_image, fgs4d_stream stream) {
+    if (!aux_image || !aligned(aux_image, 4) || !opt || opt->aux_channels != 1) return FGS4D_ERR_INVALID_ARG;
+    Prepared* P = new Prepared;
+    fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
+    if (s == FGS4D_OK)
+        s = cuda_status(launch_render_aux(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), aux_image,
+                                          (cudaStream_t)stream));
+    delete P;
+    return s;
 }
 
 fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt,
@@ -422,7 +442,7 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views,
     if (s != FGS4D_OK) return s;
     Prepared* P = new Prepared;
     s = make_views(views, n_views, opt, &P->VS);
-    if (s == FGS4D_OK) s = make_layout(n, P->VS, opt->record_fp16, -1, state_bytes, &P->L);
+    if (s == FGS4D_OK) s = make_layout(n, P->VS, opt->record_fp16, opt->aux_channels, -1, state_bytes, &P->L);
     if (s == FGS4D_OK) {
         out->counters = P->L.counters;
         out->records = P->L.records;

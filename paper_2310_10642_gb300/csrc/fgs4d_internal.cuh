@@ -46,6 +46,8 @@ struct DevOpts {
     int record_fp16;
     int tile;   // screen tile side: 16 or 32
     int batch;  // records staged per shared-memory batch while compositing: 32..256
+    int aux;    // store per-splat depth and flow (fgs4d_render_aux)
+    float flow_dt;
 };
 
 // Gaussian parameters (SoA) as the kernels see them.
@@ -79,6 +81,7 @@ struct StateLayout {
     size_t hist;           // uint32[kMaxDigits * kSortBlocksMax + kMaxDigits]
     size_t ranges;         // uint2[total_tiles]
     size_t grad2d;         // float4[3 * V*n] per-splat 2D gradient
+    size_t aux;            // float4[V*n] depth, flow u, flow v (0 when aux channels are off)
     size_t pair_keys[2];   // uint32[capacity] double buffer
     size_t pair_vals[2];   // uint32[capacity]
     size_t fixed_bytes;    // everything above except the pair buffers
@@ -602,6 +605,8 @@ cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout
                           float* image, float* final_T, int32_t* n_last, cudaStream_t st);
 cudaError_t launch_sample_split(const DevGauss& G, const int64_t* index, const float* z, int64_t m, float* out,
                                 cudaStream_t st);
+cudaError_t launch_render_aux(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
+                              float* aux_image, cudaStream_t st);
 cudaError_t launch_render_stats(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                 int pair_buf, float* image, float* final_T, int32_t* n_last,
                                 unsigned long long* stats, cudaStream_t st);

@@ -131,24 +131,30 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(uint32_t x) {
     return v;
 }
 
-// kStats additionally accumulates, into stats[0..3], the work the walk did:
-// (pixel, splat) pairs with the pixel inside the splat's support box and not
-// yet stopped, the pairs blended into the pixel, the sum of n_last, and the
-// pairs this kernel evaluated (pixel not stopped, its sub-region reached).  The
-// image, T and n_last it writes are those of the plain instantiation.
-template <int TS, class Rec, bool kStats>
+// kMode 0: the compositing of Eq. 6 (image, final T, n_last).
+// kMode 1: the same, and it accumulates into stats[0..3] the work the walk
+// did: (pixel, splat) pairs with the pixel inside the splat's support box and
+// not yet stopped, the pairs blended into the pixel, the sum of n_last, and
+// the pairs this kernel evaluated (pixel not stopped, its sub-region reached).
+// kMode 2: the same walk compositing each splat's aux record (depth, flow u,
+// flow v) instead of its colour, background 0, into aux_image only.
+template <int TS, class Rec, int kMode>
 __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
                                                               const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ pair_vals,
                                                               const Rec* __restrict__ rec, uint32_t n_splats,
                                                               float* __restrict__ image, float* __restrict__ final_T,
                                                               int32_t* __restrict__ n_last,
-                                                              unsigned long long* __restrict__ stats) {
+                                                              unsigned long long* __restrict__ stats,
+                                                              const float4* __restrict__ aux_rec,
+                                                              float* __restrict__ aux_image) {
     using TP = TilePixels<TS>;
     constexpr int P = TP::P;
+    constexpr bool kStats = kMode == 1, kAux = kMode == 2;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
     __shared__ float4 s_c[kTilePix];
+    __shared__ float4 s_x[kAux ? kTilePix : 1];
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
@@ -185,10 +191,12 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
                 stage_record<Rec>(decode_record(rec[sid], O.ln_alpha_min), s_a[tid], s_b[tid], s_c[tid]);
+                if constexpr (kAux) s_x[tid] = aux_rec[sid];
             } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
                 s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
                 s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
                 s_c[tid] = make_float4(0.f, -1.f, -1.f, 0.f);
+                if constexpr (kAux) s_x[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         __syncthreads();
@@ -221,9 +229,16 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                 }
                 if (kStats) st_blend++;
                 const float w = alpha * T[k];
-                C0[k] = fmaf(b.z, w, C0[k]);
-                C1[k] = fmaf(b.w, w, C1[k]);
-                C2[k] = fmaf(c.x, w, C2[k]);
+                if constexpr (kAux) {
+                    const float4 x = s_x[j];
+                    C0[k] = fmaf(x.x, w, C0[k]);
+                    C1[k] = fmaf(x.y, w, C1[k]);
+                    C2[k] = fmaf(x.z, w, C2[k]);
+                } else {
+                    C0[k] = fmaf(b.z, w, C0[k]);
+                    C1[k] = fmaf(b.w, w, C1[k]);
+                    C2[k] = fmaf(c.x, w, C2[k]);
+                }
                 T[k] = Tn;
                 last[k] = pos1;
             }
@@ -238,11 +253,18 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
         }
     }
     const size_t npix = (size_t)V.width * V.height;
-    float* img = image + 3 * (size_t)V.pix_base;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         if (!inside[k]) continue;
         const size_t p = (size_t)fpy[k] * V.width + (size_t)fpx[k];
+        if constexpr (kAux) {
+            float* ax = aux_image + 3 * (size_t)V.pix_base;
+            ax[p] = C0[k];
+            ax[npix + p] = C1[k];
+            ax[2 * npix + p] = C2[k];
+            continue;
+        }
+        float* img = image + 3 * (size_t)V.pix_base;
         img[p] = fmaf(T[k], V.bg[0], C0[k]);
         img[npix + p] = fmaf(T[k], V.bg[1], C1[k]);
         img[2 * npix + p] = fmaf(T[k], V.bg[2], C2[k]);
@@ -454,10 +476,11 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     }
 }
 
-template <bool kStats>
+template <int kMode>
 static cudaError_t launch_fwd_tiles(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                     int pair_buf, float* image, float* final_T, int32_t* n_last,
-                                    unsigned long long* stats, cudaStream_t st) {
+                                    unsigned long long* stats, float* aux_image, cudaStream_t st) {
+    const auto* aux = kMode == 2 ? reinterpret_cast<const float4*>(state + lay.aux) : nullptr;
     if (VS.total_tiles == 0) return cudaSuccess;
     const auto* ranges = reinterpret_cast<const uint2*>(state + lay.ranges);
     const auto* pv = reinterpret_cast<const uint32_t*>(state + lay.pair_vals[pair_buf]);
@@ -466,30 +489,35 @@ static cudaError_t launch_fwd_tiles(const ViewSet& VS, const DevOpts& O, const S
     const uint32_t S = (uint32_t)lay.n_splats;
     const dim3 grid(VS.total_tiles);
     if (O.tile == 32 && O.record_fp16)
-        render_fwd_kernel<32, SplatRecordH, kStats>
-            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last, stats);
+        render_fwd_kernel<32, SplatRecordH, kMode>
+            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last, stats, aux, aux_image);
     else if (O.tile == 32)
-        render_fwd_kernel<32, SplatRecord, kStats>
-            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last, stats);
+        render_fwd_kernel<32, SplatRecord, kMode>
+            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last, stats, aux, aux_image);
     else if (O.record_fp16)
-        render_fwd_kernel<16, SplatRecordH, kStats>
-            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last, stats);
+        render_fwd_kernel<16, SplatRecordH, kMode>
+            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last, stats, aux, aux_image);
     else
-        render_fwd_kernel<16, SplatRecord, kStats>
-            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last, stats);
+        render_fwd_kernel<16, SplatRecord, kMode>
+            <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, image, final_T, n_last, stats, aux, aux_image);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_render(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
                           float* image, float* final_T, int32_t* n_last, cudaStream_t st) {
-    return launch_fwd_tiles<false>(VS, O, lay, state, pair_buf, image, final_T, n_last, nullptr, st);
+    return launch_fwd_tiles<0>(VS, O, lay, state, pair_buf, image, final_T, n_last, nullptr, nullptr, st);
 }
 
 cudaError_t launch_render_stats(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                 int pair_buf, float* image, float* final_T, int32_t* n_last,
                                 unsigned long long* stats, cudaStream_t st) {
-    return launch_fwd_tiles<true>(VS, O, lay, state, pair_buf, image, final_T, n_last, stats, st);
+    return launch_fwd_tiles<1>(VS, O, lay, state, pair_buf, image, final_T, n_last, stats, nullptr, st);
+}
+
+cudaError_t launch_render_aux(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int pair_buf,
+                              float* aux_image, cudaStream_t st) {
+    return launch_fwd_tiles<2>(VS, O, lay, state, pair_buf, nullptr, nullptr, nullptr, nullptr, aux_image, st);
 }
 
 static cudaError_t launch_bwd_tiles(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,

@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
                                                             const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
                                                             uint32_t* __restrict__ tiles_touched,
                                                             uint32_t* __restrict__ depth_key,
-                                                            uint32_t* __restrict__ counters) {
+                                                            uint32_t* __restrict__ counters,
+                                                            float4* __restrict__ aux) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G.n) return;
     const size_t n = (size_t)G.n;
@@ -89,6 +90,27 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
         }
         tiles_touched[idx] = (uint32_t)w.tiles;
         depth_key[idx] = __float_as_uint(w.xc[2]);
+        if (aux) {
+            // Eq. 9: mu_{xyz|t} moves by Sigma_{xyz,t} / Sigma_tt per unit of t; the flow is the
+            // displacement of its projection over flow_dt (0 where the moved mean is behind the camera)
+            const float k = O.flow_dt / c.S[15];
+            float xm[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const float m = fmaf(c.S[4 * i + 3], k, w.mu3[i]);
+                xm[i] = m;
+            }
+            float xc2[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+                xc2[i] = fmaf(V.W[i * 3 + 0], xm[0], fmaf(V.W[i * 3 + 1], xm[1], fmaf(V.W[i * 3 + 2], xm[2], V.tau[i])));
+            float fu = 0.0f, fv = 0.0f;
+            if (xc2[2] > 0.0f) {
+                fu = fmaf(V.fx, xc2[0] / xc2[2], V.cx) - w.u;
+                fv = fmaf(V.fy, xc2[1] / xc2[2], V.cy) - w.v;
+            }
+            aux[idx] = make_float4(w.xc[2], fu, fv, 0.0f);
+        }
     }
 }
 
@@ -483,11 +505,12 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
     auto* rec = reinterpret_cast<SplatRecord*>(state + lay.records);
     auto* tt = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
     auto* dk = reinterpret_cast<uint32_t*>(state + lay.depth_key);
+    auto* aux = O.aux ? reinterpret_cast<float4*>(state + lay.aux) : nullptr;
     switch (G.L) {
-        case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
-        case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
-        case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
-        default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters); break;
+        case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
+        case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
+        case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
+        default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
     }
     count_launches(1);
     return cudaGetLastError();

@@ -98,7 +98,8 @@ class Options(ctypes.Structure):
     _fields_ = [("p_min", ctypes.c_float), ("near_z", ctypes.c_float), ("alpha_min", ctypes.c_float),
                 ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("clamp_fov", ctypes.c_float), ("record_fp16", ctypes.c_int), ("schur_cond", ctypes.c_float),
-                ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int), ("batch_depth", ctypes.c_int)]
+                ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int), ("batch_depth", ctypes.c_int),
+                ("aux_channels", ctypes.c_int), ("flow_dt", ctypes.c_float)]
 
 
 class GaussianGrads(ctypes.Structure):
@@ -128,7 +129,8 @@ EXPORTS = ["fgs4d_abi_version", "fgs4d_launch_count", "fgs4d_status_string", "fg
            "fgs4d_total_pixels", "fgs4d_slice_project", "fgs4d_bin_sort", "fgs4d_render", "fgs4d_render_backward",
            "fgs4d_state_layout", "fgs4d_read_counters", "fgs4d_render_backward_noalloc", "fgs4d_render_stats",
            "fgs4d_render_backward_2d", "fgs4d_project_backward",
-           "fgs4d_loss_scratch_size", "fgs4d_loss_l1_dssim", "fgs4d_adam_step", "fgs4d_sample_split"]
+           "fgs4d_loss_scratch_size", "fgs4d_loss_l1_dssim", "fgs4d_adam_step", "fgs4d_sample_split",
+           "fgs4d_render_aux"]
 NOALLOC_MAX_SPLATS = 262144
 
 
@@ -176,6 +178,9 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                                                  ctypes.POINTER(Options), vp, ctypes.c_size_t,
                                                  ctypes.POINTER(GaussianGrads), vp]
             L.fgs4d_read_counters.argtypes = [vp, ctypes.POINTER(Counters), vp]
+            L.fgs4d_render_aux.argtypes = [i64, ctypes.POINTER(View), ci, ctypes.POINTER(Options), vp,
+                                           ctypes.c_size_t, vp, vp]
+            L.fgs4d_render_aux.restype = ci
             L.fgs4d_sample_split.argtypes = [ctypes.POINTER(Gaussians), vp, vp, i64, vp, vp]
             L.fgs4d_sample_split.restype = ci
             L.fgs4d_loss_scratch_size.argtypes = [ctypes.POINTER(View), ci]
@@ -272,6 +277,12 @@ def fgs4d_project_backward(g: Gaussians, views, n_views: int, opts: Options, sta
     _check("fgs4d_project_backward", lib().fgs4d_project_backward(ctypes.byref(g), views, int(n_views),
                                                                    ctypes.byref(opts), state, state_bytes,
                                                                    ctypes.byref(grads), stream))
+
+
+def fgs4d_render_aux(n: int, views, n_views: int, opts: Options, state: int, state_bytes: int, aux_image: int,
+                     stream: int):
+    _check("fgs4d_render_aux", lib().fgs4d_render_aux(int(n), views, int(n_views), ctypes.byref(opts), state,
+                                                       state_bytes, aux_image, stream))
 
 
 def fgs4d_sample_split(g: Gaussians, index: int, z: int, m: int, out_mu: int, stream: int):

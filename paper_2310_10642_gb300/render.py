@@ -115,6 +115,16 @@ class Frame:
         N.fgs4d_render(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
                        self.image.data_ptr(), self.final_T.data_ptr(), self.n_last.data_ptr(), _stream(stream))
 
+    def render_aux(self, stream=None) -> torch.Tensor:
+        """Depth and flow maps (packed like the image: per view [3][H][W] =
+        accumulated depth, flow u, flow v) over the current lists; the frame's
+        options must have aux_channels=1 before slice_project."""
+        if not hasattr(self, "aux_image"):
+            self.aux_image = torch.empty(3 * self.total_pixels, device=self.device, dtype=torch.float32)
+        N.fgs4d_render_aux(self.n, self.c_views, self.nv, self.c_opts, self.state.data_ptr(), self.state_bytes,
+                           self.aux_image.data_ptr(), _stream(stream))
+        return self.aux_image
+
     def render_stats(self, stream=None) -> dict:
         """render() plus the work counts of its walk (one synchronisation):
         pixel-splat pairs inside support boxes, pairs blended, sum of n_last,

@@ -777,3 +777,33 @@ def test_no_4drot_variant_against_oracle():
     both = (tt[0] > 0) & (tt[1] > 0)
     assert int(both.sum()) > 10
     assert torch.equal(rec[0, both, :5], rec[1, both, :5])  # u, v and the conic
+
+
+# ---------------------------------------------------------------------------- depth and flow maps
+@pytest.mark.parametrize("tile,mixed", [(16, False), (32, False), (32, True)])
+def test_depth_and_flow_maps_match_oracle(tile, mixed):
+    """fgs4d_render_aux: accumulated camera depth and the flow of the projected
+    conditional means over flow_dt, composited with the image's weights,
+    against the oracle's compositing of the same per-splat values."""
+    G, views = ragged_scene(n=2500, seed=53)
+    dt = 0.02
+    opts = dict(tile_size=tile, record_fp16=int(mixed), aux_channels=1, flow_dt=dt)
+    fr, p, imgs, Ts = gpu_forward(G, views, opts, shs_dtype=torch.bfloat16 if mixed else None)
+    img0 = fr.image.clone()
+    aux = [a.double().cpu().numpy() for a in fr.split(fr.render_aux().clone())]
+    torch.cuda.synchronize()
+    assert torch.equal(img0, fr.image)  # the aux walk leaves the image alone
+    Gr = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy()) if mixed else G
+    tol = 3e-3 if mixed else 2e-4
+    for v, a in zip(views, aux):
+        ref = O.render(Gr, v)
+        vals = O.aux_values(Gr, v, dt)
+        want = O.render_values(Gr, v, vals)
+        ok = ref["flags"] == 0
+        assert ok.mean() > 0.9
+        scale = np.abs(vals[np.abs(vals).sum(1) > 0]).max(axis=0)
+        for ch, name in enumerate(("depth", "flow u", "flow v")):
+            err = np.abs(a[ch] - want[ch])[ok].max() / scale[ch]
+            print(f"[parity] aux {name} tile {tile} mixed {mixed}: max error / value range {err:.3e}")
+            assert err <= tol, (name, err)
+        assert np.abs(want[1:]).max() > 1e-3  # the scene does move

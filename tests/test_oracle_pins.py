@@ -458,3 +458,52 @@ def test_backward_matches_central_differences(oracle, seed):
             assert abs(an - fds[0]) <= 1e-6 * max(1.0, abs(fds[0])), (key, idx, an, fds[0])
             checked += 1
     assert checked >= 50
+
+
+def test_render_values_uses_the_image_weights(oracle):
+    """orc_render_values (depth and flow maps) composites with the walk of
+    Eq. 6: a constant value c gives c (1 - T_final) (the weights alpha_i T_i
+    sum to 1 - T_final), and the splats' own colours give the image without
+    its background term."""
+    G = I.gaussians(1500, 71, 2, 1)
+    v = I.view((0.3, 0.1, 3.5), 48, 40, 0.4, bg=(0.2, 0.5, 0.8))
+    ref = oracle.render(G, v)
+    n = G["logit"].shape[0]
+    c = np.array([2.5, -1.0, 0.25])
+    out = oracle.render_values(G, v, np.tile(c, (n, 1)))
+    assert np.abs(out - c[:, None, None] * (1.0 - ref["T"])[None]).max() < 1e-12
+    col = oracle.project_all(G, v)["color"]
+    out = oracle.render_values(G, v, col)
+    bg = np.array(v["bg"])[:, None, None] * ref["T"][None]
+    assert np.abs(out - (ref["image"] - bg)).max() < 1e-12
+    assert (1.0 - ref["T"]).max() > 0.5  # not an empty image
+
+
+def test_aux_flow_is_the_projected_displacement(oracle):
+    """aux_values: zero flow without space-time coupling (q_l = q_r = 1); with
+    an x-t rotation the conditional mean moves by Sigma_xt / Sigma_tt per unit
+    of t (Eq. 9) and the flow is the pinhole projection of that move."""
+    v = I.view((0.0, 0.0, 4.0), 64, 64, 0.5)
+    dt = 0.01
+    one = np.array([1.0, 0.0, 0.0, 0.0])
+    G = I.gaussians(3, 72, 0, 0)
+    G["mu"][:] = np.array([[0.1, -0.2, 0.0, 0.5]] * 3).T
+    G["ql"][:] = one[:, None]
+    G["qr"][:] = one[:, None]
+    G["log_s"][:] = np.log(np.array([0.3, 0.2, 0.2, 0.1]))[:, None]  # anisotropic in x and t
+    aux = oracle.aux_values(G, v, dt)
+    assert np.abs(aux[:, 1:]).max() < 1e-12
+    # rotation by th in the x-t plane: Sigma_xt / Sigma_tt = (s_x^2 - s_t^2) sin cos / (s_x^2 sin^2 + s_t^2 cos^2)
+    th = 0.4
+    q = np.array([np.cos(th / 2), 0, 0, np.sin(th / 2)])
+    G["ql"][:] = q[:, None]
+    G["qr"][:] = q[:, None]
+    R = oracle.rotation4(G["ql"][:, 0], G["qr"][:, 0])  # the stored (float32) quaternions
+    Sigma = R @ np.diag(np.exp(2 * G["log_s"][:, 0].astype(np.float64))) @ R.T
+    vel = Sigma[:3, 3] / Sigma[3, 3]
+    aux = oracle.aux_values(G, v, dt)
+    Vm = np.asarray(v["viewmat"]).reshape(3, 4)
+    mu3, _, _ = oracle.condition(G["mu"][:, 0], Sigma, v["t"])
+    x0, x1 = Vm[:, :3] @ mu3 + Vm[:, 3], Vm[:, :3] @ (mu3 + vel * dt) + Vm[:, 3]
+    want = np.array([v["fx"] * (x1[0] / x1[2] - x0[0] / x0[2]), v["fy"] * (x1[1] / x1[2] - x0[1] / x0[2])])
+    assert np.abs(aux[0, 1:] - want).max() < 1e-12 and np.abs(want).max() > 1e-3
