@@ -430,15 +430,40 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
     if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
 }
 
+// Each thread takes four consecutive sorted keys (one 16-byte load; the key
+// buffer is 256-byte aligned) and its two neighbours; a tile's range starts
+// where its key differs from the previous one and ends where it differs from
+// the next.
 __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __restrict__ keys, const uint32_t* counters,
                                                           uint32_t capacity, uint32_t total_tiles,
                                                           uint2* __restrict__ ranges) {
     const uint32_t n = min(counters[1], capacity);
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t k = keys[i];
-        if (k >= total_tiles) continue;  // dump tile (sorts last)
-        if (i == 0 || keys[i - 1] != k) ranges[k].x = i;
-        if (i == n - 1 || keys[i + 1] != k) ranges[k].y = i + 1;
+    const uint32_t n4 = (n + 3) / 4;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * q;
+        uint32_t k[4];
+        if (i0 + 4 <= n) {
+            const uint4 v = reinterpret_cast<const uint4*>(keys)[q];
+            k[0] = v.x;
+            k[1] = v.y;
+            k[2] = v.z;
+            k[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) k[j] = i0 + j < n ? keys[i0 + j] : 0xffffffffu;
+        }
+        const uint32_t prev = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+        const uint32_t next = i0 + 4 < n ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t i = i0 + j;
+            const uint32_t kj = k[j];
+            if (i >= n || kj >= total_tiles) continue;  // past the end, or the dump tile (sorts last)
+            const uint32_t left = j == 0 ? prev : k[j - 1];
+            const uint32_t right = j == 3 ? next : k[j + 1];
+            if (i == 0 || left != kj) ranges[kj].x = i;
+            if (i == n - 1 || right != kj) ranges[kj].y = i + 1;
+        }
     }
 }
 
@@ -529,7 +554,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     e = radix_sort(pk, pv, &counters[1], cap, bits, hist, digit_total, Gp, st, out_buf);
     if (e != cudaSuccess) return e;
     // 6. ranges
-    tile_ranges_kernel<<<grid_cap((cap + 255) / 256, stride_grid), 256, 0, st>>>(pk[*out_buf], counters, cap,
+    tile_ranges_kernel<<<grid_cap((cap / 4 + 255) / 256, stride_grid), 256, 0, st>>>(pk[*out_buf], counters, cap,
                                                                                          VS.total_tiles,
                                                                                          ranges);
     count_launches(1);
