@@ -375,59 +375,120 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
                                                          uint32_t* counters, uint32_t capacity, int tile,
                                                          uint32_t* __restrict__ pair_keys,
                                                          uint32_t* __restrict__ pair_vals) {
+    constexpr unsigned F = 0xffffffffu;
     const uint32_t n_vis = min(counters[0], n_max);
     const int lane = threadIdx.x & 31;
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     bool overflow = false;
     for (uint32_t base = warp0 * 32; base < n_vis; base += n_warps * 32) {
+        // lane p prepares splat base + p: its box rect and its ellipse rows
         const uint32_t p = base + lane;
-        uint32_t sid = 0, o = 0, cnt = 0, x0 = 0, y0 = 0, wx = 1, cnt_rect = 0, tbase = 0, tiles_x = 1;
+        uint32_t sid = 0, o = 0, cnt = 0;
+        int rect[4] = {0, 0, -1, -1};
+        EllipseRows e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false};
         if (p < n_vis) {
             sid = sorted_splats[p];
-            const uint32_t v = sid / n_gauss;
-            const DevView& V = VS.v[v];
+            const DevView& V = VS.v[sid / n_gauss];
             const SplatView r =
                 rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
                          : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
-            int rect[4] = {0, 0, 0, 0};
-            cnt_rect = (uint32_t)box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect);
-            x0 = (uint32_t)rect[0];
-            y0 = (uint32_t)rect[1];
-            wx = (uint32_t)max(rect[2] - rect[0] + 1, 1);
-            tbase = V.tile_base;
-            tiles_x = (uint32_t)V.tiles_x;
+            if (box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect) > 0) e = ellipse_rows(r, ln_alpha_min);
             o = offsets[p];
             cnt = tiles[sid];
         }
+        // then the warp writes each splat's pairs: tile rows in parallel over the lanes, each
+        // row's tiles contiguous, rows in order (the order slice/project counted them in)
         for (int s = 0; s < 32; s++) {
-            const uint32_t s_cnt = __shfl_sync(0xffffffffu, cnt, s);
+            const uint32_t s_cnt = __shfl_sync(F, cnt, s);
             if (s_cnt == 0) continue;
-            const uint32_t s_sid = __shfl_sync(0xffffffffu, sid, s);
-            const uint32_t s_o = __shfl_sync(0xffffffffu, o, s);
-            const uint32_t s_x0 = __shfl_sync(0xffffffffu, x0, s);
-            const uint32_t s_y0 = __shfl_sync(0xffffffffu, y0, s);
-            const uint32_t s_wx = __shfl_sync(0xffffffffu, wx, s);
-            const uint32_t s_cr = __shfl_sync(0xffffffffu, cnt_rect, s);
-            const uint32_t s_tb = __shfl_sync(0xffffffffu, tbase, s);
-            const uint32_t s_tx = __shfl_sync(0xffffffffu, tiles_x, s);
-            for (uint32_t k = lane; k < s_cnt; k += 32) {
+            const uint32_t s_sid = __shfl_sync(F, sid, s), s_o = __shfl_sync(F, o, s);
+            int s_rect[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) s_rect[q] = __shfl_sync(F, rect[q], s);
+            EllipseRows se;
+            se.u = __shfl_sync(F, e.u, s);
+            se.v = __shfl_sync(F, e.v, s);
+            se.ba = __shfl_sync(F, e.ba, s);
+            se.ia = __shfl_sync(F, e.ia, s);
+            se.ks = __shfl_sync(F, e.ks, s);
+            se.rys = __shfl_sync(F, e.rys, s);
+            se.dyl = __shfl_sync(F, e.dyl, s);
+            se.exact = __shfl_sync(F, (int)e.exact, s) != 0;
+            const DevView& V = VS.v[s_sid / n_gauss];
+            const uint32_t tb = V.tile_base, tiles_x = (uint32_t)V.tiles_x;
+            const int rows = s_rect[3] - s_rect[1] + 1;
+            uint32_t written = 0;
+            for (int r0 = 0; r0 < rows; r0 += 32) {
+                const int ty = s_rect[1] + r0 + lane;
+                int tx0 = 0, nr = 0;
+                if (r0 + lane < rows) nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
+                int incl = nr;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(F, incl, off);
+                    if (lane >= off) incl += y;
+                }
+                const uint32_t tot = (uint32_t)__shfl_sync(F, incl, 31);
+                for (uint32_t b0 = 0; b0 < tot; b0 += 32) {  // uniform trip count: every lane shuffles
+                    const uint32_t kk = b0 + lane;
+                    int lo = 0, hi = 31;  // row of pair kk: the first lane whose inclusive count exceeds kk
+#pragma unroll
+                    for (int it = 0; it < 5; it++) {
+                        const int mid = (lo + hi) >> 1;
+                        if ((uint32_t)__shfl_sync(F, incl, mid) > kk) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    const uint32_t excl = (uint32_t)(__shfl_sync(F, incl, lo) - __shfl_sync(F, nr, lo));
+                    const uint32_t rx0 = (uint32_t)__shfl_sync(F, tx0, lo);
+                    const uint32_t at_k = written + kk;
+                    if (kk < tot && at_k < s_cnt) {
+                        const uint32_t at = s_o + at_k;
+                        if (at >= capacity) {
+                            overflow = true;
+                        } else {
+                            pair_keys[at] = tb + (uint32_t)(s_rect[1] + r0 + lo) * tiles_x + rx0 + (kk - excl);
+                            pair_vals[at] = s_sid;
+                        }
+                    }
+                }
+                written += tot;
+            }
+            // the count and the rows come from the same function on the same record, so this never
+            // runs; it keeps every slot of the splat defined (the dump tile sorts last)
+            for (uint32_t k = written + lane; k < s_cnt; k += 32) {
                 const uint32_t at = s_o + k;
                 if (at >= capacity) {
                     overflow = true;
                     break;
                 }
-                uint32_t key = VS.total_tiles;
-                if (k < s_cr) {
-                    const uint32_t ty = s_y0 + k / s_wx, tx = s_x0 + k % s_wx;
-                    key = s_tb + ty * s_tx + tx;
-                }
-                pair_keys[at] = key;
+                pair_keys[at] = VS.total_tiles;
                 pair_vals[at] = s_sid;
             }
         }
     }
     if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
+}
+
+// Exact tile count of each visible splat (the support ellipse's rows, as
+// emit_pairs_kernel will write them), replacing the box count that
+// slice/project left as the visibility flag.  One thread per visible splat.
+__global__ void __launch_bounds__(256) ellipse_count_kernel(const __grid_constant__ ViewSet VS, uint32_t n_gauss,
+                                                            const uint32_t* __restrict__ sorted_splats,
+                                                            const void* __restrict__ rec, int rec_fp16,
+                                                            float ln_alpha_min, uint32_t n_max,
+                                                            const uint32_t* counters, int tile,
+                                                            uint32_t* __restrict__ tiles) {
+    const uint32_t n_vis = min(counters[0], n_max);
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_vis; p += gridDim.x * blockDim.x) {
+        const uint32_t sid = sorted_splats[p];
+        const DevView& V = VS.v[sid / n_gauss];
+        const SplatView r = rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
+                                     : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
+        int rect[4];
+        const int box = box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect);
+        tiles[sid] = box > 0 ? (uint32_t)ellipse_tiles(r, ln_alpha_min, V, tile, rect) : 0u;
+    }
 }
 
 // Each thread takes four consecutive sorted keys (one 16-byte load; the key
@@ -537,12 +598,16 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     e = radix_sort(sk, sv, &counters[0], S, 32, hist, digit_total, Gs, st, &buf);
     if (e != cudaSuccess) return e;
     const uint32_t* sorted = sv[buf];
-    // 3. pair offsets in depth order -> counters[1]
+    // 3. exact tile counts (support ellipse), then pair offsets in depth order -> counters[1]
+    const int stride_grid = 16 * sm_count;
+    ellipse_count_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(
+        VS, (uint32_t)(S / (uint32_t)VS.n), sorted, rec, O.record_fp16, O.ln_alpha_min, S, counters, O.tile, tiles);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = device_scan(LoadTilesSorted{tiles, sorted}, StoreOffset{offsets}, &counters[0], S, scan_tmp, &counters[1], Gs,
                     st);
     if (e != cudaSuccess) return e;
     // 4. emission
-    const int stride_grid = 16 * sm_count;
     emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, O.record_fp16, O.ln_alpha_min, S,
                                                        counters, cap, O.tile, pk[0], pv[0]);
     count_launches(1);

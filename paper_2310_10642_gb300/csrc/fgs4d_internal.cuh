@@ -501,6 +501,70 @@ __device__ __forceinline__ int box_tiles(float u, float v, float hx, float hy, c
     return (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
 }
 
+// Tile binning by the support ellipse (reading R7 made tight).  alpha >=
+// alpha_min needs d^T Q d <= k, k = 2 ln(alpha_eff / alpha_min), Q the conic.
+// With rx = sqrt(k Sigma_00), ry = sqrt(k Sigma_11) (the box half extents
+// without their margin) the ellipse's left edge at height dy is
+//   x_l(dy) = -(b/a) dy - sqrt(k (1 - dy^2 / ry^2) / a)
+// (and x_r with + sqrt), convex (concave) in dy, extreme at
+// dy = +-(b/c) rx.  Over the pixel rows of tile row ty the reached columns
+// therefore run from x_l at the clamped leftmost dy to x_r at the clamped
+// rightmost dy.  k gets 0.2% and x, y half a pixel of slack, so every pixel
+// whose single-precision alpha can reach alpha_min lies in a counted tile.
+// Both the tile count (slice/project) and the emitted pairs (bin_sort) come
+// from this one function on the same record values.
+struct EllipseRows {
+    float u, v, ba, ia, ks, rys, dyl;
+    bool exact;  // false: degenerate shape, every tile of the box rect is kept
+};
+
+__device__ __forceinline__ EllipseRows ellipse_rows(const SplatView& r, float ln_alpha_min) {
+    EllipseRows e;
+    e.u = r.u;
+    e.v = r.v;
+    constexpr float kSlack = 1.002f;
+    const float k = 2.0f * fmaxf(logf(r.alpha_eff) - ln_alpha_min, 0.0f);
+    const float rx = r.hx - 0.5f, ry = r.hy - 0.5f;
+    e.exact = r.a > 0.0f && r.c > 0.0f && rx > 0.0f && ry > 0.0f && k > 0.0f;
+    e.ba = e.exact ? r.b / r.a : 0.0f;
+    e.ia = e.exact ? 1.0f / r.a : 0.0f;
+    e.ks = k * kSlack;
+    e.rys = ry * sqrtf(kSlack);
+    e.dyl = e.exact ? (r.b / r.c) * rx * sqrtf(kSlack) : 0.0f;
+    return e;
+}
+
+// Tiles [*tx0, *tx0 + count) of tile row ty reached by the ellipse, within
+// the box rect (x0, y0, x1, y1).
+__device__ __forceinline__ int ellipse_row_tiles(const EllipseRows& e, const DevView& V, int tile, const int* rect,
+                                                 int ty, int* tx0) {
+    *tx0 = rect[0];
+    if (!e.exact) return rect[2] - rect[0] + 1;
+    const float row_lo = (float)max(ty * tile, 0), row_hi = (float)min(ty * tile + tile - 1, V.height - 1);
+    const float lo = fmaxf(row_lo - 0.5f - e.v, -e.rys), hi = fminf(row_hi + 0.5f - e.v, e.rys);
+    if (!(lo <= hi)) return 0;
+    const float yl = fminf(fmaxf(e.dyl, lo), hi), yr = fminf(fmaxf(-e.dyl, lo), hi);
+    const float ql = yl / e.rys, qr = yr / e.rys;
+    const float xl = -e.ba * yl - sqrtf(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
+    const float xr = -e.ba * yr + sqrtf(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
+    const float px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f), px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
+    if (!(px0 <= px1)) return 0;
+    const int t0 = max((int)px0 / tile, rect[0]), t1 = min((int)px1 / tile, rect[2]);
+    *tx0 = t0;
+    return max(t1 - t0 + 1, 0);
+}
+
+__device__ __forceinline__ int ellipse_tiles(const SplatView& r, float ln_alpha_min, const DevView& V, int tile,
+                                             const int* rect) {
+    const EllipseRows e = ellipse_rows(r, ln_alpha_min);
+    int n = 0;
+    for (int ty = rect[1]; ty <= rect[3]; ty++) {
+        int tx0;
+        n += ellipse_row_tiles(e, V, tile, rect, ty, &tx0);
+    }
+    return n;
+}
+
 // Camera transform, Jacobian, 2D covariance, conic, support box and tile rect.
 // Returns false when the splat is culled (near plane, alpha_eff, empty rect).
 __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, const DevOpts& O, ViewGeom& w,

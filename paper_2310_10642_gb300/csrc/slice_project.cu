@@ -71,9 +71,11 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
         float col[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) col[ch] = fmaxf(raw[ch] + 0.5f, 0.0f);
+        // tiles_touched here is the support box's tile count: the visibility flag of the
+        // compaction; bin_sort replaces it by the support ellipse's count for the visible splats
         if (O.record_fp16) {
             const SplatRecordH h = encode_record_h(w.u, w.v, w.conic, w.cov[2], w.alpha_eff, col);
-            // bin by the box of the stored (fp16) conic, exactly as bin_sort will
+            // the box of the stored (16-bit) conic, exactly as bin_sort will decode it
             const SplatView d = decode_record(h, O.ln_alpha_min);
             w.tiles = box_tiles(d.u, d.v, d.hx, d.hy, V, O.tile, w.rect);
             if (w.tiles == 0) {
