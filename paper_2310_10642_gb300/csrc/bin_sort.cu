@@ -378,13 +378,14 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
     constexpr unsigned F = 0xffffffffu;
     const uint32_t n_vis = min(counters[0], n_max);
     const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     bool overflow = false;
     for (uint32_t base = warp0 * 32; base < n_vis; base += n_warps * 32) {
         // lane p prepares splat base + p: its box rect and its ellipse rows
         const uint32_t p = base + lane;
-        uint32_t sid = 0, o = 0, cnt = 0;
+        uint32_t sid = 0, o = 0, cnt = 0, nbox = 0;
         int rect[4] = {0, 0, -1, -1};
         EllipseRows e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false};
         if (p < n_vis) {
@@ -393,15 +394,18 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             const SplatView r =
                 rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
                          : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
-            if (box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect) > 0) e = ellipse_rows(r, ln_alpha_min);
+            nbox = (uint32_t)box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect);
+            if (nbox > 0) e = ellipse_rows(r, ln_alpha_min);
             o = offsets[p];
             cnt = tiles[sid];
         }
-        // then the warp writes each splat's pairs: tile rows in parallel over the lanes, each
-        // row's tiles contiguous, rows in order (the order slice/project counted them in)
+        // the warp walks each splat's box tiles row by row, 32 at a time; a lane keeps its tile
+        // when the ellipse's span of that row covers it, and a ballot packs the kept tiles into
+        // the splat's slots in the same order the count took them (row by row, left to right)
         for (int s = 0; s < 32; s++) {
             const uint32_t s_cnt = __shfl_sync(F, cnt, s);
             if (s_cnt == 0) continue;
+            const uint32_t s_box = __shfl_sync(F, nbox, s);
             const uint32_t s_sid = __shfl_sync(F, sid, s), s_o = __shfl_sync(F, o, s);
             int s_rect[4];
 #pragma unroll
@@ -417,42 +421,31 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             se.exact = __shfl_sync(F, (int)e.exact, s) != 0;
             const DevView& V = VS.v[s_sid / n_gauss];
             const uint32_t tb = V.tile_base, tiles_x = (uint32_t)V.tiles_x;
-            const int rows = s_rect[3] - s_rect[1] + 1;
+            const uint32_t wx = (uint32_t)(s_rect[2] - s_rect[0] + 1);
             uint32_t written = 0;
-            for (int r0 = 0; r0 < rows; r0 += 32) {
-                const int ty = s_rect[1] + r0 + lane;
-                int tx0 = 0, nr = 0;
-                if (r0 + lane < rows) nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
-                int incl = nr;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int y = __shfl_up_sync(F, incl, off);
-                    if (lane >= off) incl += y;
+            for (uint32_t b0 = 0; b0 < s_box; b0 += 32) {  // uniform trip count
+                const uint32_t k = b0 + lane;
+                bool keep = false;
+                uint32_t key = 0;
+                if (k < s_box) {
+                    const int ty = s_rect[1] + (int)(k / wx), tx = s_rect[0] + (int)(k % wx);
+                    int tx0;
+                    const int nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
+                    keep = tx >= tx0 && tx < tx0 + nr;
+                    key = tb + (uint32_t)ty * tiles_x + (uint32_t)tx;
                 }
-                const uint32_t tot = (uint32_t)__shfl_sync(F, incl, 31);
-                for (uint32_t b0 = 0; b0 < tot; b0 += 32) {  // uniform trip count: every lane shuffles
-                    const uint32_t kk = b0 + lane;
-                    int lo = 0, hi = 31;  // row of pair kk: the first lane whose inclusive count exceeds kk
-#pragma unroll
-                    for (int it = 0; it < 5; it++) {
-                        const int mid = (lo + hi) >> 1;
-                        if ((uint32_t)__shfl_sync(F, incl, mid) > kk) hi = mid;
-                        else lo = mid + 1;
-                    }
-                    const uint32_t excl = (uint32_t)(__shfl_sync(F, incl, lo) - __shfl_sync(F, nr, lo));
-                    const uint32_t rx0 = (uint32_t)__shfl_sync(F, tx0, lo);
-                    const uint32_t at_k = written + kk;
-                    if (kk < tot && at_k < s_cnt) {
-                        const uint32_t at = s_o + at_k;
-                        if (at >= capacity) {
-                            overflow = true;
-                        } else {
-                            pair_keys[at] = tb + (uint32_t)(s_rect[1] + r0 + lo) * tiles_x + rx0 + (kk - excl);
-                            pair_vals[at] = s_sid;
-                        }
+                const uint32_t kept = __ballot_sync(F, keep);
+                const uint32_t pos = written + (uint32_t)__popc(kept & lt);
+                if (keep && pos < s_cnt) {
+                    const uint32_t at = s_o + pos;
+                    if (at >= capacity) {
+                        overflow = true;
+                    } else {
+                        pair_keys[at] = key;
+                        pair_vals[at] = s_sid;
                     }
                 }
-                written += tot;
+                written += (uint32_t)__popc(kept);
             }
             // the count and the rows come from the same function on the same record, so this never
             // runs; it keeps every slot of the splat defined (the dump tile sorts last)

@@ -534,22 +534,32 @@ __device__ __forceinline__ EllipseRows ellipse_rows(const SplatView& r, float ln
     return e;
 }
 
+// The hardware square root (about one ulp): the spans carry half a pixel of
+// slack, far more than its error.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Tiles [*tx0, *tx0 + count) of tile row ty reached by the ellipse, within
-// the box rect (x0, y0, x1, y1).
+// the box rect (x0, y0, x1, y1).  tile is 16 or 32.
 __device__ __forceinline__ int ellipse_row_tiles(const EllipseRows& e, const DevView& V, int tile, const int* rect,
                                                  int ty, int* tx0) {
     *tx0 = rect[0];
     if (!e.exact) return rect[2] - rect[0] + 1;
-    const float row_lo = (float)max(ty * tile, 0), row_hi = (float)min(ty * tile + tile - 1, V.height - 1);
+    const int sh = tile == 32 ? 5 : 4;
+    const float row_lo = (float)(ty << sh), row_hi = (float)min((ty << sh) + tile - 1, V.height - 1);
     const float lo = fmaxf(row_lo - 0.5f - e.v, -e.rys), hi = fminf(row_hi + 0.5f - e.v, e.rys);
     if (!(lo <= hi)) return 0;
     const float yl = fminf(fmaxf(e.dyl, lo), hi), yr = fminf(fmaxf(-e.dyl, lo), hi);
-    const float ql = yl / e.rys, qr = yr / e.rys;
-    const float xl = -e.ba * yl - sqrtf(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
-    const float xr = -e.ba * yr + sqrtf(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
+    const float ir = 1.0f / e.rys;
+    const float ql = yl * ir, qr = yr * ir;
+    const float xl = -e.ba * yl - sqrt_approx(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
+    const float xr = -e.ba * yr + sqrt_approx(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
     const float px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f), px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
     if (!(px0 <= px1)) return 0;
-    const int t0 = max((int)px0 / tile, rect[0]), t1 = min((int)px1 / tile, rect[2]);
+    const int t0 = max((int)px0 >> sh, rect[0]), t1 = min((int)px1 >> sh, rect[2]);
     *tx0 = t0;
     return max(t1 - t0 + 1, 0);
 }
