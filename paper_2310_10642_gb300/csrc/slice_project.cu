@@ -196,15 +196,17 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
                 float ddt = 0.0f;
                 float graws[3];
+                // the time basis cos(2 pi f dt / T) and sin(...) for f = 0..K by angle addition from
+                // the f = 1 pair (computed once per splat, not once per order and channel)
+                const float arg1 = 2.0f * w.dt * G.inv_period;
+                const float c1 = cospif(arg1), s1 = sinpif(arg1);
                 for (int ch = 0; ch < 3; ch++) {
                     float P[16];
     #pragma unroll
                     for (int j = 0; j < NB; j++) P[j] = 0.0f;
                     float Q = 0.0f;
+                    float cf = 1.0f, sf = 0.0f;
                     for (int f = 0; f <= G.K; f++) {
-                        const float arg = 2.0f * (float)f * w.dt * G.inv_period;
-                        const float cf = cospif(arg);
-                        const float sf = sinpif(arg);
                         const float om = 6.283185307179586f * (float)f * G.inv_period;
                         float kY = 0.0f;
     #pragma unroll
@@ -214,6 +216,9 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                             kY = fmaf(k, Y[j], kY);
                         }
                         Q = fmaf(-om * sf, kY, Q);
+                        const float cn = fmaf(cf, c1, -sf * s1);
+                        sf = fmaf(sf, c1, cf * s1);
+                        cf = cn;
                     }
                     float raw = 0.0f;
     #pragma unroll
@@ -351,6 +356,10 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         m2d = segment_sum(m2d, lane, seg_last);
         mt = segment_sum(mt, lane, seg_last);
         if (!(active && c.ok && lane == seg_first)) continue;
+        // The leader rebuilds the rotation chain from the parameters, so that R, M and the
+        // quaternions are not live across the per-splat part above.
+        Core cl;
+        load_core(G, g, cl);
 
         // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
         float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
@@ -367,16 +376,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 for (int k = 0; k < 4; k++) {
                     float acc = 0.0f;
     #pragma unroll
-                    for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], c.M[j * 4 + k], acc);
+                    for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], cl.M[j * 4 + k], acc);
                     const float dM = 2.0f * acc;
-                    dR[i * 4 + k] = dM * c.s[k];
-                    gls[k] = fmaf(dM, c.R[i * 4 + k], gls[k]);
+                    dR[i * 4 + k] = dM * cl.s[k];
+                    gls[k] = fmaf(dM, cl.R[i * 4 + k], gls[k]);
                 }
     #pragma unroll
-            for (int k = 0; k < 4; k++) gls[k] *= c.s[k];
+            for (int k = 0; k < 4; k++) gls[k] *= cl.s[k];
             if (G.rot3) {
                 // R = blockdiag(R3(q), 1): dL/dq through the 3x3 block, then the normalisation
-                const float w = c.qln[0], x = c.qln[1], y = c.qln[2], z = c.qln[3];
+                const float w = cl.qln[0], x = cl.qln[1], y = cl.qln[2], z = cl.qln[3];
                 const float* d = dR;
                 const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[4] - x * d[6] - y * d[8] + x * d[9]);
                 const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[4] - 2.0f * x * d[5] - w * d[6] + z * d[8] +
@@ -388,13 +397,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 const float gq[4] = {gw, gx, gy, gz};
                 float dq = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 4; i++) dq = fmaf(gq[i], c.qln[i], dq);
+                for (int i = 0; i < 4; i++) dq = fmaf(gq[i], cl.qln[i], dq);
 #pragma unroll
-                for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * c.qln[i]) / c.nl;
+                for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * cl.qln[i]) / cl.nl;
             } else {
             float Lm[16], Rm[16];
-            left_matrix(c.qln, Lm);
-            right_matrix(c.qrn, Rm);
+            left_matrix(cl.qln, Lm);
+            right_matrix(cl.qrn, Rm);
             float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
     #pragma unroll
             for (int i = 0; i < 4; i++)
@@ -416,16 +425,16 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
             float dl = 0.0f, dr = 0.0f;
     #pragma unroll
             for (int i = 0; i < 4; i++) {
-                dl = fmaf(gl[i], c.qln[i], dl);
-                dr = fmaf(gr[i], c.qrn[i], dr);
+                dl = fmaf(gl[i], cl.qln[i], dl);
+                dr = fmaf(gr[i], cl.qrn[i], dr);
             }
     #pragma unroll
             for (int i = 0; i < 4; i++) {
-                gql[i] = (gl[i] - dl * c.qln[i]) / c.nl;
-                gqr[i] = (gr[i] - dr * c.qrn[i]) / c.nr;
+                gql[i] = (gl[i] - dl * cl.qln[i]) / cl.nl;
+                gqr[i] = (gr[i] - dr * cl.qrn[i]) / cl.nr;
             }
             }
-            glogit = galpha * c.alpha * (1.0f - c.alpha);
+            glogit = galpha * cl.alpha * (1.0f - cl.alpha);
         } else {
     #pragma unroll
             for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
