@@ -387,10 +387,12 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
         const uint32_t p = base + lane;
         uint32_t sid = 0, o = 0, cnt = 0, nbox = 0;
         int rect[4] = {0, 0, -1, -1};
-        EllipseRows e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false};
+        EllipseRows e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false};
+        int vw = 0;
         if (p < n_vis) {
             sid = sorted_splats[p];
-            const DevView& V = VS.v[sid / n_gauss];
+            vw = (int)(sid / n_gauss);
+            const DevView& V = VS.v[vw];
             const SplatView r =
                 rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
                          : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
@@ -417,20 +419,29 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__
             se.ia = __shfl_sync(F, e.ia, s);
             se.ks = __shfl_sync(F, e.ks, s);
             se.rys = __shfl_sync(F, e.rys, s);
+            se.irys = __shfl_sync(F, e.irys, s);
             se.dyl = __shfl_sync(F, e.dyl, s);
             se.exact = __shfl_sync(F, (int)e.exact, s) != 0;
-            const DevView& V = VS.v[s_sid / n_gauss];
+            const DevView& V = VS.v[__shfl_sync(F, vw, s)];
             const uint32_t tb = V.tile_base, tiles_x = (uint32_t)V.tiles_x;
             const uint32_t wx = (uint32_t)(s_rect[2] - s_rect[0] + 1);
+            const float inv_wx = 1.0f / (float)wx;
+            // spans of the first 32 rows, one per lane; rows beyond are computed where needed
+            int row_tx0 = 0, row_nr = 0;
+            if (s_rect[1] + lane <= s_rect[3])
+                row_nr = ellipse_row_tiles(se, V, tile, s_rect, s_rect[1] + lane, &row_tx0);
             uint32_t written = 0;
             for (uint32_t b0 = 0; b0 < s_box; b0 += 32) {  // uniform trip count
                 const uint32_t k = b0 + lane;
+                uint32_t r = (uint32_t)((float)k * inv_wx);  // k / wx, corrected to the exact quotient
+                if (r * wx > k) r--;
+                else if ((r + 1) * wx <= k) r++;
+                int tx0 = __shfl_sync(F, row_tx0, r & 31u), nr = __shfl_sync(F, row_nr, r & 31u);
                 bool keep = false;
                 uint32_t key = 0;
                 if (k < s_box) {
-                    const int ty = s_rect[1] + (int)(k / wx), tx = s_rect[0] + (int)(k % wx);
-                    int tx0;
-                    const int nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
+                    const int ty = s_rect[1] + (int)r, tx = s_rect[0] + (int)(k - r * wx);
+                    if (r >= 32u) nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
                     keep = tx >= tx0 && tx < tx0 + nr;
                     key = tb + (uint32_t)ty * tiles_x + (uint32_t)tx;
                 }

@@ -514,7 +514,7 @@ __device__ __forceinline__ int box_tiles(float u, float v, float hx, float hy, c
 // Both the tile count (slice/project) and the emitted pairs (bin_sort) come
 // from this one function on the same record values.
 struct EllipseRows {
-    float u, v, ba, ia, ks, rys, dyl;
+    float u, v, ba, ia, ks, rys, irys, dyl;
     bool exact;  // false: degenerate shape, every tile of the box rect is kept
 };
 
@@ -530,6 +530,7 @@ __device__ __forceinline__ EllipseRows ellipse_rows(const SplatView& r, float ln
     e.ia = e.exact ? 1.0f / r.a : 0.0f;
     e.ks = k * kSlack;
     e.rys = ry * sqrtf(kSlack);
+    e.irys = e.exact ? 1.0f / e.rys : 0.0f;
     e.dyl = e.exact ? (r.b / r.c) * rx * sqrtf(kSlack) : 0.0f;
     return e;
 }
@@ -553,8 +554,7 @@ __device__ __forceinline__ int ellipse_row_tiles(const EllipseRows& e, const Dev
     const float lo = fmaxf(row_lo - 0.5f - e.v, -e.rys), hi = fminf(row_hi + 0.5f - e.v, e.rys);
     if (!(lo <= hi)) return 0;
     const float yl = fminf(fmaxf(e.dyl, lo), hi), yr = fminf(fmaxf(-e.dyl, lo), hi);
-    const float ir = 1.0f / e.rys;
-    const float ql = yl * ir, qr = yr * ir;
+    const float ql = yl * e.irys, qr = yr * e.irys;
     const float xl = -e.ba * yl - sqrt_approx(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
     const float xr = -e.ba * yr + sqrt_approx(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
     const float px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f), px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
