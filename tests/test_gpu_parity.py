@@ -830,3 +830,55 @@ def test_depth_and_flow_maps_match_oracle(tile, mixed):
             print(f"[parity] aux {name} tile {tile} mixed {mixed}: max error / value range {err:.3e}")
             assert err <= tol, (name, err)
         assert np.abs(want[1:]).max() > 1e-3  # the scene does move
+
+
+# ---------------------------------------------------------------------------- maximum sizes, other workloads
+def test_maximum_sizes():
+    """The largest batch (FGS4D_MAX_VIEWS views of uneven sizes in one launch)
+    and the widest and tallest images the ABI accepts (16384 pixels)."""
+    from paper_2310_10642_gb300 import native as N
+    G = I.gaussians(3000, 81, 2, 1)
+    r = np.random.default_rng(8)
+    views = [I.view(tuple(r.normal(size=3) * 0.3 + np.array([0.0, 0.0, 3.6])), int(r.integers(8, 40)),
+                    int(r.integers(8, 40)), float(r.uniform())) for _ in range(N.MAX_VIEWS)]
+    for tile in (16, 32):
+        _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
+        for i in (0, 63, N.MAX_VIEWS - 1):
+            assert_image_parity(imgs[i], Ts[i], O.render(G, views[i]), max_flag_frac=1.0)
+    # 50 degrees along the long side, so each view sees the scene through a thin slot
+    for w, h in ((16384, 3), (5, 16384)):
+        fx = 0.5 * max(w, h) / math.tan(math.radians(25.0))
+        v = I.view((0.0, 0.0, 3.0), w, h, 0.5, fov_x_deg=2.0 * math.degrees(math.atan(0.5 * w / fx)))
+        _, _, imgs, Ts = gpu_forward(G, [v], dict(tile_size=32))
+        assert_image_parity(imgs[0], Ts[0], O.render(G, v), max_flag_frac=1.0)
+
+
+def test_config1_crops_and_gradients():
+    """Differentiable render at the 100k-Gaussian workload (16 cameras on a
+    sphere, 800x800, per-view t): 64x64 crops of two views against the oracle,
+    and the gradient of a loss on those crops."""
+    c = I.config(1)
+    G, views = c["gaussians"], c["views"]
+    fr, p, imgs, Ts = gpu_forward(G, views, dict(c["options"], tile_size=32))
+    crop = 64
+    dL = [np.zeros((3, v["height"], v["width"])) for v in views]
+    rng = np.random.default_rng(21)
+    picks = [3, 11]
+    for vi in picks:
+        v = views[vi]
+        x0, y0 = v["width"] // 2 - crop // 2, v["height"] // 2 - crop // 2
+        ref = O.render(G, v, window=(x0, y0, crop, crop), prefilter=True)
+        st = assert_image_parity(imgs[vi][:, y0:y0 + crop, x0:x0 + crop], Ts[vi][y0:y0 + crop, x0:x0 + crop], ref)
+        print(f"[parity] config 1 view {vi} crop: {st}")
+        w = rng.normal(size=(3, crop, crop))
+        w[:, ref["flags"] != 0] = 0.0
+        dL[vi][:, y0:y0 + crop, x0:x0 + crop] = w
+    gg = grads_gpu(fr, p, dL)
+    go = None
+    for vi in picks:
+        v = views[vi]
+        x0, y0 = v["width"] // 2 - crop // 2, v["height"] // 2 - crop // 2
+        gv = O.backward(G, v, dL[vi][:, y0:y0 + crop, x0:x0 + crop], window=(x0, y0, crop, crop), prefilter=True)
+        gv.pop("grad2d")
+        go = gv if go is None else {k: go[k] + gv[k] for k in go}
+    assert_grad_parity(gg, go)
