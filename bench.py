@@ -589,63 +589,16 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in host_p.values()) + host_dL.numel() * 4
         d2h = host_img.numel() * 4 + sum(t.numel() * 4 for t in host_g.values())
 
-        # Pipelined across steps: while step k computes, the inputs of step k + 1 are copied in
-        # and the outputs of step k - 1 copied out on two copy streams, into and out of two
-        # device buffer sets; events keep a buffer from being overwritten while in use.
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-        slots = []
-        for _ in range(2):
-            dp = {k: torch.empty_like(p[k]) for k in R.PARAM_KEYS}
-            dp.update({k: p[k] for k in ("sh_degree", "n_freq", "period")})
-            slots.append(dict(p=dp, dL=torch.empty_like(dL), img=torch.empty(3 * npix, device="cuda"),
-                              g={k: torch.empty(p[k].shape, device="cuda") for k in R.PARAM_KEYS},
-                              ev_in=torch.cuda.Event(), ev_used=torch.cuda.Event(), ev_out=torch.cuda.Event()))
-        for sl in slots:  # every event starts recorded, so the first waits do not block
-            for ev in ("ev_in", "ev_used", "ev_out"):
-                sl[ev].record(stream)
-
-        def copy_in(sl):
-            with torch.cuda.stream(s_in):
-                s_in.wait_event(sl["ev_used"])  # the step that last read this slot is done
-                for k in R.PARAM_KEYS:
-                    sl["p"][k].copy_(host_p[k], non_blocking=True)
-                sl["dL"].copy_(host_dL, non_blocking=True)
-                sl["ev_in"].record(s_in)
-
-        def compute(sl):
-            stream.wait_event(sl["ev_in"])
-            stream.wait_event(sl["ev_out"])  # the outputs of this slot have left the device
-            frame.slice_project(sl["p"])
-            frame.bin_sort()
-            frame.render()
-            frame.backward(sl["p"], sl["dL"], sl["g"])
-            sl["img"].copy_(frame.image, non_blocking=True)
-            sl["ev_used"].record(stream)
-
-        def copy_out(sl):
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(sl["ev_used"])
-                host_img.copy_(sl["img"], non_blocking=True)
-                for k in R.PARAM_KEYS:
-                    host_g[k].copy_(sl["g"][k], non_blocking=True)
-                sl["ev_out"].record(s_out)
-
-        def run_e2e(steps):
-            copy_in(slots[0])
-            for k in range(steps):
-                if k + 1 < steps:
-                    copy_in(slots[(k + 1) % 2])
-                compute(slots[k % 2])
-                copy_out(slots[k % 2])
-            stream.wait_stream(s_out)
-
-        run_e2e(3)
+        # pipelined across steps (HostPipeline): the inputs of step k + 1 go in and the outputs of
+        # step k - 1 come out on copy streams while step k computes
+        from paper_2310_10642_gb300.pipeline import HostPipeline
+        pipe = HostPipeline(frame, p)
+        pipe.run([(host_p, host_dL)] * 3, [(host_img, host_g)] * 3)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ks = max(3, min(args.steps, 10))
         e0.record(stream)
-        s_in.wait_stream(stream)
-        run_e2e(ks)
+        pipe.run([(host_p, host_dL)] * ks, [(host_img, host_g)] * ks)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1) / ks

@@ -882,3 +882,34 @@ def test_config1_crops_and_gradients():
         gv.pop("grad2d")
         go = gv if go is None else {k: go[k] + gv[k] for k in go}
     assert_grad_parity(gg, go)
+
+
+def test_host_pipeline_equals_plain_steps():
+    """HostPipeline (copies of neighbouring steps overlapped with compute)
+    returns, for each step's host inputs, what a plain forward + backward of
+    those inputs returns."""
+    from paper_2310_10642_gb300 import render as R
+    from paper_2310_10642_gb300.pipeline import HostPipeline
+    G, views = ragged_scene(n=1500, seed=61)
+    p = R.params_to_device(G)
+    fr = R.Frame(G["logit"].shape[0], views, dict(tile_size=32))
+    fr.forward(p)
+    npix = fr.total_pixels
+    gen = torch.Generator().manual_seed(2)
+    inputs, outputs, want = [], [], []
+    for k in range(3):
+        hp = {key: (p[key].cpu() + (0.01 * k if key == "mu" else 0.0)).pin_memory() for key in R.PARAM_KEYS}
+        hd = torch.randn(3 * npix, generator=gen).pin_memory()
+        inputs.append((hp, hd))
+        outputs.append((torch.empty(3 * npix).pin_memory(),
+                        {key: torch.empty(p[key].shape).pin_memory() for key in R.PARAM_KEYS}))
+        dp = dict(p, **{key: hp[key].cuda() for key in R.PARAM_KEYS})
+        fr.forward(dp, check=False)
+        g = fr.backward(dp, hd.cuda())
+        want.append((fr.image.cpu(), {key: v.cpu() for key, v in g.items()}))
+    HostPipeline(fr, p).run(inputs, outputs)
+    torch.cuda.synchronize()
+    for (img, g), (wi, wg) in zip(outputs, want):
+        assert torch.equal(img, wi)
+        for key in R.PARAM_KEYS:
+            assert float((g[key] - wg[key]).norm() / wg[key].norm()) < 1e-5, key
