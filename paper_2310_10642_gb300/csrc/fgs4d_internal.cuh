@@ -278,11 +278,9 @@ __device__ __forceinline__ void sh_grad(int L, float x, float y, float z, const 
     }
 }
 
-__device__ __forceinline__ float load_sh(const DevGauss& G, int row, int g) {
-    const size_t i = (size_t)row * (size_t)G.n + (size_t)g;
-    if (G.shs_bf16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(G.shs)[i]);
-    return __ldg(reinterpret_cast<const float*>(G.shs) + i);
-}
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+
 
 // ---------------------------------------------------------------------------
 // Per-Gaussian, view-independent part: activations, R = L(q_l) R(q_r),

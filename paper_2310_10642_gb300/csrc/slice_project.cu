@@ -17,24 +17,81 @@
 
 namespace fgs4d {
 
+// Coefficients of Gaussian g: row r at sh[r * n]; one address increment per
+// row (row stride n), the storage type resolved outside the loops.
+template <int L, class T>
+__device__ __forceinline__ void color_sum(const T* __restrict__ sh, size_t n, int K, float dt_scaled, const float* Y,
+                                          float* raw) {
+    constexpr int NB = (L + 1) * (L + 1);
+    raw[0] = raw[1] = raw[2] = 0.0f;
+    for (int f = 0; f <= K; f++) {
+        const float cf = cospif((float)f * dt_scaled);
+        const T* row = sh + (size_t)(f * NB * 3) * n;
+#pragma unroll
+        for (int j = 0; j < NB; j++) {
+            const float b = cf * Y[j];
+            raw[0] = fmaf(b, to_float(__ldg(row)), raw[0]);
+            raw[1] = fmaf(b, to_float(__ldg(row + n)), raw[1]);
+            raw[2] = fmaf(b, to_float(__ldg(row + 2 * n)), raw[2]);
+            row += 3 * n;
+        }
+    }
+}
+
 template <int L>
 __device__ __forceinline__ void color_forward(const DevGauss& G, int g, const ViewGeom& w, const DevView& V,
                                               float* raw) {
-    constexpr int NB = (L + 1) * (L + 1);
     float d[3];
     view_dir(w, V, d);
     float Y[16];
     sh_eval(L, d[0], d[1], d[2], Y);
-    raw[0] = raw[1] = raw[2] = 0.0f;
-    for (int f = 0; f <= G.K; f++) {
-        const float cf = cospif(2.0f * (float)f * w.dt * G.inv_period);
+    const float dts = 2.0f * w.dt * G.inv_period;
+    if (G.shs_bf16)
+        color_sum<L>(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
+    else
+        color_sum<L>(reinterpret_cast<const float*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
+}
+
+// Colour part of the adjoint for one splat (Eq. 11): per channel the raw
+// colour, its clamp, the cotangent graw, and the sums wsum_j = sum_ch graw P_j
+// (P_j = sum_f cos_f k_fj) and ddt = sum_ch graw sum_f dcos_f/ddt kY_f that the
+// direction and time gradients need.  cos/sin of the orders by angle addition.
+template <int L, class T>
+__device__ __forceinline__ void color_adjoint(const T* __restrict__ sh, size_t n, int K, float c1, float s1,
+                                              float inv_period, const float* Y, const float* dcol, float* wsum,
+                                              float& ddt, float* graws) {
+    constexpr int NB = (L + 1) * (L + 1);
+    for (int ch = 0; ch < 3; ch++) {
+        float P[16];
 #pragma unroll
-        for (int j = 0; j < NB; j++) {
-            const float b = cf * Y[j];
-            const int row = (f * NB + j) * 3;
-            raw[0] = fmaf(b, load_sh(G, row + 0, g), raw[0]);
-            raw[1] = fmaf(b, load_sh(G, row + 1, g), raw[1]);
-            raw[2] = fmaf(b, load_sh(G, row + 2, g), raw[2]);
+        for (int j = 0; j < NB; j++) P[j] = 0.0f;
+        float Q = 0.0f;
+        float cf = 1.0f, sf = 0.0f;
+        const T* row = sh + (size_t)ch * n;
+        for (int f = 0; f <= K; f++) {
+            const float om = 6.283185307179586f * (float)f * inv_period;
+            float kY = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; j++) {
+                const float k = to_float(__ldg(row));
+                row += 3 * n;
+                P[j] = fmaf(cf, k, P[j]);
+                kY = fmaf(k, Y[j], kY);
+            }
+            Q = fmaf(-om * sf, kY, Q);
+            const float cn = fmaf(cf, c1, -sf * s1);
+            sf = fmaf(sf, c1, cf * s1);
+            cf = cn;
+        }
+        float raw = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
+        const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
+        graws[ch] = graw;
+        if (graw != 0.0f) {
+#pragma unroll
+            for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
+            ddt = fmaf(graw, Q, ddt);
         }
     }
 }
@@ -196,41 +253,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
                 float ddt = 0.0f;
                 float graws[3];
-                // the time basis cos(2 pi f dt / T) and sin(...) for f = 0..K by angle addition from
-                // the f = 1 pair (computed once per splat, not once per order and channel)
                 const float arg1 = 2.0f * w.dt * G.inv_period;
                 const float c1 = cospif(arg1), s1 = sinpif(arg1);
-                for (int ch = 0; ch < 3; ch++) {
-                    float P[16];
-    #pragma unroll
-                    for (int j = 0; j < NB; j++) P[j] = 0.0f;
-                    float Q = 0.0f;
-                    float cf = 1.0f, sf = 0.0f;
-                    for (int f = 0; f <= G.K; f++) {
-                        const float om = 6.283185307179586f * (float)f * G.inv_period;
-                        float kY = 0.0f;
-    #pragma unroll
-                        for (int j = 0; j < NB; j++) {
-                            const float k = load_sh(G, (f * NB + j) * 3 + ch, g);
-                            P[j] = fmaf(cf, k, P[j]);
-                            kY = fmaf(k, Y[j], kY);
-                        }
-                        Q = fmaf(-om * sf, kY, Q);
-                        const float cn = fmaf(cf, c1, -sf * s1);
-                        sf = fmaf(sf, c1, cf * s1);
-                        cf = cn;
-                    }
-                    float raw = 0.0f;
-    #pragma unroll
-                    for (int j = 0; j < NB; j++) raw = fmaf(P[j], Y[j], raw);
-                    const float graw = (raw + 0.5f > 0.0f) ? dcol[ch] : 0.0f;
-                    graws[ch] = graw;
-                    if (graw != 0.0f) {
-    #pragma unroll
-                        for (int j = 0; j < NB; j++) wsum[j] = fmaf(graw, P[j], wsum[j]);
-                        ddt = fmaf(graw, Q, ddt);
-                    }
-                }
+                if (G.shs_bf16)
+                    color_adjoint<L>(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, n, G.K, c1, s1,
+                                     G.inv_period, Y, dcol, wsum, ddt, graws);
+                else
+                    color_adjoint<L>(reinterpret_cast<const float*>(G.shs) + g, n, G.K, c1, s1, G.inv_period, Y,
+                                     dcol, wsum, ddt, graws);
                 // colour cotangent for the coefficient gradients (sh_backward_kernel)
                 grad2d[3 * idx + 0] = make_float4(d[0], d[1], d[2], w.dt);
                 grad2d[3 * idx + 1] = make_float4(graws[0], graws[1], graws[2], 0.0f);
