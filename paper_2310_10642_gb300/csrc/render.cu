@@ -4,11 +4,13 @@
 // one pixel; with 32x32 tiles each thread owns a 2x2 block, which amortises
 // the shared-memory reads of a splat over four pixels and cuts the number of
 // (splat, tile) pairs the binning has to sort.  Each warp owns a compact
-// region of the tile (8x4 pixels, resp. 16x8 in four 8x4 sub-regions), so
-// that a splat whose support box misses the region (or a sub-region) is
-// skipped by the whole warp at once.  The tile's
-// depth-ordered splat list is walked in batches of 256: each thread gathers
-// one splat record into shared memory, then every pixel evaluates the batch.
+// region of the tile (8x4 pixels, resp. 16x8 in four 8x4 sub-regions).  The
+// tile's depth-ordered splat list is walked in batches of up to 256: each
+// thread gathers one splat record into shared memory together with a mask of
+// the 8x4 sub-regions its support box reaches; each warp then ballots over
+// the masks and visits, in list order, only the splats that reach one of its
+// own sub-regions (most splats are small next to a 32x32 tile and reach one
+// or two of its 32 sub-regions).
 // A CTA stops as soon as all its pixels have terminated (__syncthreads_count).
 //
 // Per pixel and splat (readings R4-R6):
@@ -106,23 +108,34 @@ struct TilePixels {
     // offset of pixel k from pixel 0 (exact in float)
     __device__ __forceinline__ static constexpr float off_x(int k) { return P == 4 ? (float)((k & 1) * 8) : 0.0f; }
     __device__ __forceinline__ static constexpr float off_y(int k) { return P == 4 ? (float)((k >> 1) * 4) : 0.0f; }
-    // Bit k set when the support box [u - hx, u + hx] x [v - hy, v + hy] may
-    // reach sub-region k; only called once the box meets the whole region.
-    __device__ __forceinline__ static unsigned sub_mask(float u, float v, float hx, float hy, float rx, float ry) {
-        if (P == 1) return 1u;
-        const bool xl = u - hx <= rx + 7.0f, xr = u + hx >= rx + 8.0f;
-        const bool yt = v - hy <= ry + 3.0f, yb = v + hy >= ry + 4.0f;
-        return (unsigned)(xl && yt) | ((unsigned)(xr && yt) << 1) | ((unsigned)(xl && yb) << 2) |
-               ((unsigned)(xr && yb) << 3);
+    // Sub-regions of the tile: NC = TS/8 columns of 8 pixels, NR = TS/4 rows
+    // of 4.  Sub-region (c, r) is sub-region k of warp w with
+    // bit(c, r) = w * P + k; warp w's P bits are its sub-regions 0..P-1.
+    static constexpr int NC = TS / 8, NR = TS / 4;
+    static constexpr int kSubAll = (1 << P) - 1;
+    __device__ __forceinline__ static constexpr int col_bit(int c) { return (c / (NC / 2)) * P + c % (NC / 2); }
+    __device__ __forceinline__ static constexpr int row_shift(int r) {
+        return (r / (NR / 4)) * 2 * P + (r % (NR / 4)) * (NC / 2);
+    }
+    // Bit bit(c, r) set when the support box [u - hx, u + hx] x [v - hy, v + hy]
+    // reaches the pixel centres of sub-region (c, r) of the tile whose corner
+    // pixel is (x0, y0).  Evaluated once per staged splat; every warp then
+    // visits only the splats with one of its own bits set.  Outside the box
+    // alpha < alpha_min, so a pixel of a sub-region without its bit would not
+    // have been blended.
+    __device__ __forceinline__ static uint32_t sub_masks(float u, float v, float hx, float hy, float x0, float y0) {
+        const float xl = u - hx, xr = u + hx, yt = v - hy, yb = v + hy;
+        uint32_t row = 0;
+#pragma unroll
+        for (int c = 0; c < NC; c++)
+            if (xr >= x0 + (float)(8 * c) && xl <= x0 + (float)(8 * c + 7)) row |= 1u << col_bit(c);
+        uint32_t m = 0;
+#pragma unroll
+        for (int r = 0; r < NR; r++)
+            if (yb >= y0 + (float)(4 * r) && yt <= y0 + (float)(4 * r + 3)) m |= row << row_shift(r);
+        return m;
     }
 };
-
-// True when the support box [u - hx, u + hx] x [v - hy, v + hy] reaches the
-// pixel-centre box [rx, rx + RW - 1] x [ry, ry + RH - 1].
-template <int RW, int RH>
-__device__ __forceinline__ bool box_meets_region(float u, float v, float hx, float hy, float rx, float ry) {
-    return (u + hx >= rx) && (u - hx <= rx + (float)(RW - 1)) && (v + hy >= ry) && (v - hy <= ry + (float)(RH - 1));
-}
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(uint32_t x) {
     unsigned long long v = x;
@@ -155,16 +168,16 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
     __shared__ float4 s_b[kTilePix];
     __shared__ float4 s_c[kTilePix];
     __shared__ float4 s_x[kAux ? kTilePix : 1];
-    const int tid = threadIdx.x;
+    __shared__ uint32_t s_m[kTilePix];  // sub-region mask of each staged splat
+    const int tid = threadIdx.x, lane = tid & 31, wshift = (tid >> 5) * P;
+    const unsigned F = 0xffffffffu;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
     const DevView& V = VS.v[v];
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
-    int irx, iry;
-    TP::region(tid, tx * TS, ty * TS, irx, iry);
-    const float frx = (float)irx, fry = (float)iry;
+    const float fx0 = (float)(tx * TS), fy0 = (float)(ty * TS);
     float fpx[P], fpy[P], T[P], C0[P], C1[P], C2[P];
     int32_t last[P];
     bool pdone[P], inside[P];
@@ -190,65 +203,71 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
         if (tid < B && idx < range.y) {
             const uint32_t sid = pair_vals[idx];
             if (sid < n_splats) {
-                stage_record<Rec>(decode_record(rec[sid], O.ln_alpha_min), s_a[tid], s_b[tid], s_c[tid]);
+                const SplatView r = decode_record(rec[sid], O.ln_alpha_min);
+                stage_record<Rec>(r, s_a[tid], s_b[tid], s_c[tid]);
+                s_m[tid] = TP::sub_masks(r.u, r.v, r.hx, r.hy, fx0, fy0);
                 if constexpr (kAux) s_x[tid] = aux_rec[sid];
             } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
-                s_a[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_b[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-                s_c[tid] = make_float4(0.f, -1.f, -1.f, 0.f);
-                if constexpr (kAux) s_x[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_m[tid] = 0u;
             }
         }
         __syncthreads();
         const int cnt = (int)min((uint32_t)B, range.y - base);
-        for (int j = 0; j < cnt && !done; j++) {
-            const float4 a = s_a[j];
-            const float4 c = s_c[j];
-            if (!box_meets_region<TP::RW, TP::RH>(a.x, a.y, c.y, c.z, frx, fry)) continue;  // warp-uniform
-            const unsigned sub = TP::sub_mask(a.x, a.y, c.y, c.z, frx, fry);            // warp-uniform
-            const float4 b = s_b[j];
-            const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
+        // The warp walks the batch 32 slots at a time; a ballot picks the
+        // slots whose splat reaches one of its sub-regions, visited in order.
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            if (__all_sync(F, done)) break;
+            const int jl = c0 + lane;
+            const uint32_t nib = jl < cnt ? (s_m[jl] >> wshift) & (uint32_t)TP::kSubAll : 0u;
+            uint32_t hits = __ballot_sync(F, nib != 0u);
+            while (hits) {
+                const int l = __ffs(hits) - 1;
+                hits &= hits - 1u;
+                const unsigned sub = __shfl_sync(F, nib, l);
+                const int j = c0 + l;
+                const float4 a = s_a[j];
+                const float4 b = s_b[j];
+                const float4 c = s_c[j];
+                const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
 #pragma unroll
-            for (int k = 0; k < P; k++) {
-                if (!(sub >> k & 1u)) continue;
-                if (pdone[k]) continue;
-                const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
-                if (kStats) {
-                    st_eval++;
-                    st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
+                for (int k = 0; k < P; k++) {
+                    if (!(sub >> k & 1u)) continue;
+                    if (pdone[k]) continue;
+                    const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
+                    if (kStats) {
+                        st_eval++;
+                        st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
+                    }
+                    const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
+                    if (!(p2 <= 0.0f)) continue;
+                    const float araw = __fmul_rn(b.y, ex2_approx(p2));
+                    const float alpha = fminf(O.alpha_max, araw);
+                    if (alpha < O.alpha_min) continue;
+                    const float Tn = T[k] * (1.0f - alpha);
+                    if (Tn < O.T_min) {
+                        pdone[k] = true;
+                        continue;
+                    }
+                    if (kStats) st_blend++;
+                    const float w = alpha * T[k];
+                    if constexpr (kAux) {
+                        const float4 x = s_x[j];
+                        C0[k] = fmaf(x.x, w, C0[k]);
+                        C1[k] = fmaf(x.y, w, C1[k]);
+                        C2[k] = fmaf(x.z, w, C2[k]);
+                    } else {
+                        C0[k] = fmaf(b.z, w, C0[k]);
+                        C1[k] = fmaf(b.w, w, C1[k]);
+                        C2[k] = fmaf(c.x, w, C2[k]);
+                    }
+                    T[k] = Tn;
+                    last[k] = pos1;
                 }
-                const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
-                if (!(p2 <= 0.0f)) continue;
-                const float araw = __fmul_rn(b.y, ex2_approx(p2));
-                const float alpha = fminf(O.alpha_max, araw);
-                if (alpha < O.alpha_min) continue;
-                const float Tn = T[k] * (1.0f - alpha);
-                if (Tn < O.T_min) {
-                    pdone[k] = true;
-                    continue;
-                }
-                if (kStats) st_blend++;
-                const float w = alpha * T[k];
-                if constexpr (kAux) {
-                    const float4 x = s_x[j];
-                    C0[k] = fmaf(x.x, w, C0[k]);
-                    C1[k] = fmaf(x.y, w, C1[k]);
-                    C2[k] = fmaf(x.z, w, C2[k]);
-                } else {
-                    C0[k] = fmaf(b.z, w, C0[k]);
-                    C1[k] = fmaf(b.w, w, C1[k]);
-                    C2[k] = fmaf(c.x, w, C2[k]);
-                }
-                T[k] = Tn;
-                last[k] = pos1;
-            }
-            if (P > 1) {
                 bool all = true;
 #pragma unroll
                 for (int k = 0; k < P; k++) all = all && pdone[k];
                 done = all;
-            } else {
-                done = pdone[0];
+                if (__all_sync(F, done)) hits = 0u;
             }
         }
     }
@@ -328,21 +347,20 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     constexpr int P = TP::P;
     __shared__ float4 s_a[kTilePix];
     __shared__ float4 s_b[kTilePix];
-    __shared__ float4 s_n[kTilePix];  // natural conic (a, b, c), for the flush
-    __shared__ float4 s_r[kTilePix];  // support box half extents hx, hy, and B
+    __shared__ float4 s_n[kTilePix];    // natural conic (a, b, c) for the flush, and the colour's B
+    __shared__ uint32_t s_m[kTilePix];  // sub-region mask of each staged splat
     __shared__ uint32_t s_sid[kTilePix];
     __shared__ __align__(16) float s_g[kTilePix * kGradStride];
     __shared__ int s_max;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x, lane = tid & 31, wshift = (tid >> 5) * P;
+    const unsigned F = 0xffffffffu;
     const uint32_t tile = blockIdx.x;
     const int v = find_view(VS, tile);
     const DevView& V = VS.v[v];
     const uint32_t local = tile - V.tile_base;
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
-    int irx, iry;
-    TP::region(tid, tx * TS, ty * TS, irx, iry);
-    const float frx = (float)irx, fry = (float)iry;
+    const float fx0 = (float)(tx * TS), fy0 = (float)(ty * TS);
     const size_t npix = (size_t)V.width * V.height;
     const float* gimg = dL_dimage + 3 * (size_t)V.pix_base;
     // Per pixel: T (recovered back to front), dL/dC, and S = dL/dC . acc where
@@ -392,63 +410,73 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
             const SplatView r = decode_record(rec[sid], O.ln_alpha_min);
             float4 sc;
             stage_record<Rec>(r, s_a[tid], s_b[tid], sc);
-            s_n[tid] = make_float4(r.a, r.b, r.c, 0.0f);
-            s_r[tid] = make_float4(sc.y, sc.z, sc.x, 0.0f);
+            s_n[tid] = make_float4(r.a, r.b, r.c, sc.x);
+            s_m[tid] = TP::sub_masks(r.u, r.v, r.hx, r.hy, fx0, fy0);
             s_sid[tid] = sid;
         }
         __syncthreads();
-        for (int j = 0; j < cnt; j++) {
-            const int pos = end - 1 - j;  // 0-based position in the tile list
-            if (pos >= warp_last) continue;  // warp-uniform
-            const float4 a = s_a[j];
-            const float4 hb = s_r[j];
-            if (!box_meets_region<TP::RW, TP::RH>(a.x, a.y, hb.x, hb.y, frx, fry)) continue;  // warp-uniform
-            const unsigned sub = TP::sub_mask(a.x, a.y, hb.x, hb.y, frx, fry);             // warp-uniform
-            // sums over the warp's pixels, with g = dL/dpower:
-            //   g dx, g dy, g dx^2, g dx dy, g dy^2, dL/dalpha_eff, dL/dR, dL/dG (and dL/dB);
-            // the flush turns the first five into dL/d(u, v, a, b, c) with the splat's conic
-            float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float g_bl = 0.0f;
-            bool contrib = false;
-            const float4 b = s_b[j];
+        // The warp walks the batch 32 slots at a time (back to front); a
+        // ballot picks the slots whose splat reaches one of its sub-regions
+        // and lies in front of the warp's last blended position.
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            const int jl = c0 + lane;
+            const uint32_t nib =
+                (jl < cnt && end - 1 - jl < warp_last) ? (s_m[jl] >> wshift) & (uint32_t)TP::kSubAll : 0u;
+            uint32_t hits = __ballot_sync(F, nib != 0u);
+            while (hits) {
+                const int l = __ffs(hits) - 1;
+                hits &= hits - 1u;
+                const unsigned sub = __shfl_sync(F, nib, l);
+                const int j = c0 + l;
+                const int pos = end - 1 - j;  // 0-based position in the tile list
+                const float4 a = s_a[j];
+                const float4 b = s_b[j];
+                const float cB = s_n[j].w;
+                // sums over the warp's pixels, with g = dL/dpower:
+                //   g dx, g dy, g dx^2, g dx dy, g dy^2, dL/dalpha_eff, dL/dR, dL/dG (and dL/dB);
+                // the flush turns the first five into dL/d(u, v, a, b, c) with the splat's conic
+                float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float g_bl = 0.0f;
+                bool contrib = false;
 #pragma unroll
-            for (int k = 0; k < P; k++) {
-                if (!(sub >> k & 1u)) continue;
-                if (pos >= last[k]) continue;
-                const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
-                const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
-                if (!(p2 <= 0.0f)) continue;
-                const float G = ex2_approx(p2);
-                const float araw = __fmul_rn(b.y, G);
-                const float alpha = fminf(O.alpha_max, araw);
-                if (alpha < O.alpha_min) continue;
-                contrib = true;
-                const float inv_om = rcp_approx(1.0f - alpha);
-                const float Ti = T[k] * inv_om;  // transmittance before this splat
-                const float dCc = fmaf(dC0[k], b.z, fmaf(dC1[k], b.w, dC2[k] * hb.z));
-                const float dalpha = fmaf(Ti, dCc, -Sacc[k] * inv_om);
-                const float w = alpha * Ti;
-                gv[6] = fmaf(dC0[k], w, gv[6]);
-                gv[7] = fmaf(dC1[k], w, gv[7]);
-                g_bl = fmaf(dC2[k], w, g_bl);
-                Sacc[k] = fmaf(w, dCc, Sacc[k]);
-                T[k] = Ti;
-                if (!(araw > O.alpha_max)) {
-                    gv[5] = fmaf(dalpha, G, gv[5]);
-                    const float dpow = dalpha * araw;
-                    const float hx = dpow * dx, hy = dpow * dy;
-                    gv[0] += hx;
-                    gv[1] += hy;
-                    gv[2] = fmaf(hx, dx, gv[2]);
-                    gv[3] = fmaf(hx, dy, gv[3]);
-                    gv[4] = fmaf(hy, dy, gv[4]);
+                for (int k = 0; k < P; k++) {
+                    if (!(sub >> k & 1u)) continue;
+                    if (pos >= last[k]) continue;
+                    const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
+                    const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
+                    if (!(p2 <= 0.0f)) continue;
+                    const float G = ex2_approx(p2);
+                    const float araw = __fmul_rn(b.y, G);
+                    const float alpha = fminf(O.alpha_max, araw);
+                    if (alpha < O.alpha_min) continue;
+                    contrib = true;
+                    const float inv_om = rcp_approx(1.0f - alpha);
+                    const float Ti = T[k] * inv_om;  // transmittance before this splat
+                    const float dCc = fmaf(dC0[k], b.z, fmaf(dC1[k], b.w, dC2[k] * cB));
+                    const float dalpha = fmaf(Ti, dCc, -Sacc[k] * inv_om);
+                    const float w = alpha * Ti;
+                    gv[6] = fmaf(dC0[k], w, gv[6]);
+                    gv[7] = fmaf(dC1[k], w, gv[7]);
+                    g_bl = fmaf(dC2[k], w, g_bl);
+                    Sacc[k] = fmaf(w, dCc, Sacc[k]);
+                    T[k] = Ti;
+                    if (!(araw > O.alpha_max)) {
+                        gv[5] = fmaf(dalpha, G, gv[5]);
+                        const float dpow = dalpha * araw;
+                        const float hx = dpow * dx, hy = dpow * dy;
+                        gv[0] += hx;
+                        gv[1] += hy;
+                        gv[2] = fmaf(hx, dx, gv[2]);
+                        gv[3] = fmaf(hx, dy, gv[3]);
+                        gv[4] = fmaf(hy, dy, gv[4]);
+                    }
                 }
-            }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_reduce8(gv, lane);
-                if ((lane & 3) == 0) atomicAdd(&s_g[j * kGradStride + (lane >> 2)], tot);
-                const float tb = warp_sum(g_bl);
-                if (lane == 0) atomicAdd(&s_g[j * kGradStride + 8], tb);
+                if (__any_sync(F, contrib)) {
+                    const float tot = warp_reduce8(gv, lane);
+                    if ((lane & 3) == 0) atomicAdd(&s_g[j * kGradStride + (lane >> 2)], tot);
+                    const float tb = warp_sum(g_bl);
+                    if (lane == 0) atomicAdd(&s_g[j * kGradStride + 8], tb);
+                }
             }
         }
         __syncthreads();
