@@ -152,7 +152,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(uint32_t x) {
 // kMode 2: the same walk compositing each splat's aux record (depth, flow u,
 // flow v) instead of its colour, background 0, into aux_image only.
 template <int TS, class Rec, int kMode>
-__global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
+__global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_constant__ ViewSet VS, const DevOpts O,
                                                               const uint2* __restrict__ ranges,
                                                               const uint32_t* __restrict__ pair_vals,
                                                               const Rec* __restrict__ rec, uint32_t n_splats,
@@ -178,27 +178,27 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
     const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
     const float fx0 = (float)(tx * TS), fy0 = (float)(ty * TS);
-    float fpx[P], fpy[P], T[P], C0[P], C1[P], C2[P];
+    float T[P], C0[P], C1[P], C2[P];
     int32_t last[P];
-    bool pdone[P], inside[P];
-    bool done = true;
+    // bit k of `inside`: pixel k lies in the image; of `live`: it has not stopped
+    uint32_t inside = 0;
     uint32_t st_box = 0, st_blend = 0, st_eval = 0;
+    int bpx, bpy;  // pixel 0 of this thread; pixel k lies at a constant offset
+    TP::coords(tid, tx * TS, ty * TS, 0, bpx, bpy);
+    const float fbx = (float)bpx, fby = (float)bpy;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         int px, py;
         TP::coords(tid, tx * TS, ty * TS, k, px, py);
-        inside[k] = px < V.width && py < V.height;
-        fpx[k] = (float)px;
-        fpy[k] = (float)py;
+        if (px < V.width && py < V.height) inside |= 1u << k;
         T[k] = 1.0f;
         C0[k] = C1[k] = C2[k] = 0.0f;
         last[k] = 0;
-        pdone[k] = !inside[k];
-        done = done && pdone[k];
     }
+    uint32_t live = inside;
     const int B = O.batch;  // records per batch, <= kTilePix
     for (uint32_t base = range.x; base < range.y; base += (uint32_t)B) {
-        if (__syncthreads_count(done) == kTilePix) break;
+        if (__syncthreads_count(live == 0u) == kTilePix) break;
         const uint32_t idx = base + tid;
         if (tid < B && idx < range.y) {
             const uint32_t sid = pair_vals[idx];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
         // The warp walks the batch 32 slots at a time; a ballot picks the
         // slots whose splat reaches one of its sub-regions, visited in order.
         for (int c0 = 0; c0 < cnt; c0 += 32) {
-            if (__all_sync(F, done)) break;
+            if (__all_sync(F, live == 0u)) break;
             const int jl = c0 + lane;
             const uint32_t nib = jl < cnt ? (s_m[jl] >> wshift) & (uint32_t)TP::kSubAll : 0u;
             uint32_t hits = __ballot_sync(F, nib != 0u);
@@ -229,11 +229,11 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                 const float4 b = s_b[j];
                 const float4 c = s_c[j];
                 const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
+                const uint32_t act = sub & live;
 #pragma unroll
                 for (int k = 0; k < P; k++) {
-                    if (!(sub >> k & 1u)) continue;
-                    if (pdone[k]) continue;
-                    const float dx = __fsub_rn(fpx[k], a.x), dy = __fsub_rn(fpy[k], a.y);
+                    if (!(act >> k & 1u)) continue;
+                    const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                     if (kStats) {
                         st_eval++;
                         st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                     if (alpha < O.alpha_min) continue;
                     const float Tn = T[k] * (1.0f - alpha);
                     if (Tn < O.T_min) {
-                        pdone[k] = true;
+                        live &= ~(1u << k);
                         continue;
                     }
                     if (kStats) st_blend++;
@@ -263,19 +263,16 @@ __global__ void __launch_bounds__(kTilePix) render_fwd_kernel(const __grid_const
                     T[k] = Tn;
                     last[k] = pos1;
                 }
-                bool all = true;
-#pragma unroll
-                for (int k = 0; k < P; k++) all = all && pdone[k];
-                done = all;
-                if (__all_sync(F, done)) hits = 0u;
+                // a pixel stopped: the warp is done once all of its pixels have
+                if (__any_sync(F, act & ~live) && __all_sync(F, live == 0u)) hits = 0u;
             }
         }
     }
     const size_t npix = (size_t)V.width * V.height;
 #pragma unroll
     for (int k = 0; k < P; k++) {
-        if (!inside[k]) continue;
-        const size_t p = (size_t)fpy[k] * V.width + (size_t)fpx[k];
+        if (!(inside >> k & 1u)) continue;
+        const size_t p = (size_t)(bpy + (int)TP::off_y(k)) * V.width + (size_t)(bpx + (int)TP::off_x(k));
         if constexpr (kAux) {
             float* ax = aux_image + 3 * (size_t)V.pix_base;
             ax[p] = C0[k];
