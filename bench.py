@@ -60,7 +60,9 @@ def parse():
                     help="mixed: BF16 4DSH coefficients + 16-bit conic records; fp32: plain FP32 storage")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly, not as a CUDA graph")
     ap.add_argument("--tile", default="auto", choices=["auto", "16", "32"],
-                    help="screen tile side; auto: the autotuner times both on this workload")
+                    help="compositing tile side; auto: the autotuner times both on this workload")
+    ap.add_argument("--bin-size", default="auto", choices=["auto", "16", "32", "64"],
+                    help="binning tile side (a multiple of the compositing tile); auto: picked with the tile size")
     ap.add_argument("--batch-depth", default="auto", choices=["auto", "32", "64", "128", "256"],
                     help="splat records staged per shared-memory batch; auto: picked with the tile size")
     return ap.parse_args()
@@ -120,6 +122,8 @@ class ClockSampler:
 KERNEL_SOURCES = ("paper_2310_10642_gb300/csrc/render.cu", "paper_2310_10642_gb300/csrc/fgs4d_internal.cuh")
 STAGE_PROFILE = {"render_backward_2d": "render_bwd_kernel_1M_2views_1352x1014.md",
                  "render": "render_fwd_kernel_1M_2views_1352x1014.md"}
+# launch shape of those captures: their traffic applies to runs with this shape only
+PROFILED_SHAPE = dict(tile_size=32, bin_size=64, batch_depth=256)
 
 
 def profiled_traffic(stage: str):
@@ -250,7 +254,8 @@ def main_train(args):
     mixed = args.precision == "mixed"
     tile = 32 if args.tile == "auto" else int(args.tile)
     depth = 256 if args.batch_depth == "auto" else int(args.batch_depth)
-    opts = dict(c["options"], tile_size=tile, batch_depth=depth)
+    binsz = max(tile, 64) if args.bin_size == "auto" else int(args.bin_size)
+    opts = dict(c["options"], tile_size=tile, bin_size=binsz, batch_depth=depth)
     tg_host = torch.cat([torch.as_tensor(t).reshape(-1) for t in I.random_target(views, 44)]).pin_memory()
     tg = tg_host.cuda()
     p = R.params_to_device(G)
@@ -343,7 +348,7 @@ def main_train(args):
                    n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4),
                    steps_per_s=round(1e3 * args.steps / total_ms, 3), higher_is_better=True, scaling="weak",
                    vs_baseline=None, dtype="f32", data="synthetic",
-                   config=dict(TRAIN_WORKLOAD, n=n, n_views=len(views), tile=tile, batch_depth=depth,
+                   config=dict(TRAIN_WORKLOAD, n=n, n_views=len(views), tile=tile, bin=binsz, batch_depth=depth,
                                precision="BF16 4DSH copy + 16-bit conic records, FP32 master weights" if mixed
                                else "FP32", cuda_graph=True, pixels_per_step=npix,
                                l2="inputs larger than L2 (1.9 GB FP32 parameters + Adam state)",
@@ -387,11 +392,15 @@ def main():
     opts = dict(opts, record_fp16=int(mixed))
     tiles = A.TILE_SIZES if args.tile == "auto" else (int(args.tile),)
     depths = A.BATCH_DEPTHS if args.batch_depth == "auto" else (int(args.batch_depth),)
+    cands = [c for c in A.candidates(tiles, depths)
+             if args.bin_size == "auto" or c["bin_size"] == int(args.bin_size)]
+    if not cands:
+        raise SystemExit("--bin-size must be a multiple of the tile size")
     tune_table = None
-    if len(tiles) * len(depths) > 1:  # launch shape from the autotuner, timed on this workload (untimed here)
-        opts, tune_table = A.tune(p, views, opts, cands=A.candidates(tiles, depths), cache=None)
+    if len(cands) > 1:  # launch shape from the autotuner, timed on this workload (untimed here)
+        opts, tune_table = A.tune(p, views, opts, cands=cands, cache=None)
     else:
-        opts = dict(opts, tile_size=tiles[0], batch_depth=depths[0])
+        opts = dict(opts, **cands[0])
     opts_fp32 = dict(opts, record_fp16=0)
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda").manual_seed(1234)
@@ -544,7 +553,7 @@ def main():
                                        frac=round(a_ / hbm, 4))
     dom = max(stage_ms, key=stage_ms.get)
     full_workload = (args.n is None and args.views is None and args.scale == 1.0 and mixed
-                     and opts["tile_size"] == 32 and opts["batch_depth"] == 256)
+                     and all(opts[k] == v for k, v in PROFILED_SHAPE.items()))
     traffic, traffic_note = profiled_traffic(dom) if full_workload else (None, "not the profiled workload")
     kernel_of = {"render_backward_2d": "render_bwd_kernel (stage: 2D-gradient memset + kernel)",
                  "render": "render_fwd_kernel", "project_backward": "project_backward_kernel + sh_backward_kernel",
@@ -617,7 +626,8 @@ def main():
                    unit="Mpix/s", n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(ms_step, 4),
                    higher_is_better=True, scaling="weak", vs_baseline=None,
                    dtype="f32", data="synthetic",
-                   config=dict(WORKLOAD, n=n, views=V, tile=opts["tile_size"], batch_depth=opts["batch_depth"],
+                   config=dict(WORKLOAD, n=n, views=V, tile=opts["tile_size"], bin=opts["bin_size"],
+                               batch_depth=opts["batch_depth"],
                                autotune=tune_table, precision=(
                        "BF16 4DSH coefficients, 16-bit Cholesky conics; FP32 arithmetic" if mixed else "FP32"),
                        cuda_graph=graph is not None,

@@ -48,11 +48,11 @@
 extern "C" {
 #endif
 
-#define FGS4D_ABI_VERSION 2
+#define FGS4D_ABI_VERSION 3
 #define FGS4D_MAX_VIEWS 128   /* views per call */
 #define FGS4D_MAX_SH_DEGREE 3 /* L */
 #define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
-#define FGS4D_TILE 16         /* default screen tile: 16 x 16 pixels (32 x 32 selectable) */
+#define FGS4D_TILE 16         /* default compositing tile: 16 x 16 pixels (32 x 32 selectable) */
 
 typedef struct CUstream_st *fgs4d_stream; /* identical to cudaStream_t */
 
@@ -129,14 +129,21 @@ typedef struct {
     int record_fp16;  /* 0: FP32 splat records; 1: FP16 conic (mixed precision) */
     float schur_cond; /* 1e-3: FP64 Schur complement when min_i Sigma3_ii/Sigma_ii is below */
     float conic_cond; /* 1e-4: FP64 2x2 inversion when det/(S00*S11) is below */
-    int tile_size;    /* 16 or 32: side of the square screen tiles (binning and compositing);
-                         32 bins each splat to ~3x fewer tiles, each thread composites 2x2 pixels */
+    int tile_size;    /* 16 or 32: side of the square compositing tiles (one thread block each);
+                         with 32 each thread composites 2x2 pixels */
     int batch_depth;  /* 256: splat records a tile stages in shared memory per batch while
                          compositing (32, 64, 128 or 256); results do not depend on it */
     int aux_channels; /* 0; 1: fgs4d_slice_project also stores, per splat, its camera depth and
                          the displacement of its projected mean from t to t + flow_dt, for
                          fgs4d_render_aux (the state grows by 16 bytes per splat) */
     float flow_dt;    /* 1/300: time step of the optical-flow channels (one frame of 300) */
+    int bin_size;     /* 0: tile_size; else 16, 32 or 64 and a multiple of tile_size: side of the
+                         binning tiles, the screen cells whose depth-ordered splat lists
+                         fgs4d_bin_sort builds; each list serves the (bin_size/tile_size)^2
+                         compositing tiles inside its cell.  Larger cells make fewer (splat,
+                         tile) pairs to sort when splats span several compositing tiles;
+                         results do not depend on it.  "Tile" in the counters, the state
+                         layout and fgs4d_bin_sort means a binning tile. */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but
@@ -192,8 +199,9 @@ int64_t fgs4d_total_pixels(const fgs4d_view *views, int n_views);
 fgs4d_status fgs4d_slice_project(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
                                  const fgs4d_options *opt, void *state, size_t state_bytes, fgs4d_stream stream);
 
-/* Bin the splats to 16x16 tiles and order each tile's list by (depth,
-   Gaussian index) with the library's on-device radix sort (Sec. 3.1/3.2).
+/* Bin the splats to the binning tiles (bin_size x bin_size pixels) their
+   support ellipse reaches and order each tile's list by (depth, Gaussian
+   index) with the library's on-device radix sort (Sec. 3.1/3.2).
    Pairs beyond the capacity are dropped and FGS4D_STATUS_PAIR_OVERFLOW is set. */
 fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
                             size_t state_bytes, fgs4d_stream stream);

@@ -1,12 +1,13 @@
-"""Picks the screen-tile size and the per-tile batch depth of a frame by timing.
+"""Picks the tile sizes and the per-tile batch depth of a frame by timing.
 
-The compositing kernels have two launch-shape knobs that change speed but not
-results: ``tile_size`` (16 or 32, the side of the square screen tiles that
-binning and compositing share) and ``batch_depth`` (how many splat records a
-tile stages in shared memory per batch).  Which pair is fastest depends on
-the splat-size distribution and the image sizes, so ``tune`` renders the
-caller's own frame (forward + backward) with every candidate, times it with
-CUDA events, and returns the fastest.  Results are cached in a JSON file keyed
+Three launch-shape knobs change speed but not results: ``tile_size`` (16 or
+32, the side of the square compositing tiles, one thread block each),
+``bin_size`` (16, 32 or 64, a multiple of ``tile_size``: the side of the
+binning tiles whose depth-ordered lists the sort builds) and ``batch_depth``
+(how many splat records a block stages in shared memory per batch).  Which
+combination is fastest depends on the splat-size distribution and the image
+sizes, so ``tune`` renders the caller's own frame (forward + backward) with
+every candidate, times it with CUDA events, and returns the fastest.  Results are cached in a JSON file keyed
 by the device and the shape of the workload, so a training loop tunes once.
 
 Cache file: ``$FGS4D_AUTOTUNE_CACHE`` if set, else
@@ -20,8 +21,10 @@ import statistics
 from typing import Callable
 
 TILE_SIZES = (16, 32)
+BIN_FACTORS = (1, 2, 4)  # binning tile side / compositing tile side
+MAX_BIN = 64
 BATCH_DEPTHS = (64, 128, 256)
-KNOBS = ("tile_size", "batch_depth")
+KNOBS = ("tile_size", "bin_size", "batch_depth")
 
 
 def default_cache_path() -> str:
@@ -29,8 +32,9 @@ def default_cache_path() -> str:
                           os.path.join(os.path.expanduser("~"), ".cache", "fgs4d", "autotune.json"))
 
 
-def candidates(tiles=TILE_SIZES, depths=BATCH_DEPTHS) -> list:
-    return [dict(tile_size=t, batch_depth=b) for t in tiles for b in depths]
+def candidates(tiles=TILE_SIZES, depths=BATCH_DEPTHS, factors=BIN_FACTORS) -> list:
+    return [dict(tile_size=t, bin_size=t * f, batch_depth=b) for t in tiles for f in factors if t * f <= MAX_BIN
+            for b in depths]
 
 
 def workload_key(device_name: str, n: int, views: list, sh_degree: int, n_freq: int, record_fp16: int,
@@ -93,7 +97,7 @@ def tune_with(timer: Callable[[dict], float], cands: list, key: str, cache: str 
 
 def tune(params: dict, views: list, options: dict | None = None, cands: list | None = None, reps: int = 3,
          warmup: int = 2, cache: str | None = "default") -> tuple:
-    """Fastest (tile_size, batch_depth) for rendering ``params`` into ``views``
+    """Fastest (tile_size, bin_size, batch_depth) for rendering ``params`` into ``views``
     forward and backward.  Returns (options with the choice filled in, table
     of candidate timings in ms per forward+backward).  Runs the frame
     ``(warmup + reps) x len(cands)`` times."""

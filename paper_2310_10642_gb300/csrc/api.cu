@@ -37,6 +37,9 @@ fgs4d_status check_options(const fgs4d_options* o) {
     if (!(o->near_z > 0.0f) || o->p_min > 1.0f || o->T_min >= 1.0f) return FGS4D_ERR_INVALID_ARG;
     if (o->record_fp16 != 0 && o->record_fp16 != 1) return FGS4D_ERR_INVALID_ARG;
     if (o->tile_size != 16 && o->tile_size != 32) return FGS4D_ERR_INVALID_ARG;
+    if (o->bin_size != 0 && ((o->bin_size != 16 && o->bin_size != 32 && o->bin_size != 64) ||
+                             o->bin_size % o->tile_size != 0))
+        return FGS4D_ERR_INVALID_ARG;
     if (o->batch_depth != 32 && o->batch_depth != 64 && o->batch_depth != 128 && o->batch_depth != 256)
         return FGS4D_ERR_INVALID_ARG;
     if (o->aux_channels != 0 && o->aux_channels != 1) return FGS4D_ERR_INVALID_ARG;
@@ -57,6 +60,7 @@ DevOpts dev_options(const fgs4d_options* o) {
     d.ln_alpha_min = logf(o->alpha_min);
     d.record_fp16 = o->record_fp16;
     d.tile = o->tile_size;
+    d.bin = o->bin_size ? o->bin_size : o->tile_size;
     d.batch = o->batch_depth;
     d.aux = o->aux_channels;
     d.flow_dt = o->flow_dt;
@@ -102,8 +106,9 @@ fgs4d_status make_views(const fgs4d_view* views, int n_views, const fgs4d_option
         }
         d.width = h.width;
         d.height = h.height;
-        d.tiles_x = (h.width + o->tile_size - 1) / o->tile_size;
-        d.tiles_y = (h.height + o->tile_size - 1) / o->tile_size;
+        const int bin = o->bin_size ? o->bin_size : o->tile_size;
+        d.tiles_x = (h.width + bin - 1) / bin;
+        d.tiles_y = (h.height + bin - 1) / bin;
         d.tile_base = (uint32_t)tiles;
         d.pix_base = (uint32_t)pix;
         tiles += (uint64_t)d.tiles_x * d.tiles_y;
@@ -262,6 +267,7 @@ void fgs4d_default_options(fgs4d_options* o) {
     o->batch_depth = 256;
     o->aux_channels = 0;
     o->flow_dt = 1.0f / 300.0f;
+    o->bin_size = 0;
 }
 
 int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {

@@ -605,7 +605,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     // 3. exact tile counts (support ellipse), then pair offsets in depth order -> counters[1]
     const int stride_grid = 16 * sm_count;
     ellipse_count_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(
-        VS, (uint32_t)(S / (uint32_t)VS.n), sorted, rec, O.record_fp16, O.ln_alpha_min, S, counters, O.tile, tiles);
+        VS, (uint32_t)(S / (uint32_t)VS.n), sorted, rec, O.record_fp16, O.ln_alpha_min, S, counters, O.bin, tiles);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = device_scan(LoadTilesSorted{tiles, sorted}, StoreOffset{offsets}, &counters[0], S, scan_tmp, &counters[1], Gs,
@@ -613,7 +613,7 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     if (e != cudaSuccess) return e;
     // 4. emission
     emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, O.record_fp16, O.ln_alpha_min, S,
-                                                       counters, cap, O.tile, pk[0], pv[0]);
+                                                       counters, cap, O.bin, pk[0], pv[0]);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;

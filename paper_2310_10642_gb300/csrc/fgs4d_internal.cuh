@@ -28,8 +28,8 @@ struct DevView {
     float limx, limy;  // clamp of x/z, y/z inside the Jacobian (huge when off)
     float t;
     float bg[3];
-    int width, height, tiles_x, tiles_y;
-    uint32_t tile_base;  // first global tile id of this view
+    int width, height, tiles_x, tiles_y;  // binning tiles across and down
+    uint32_t tile_base;  // first global binning tile id of this view
     uint32_t pix_base;   // first pixel (offset into final_T / n_last)
 };
 
@@ -44,7 +44,8 @@ struct DevOpts {
     float schur_cond, conic_cond;
     float ln_alpha_min;
     int record_fp16;
-    int tile;   // screen tile side: 16 or 32
+    int tile;   // compositing tile side: 16 or 32 (one thread block)
+    int bin;    // binning tile side: 16, 32 or 64, a multiple of tile
     int batch;  // records staged per shared-memory batch while compositing: 32..256
     int aux;    // store per-splat depth and flow (fgs4d_render_aux)
     float flow_dt;
@@ -541,22 +542,32 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// Tiles [*tx0, *tx0 + count) of tile row ty reached by the ellipse, within
-// the box rect (x0, y0, x1, y1).  tile is 16 or 32.
-__device__ __forceinline__ int ellipse_row_tiles(const EllipseRows& e, const DevView& V, int tile, const int* rect,
-                                                 int ty, int* tx0) {
-    *tx0 = rect[0];
-    if (!e.exact) return rect[2] - rect[0] + 1;
-    const int sh = tile == 32 ? 5 : 4;
-    const float row_lo = (float)(ty << sh), row_hi = (float)min((ty << sh) + tile - 1, V.height - 1);
+// Pixel columns [*px0, *px1] reached by the ellipse over the pixel rows
+// row_lo..row_hi (integers, within the image), clamped to the image; false
+// when it reaches none of them.  Needs e.exact.
+__device__ __forceinline__ bool ellipse_row_span(const EllipseRows& e, const DevView& V, float row_lo, float row_hi,
+                                                 float* px0, float* px1) {
     const float lo = fmaxf(row_lo - 0.5f - e.v, -e.rys), hi = fminf(row_hi + 0.5f - e.v, e.rys);
-    if (!(lo <= hi)) return 0;
+    if (!(lo <= hi)) return false;
     const float yl = fminf(fmaxf(e.dyl, lo), hi), yr = fminf(fmaxf(-e.dyl, lo), hi);
     const float ql = yl * e.irys, qr = yr * e.irys;
     const float xl = -e.ba * yl - sqrt_approx(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
     const float xr = -e.ba * yr + sqrt_approx(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
-    const float px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f), px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
-    if (!(px0 <= px1)) return 0;
+    *px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f);
+    *px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
+    return *px0 <= *px1;
+}
+
+// Tiles [*tx0, *tx0 + count) of tile row ty reached by the ellipse, within
+// the box rect (x0, y0, x1, y1).  tile is 16, 32 or 64.
+__device__ __forceinline__ int ellipse_row_tiles(const EllipseRows& e, const DevView& V, int tile, const int* rect,
+                                                 int ty, int* tx0) {
+    *tx0 = rect[0];
+    if (!e.exact) return rect[2] - rect[0] + 1;
+    const int sh = __ffs(tile) - 1;
+    const float row_lo = (float)(ty << sh), row_hi = (float)min((ty << sh) + tile - 1, V.height - 1);
+    float px0, px1;
+    if (!ellipse_row_span(e, V, row_lo, row_hi, &px0, &px1)) return 0;
     const int t0 = max((int)px0 >> sh, rect[0]), t1 = min((int)px1 >> sh, rect[2]);
     *tx0 = t0;
     return max(t1 - t0 + 1, 0);
@@ -651,7 +662,7 @@ __device__ __forceinline__ bool project_view(const Core& c, const DevView& V, co
     const float k2 = 2.0f * fmaxf(logf(w.alpha_eff) - O.ln_alpha_min, 0.0f);
     w.hx = sqrtf(k2 * w.cov[0]) + 0.5f;
     w.hy = sqrtf(k2 * w.cov[2]) + 0.5f;
-    w.tiles = box_tiles(w.u, w.v, w.hx, w.hy, V, O.tile, w.rect);
+    w.tiles = box_tiles(w.u, w.v, w.hx, w.hy, V, O.bin, w.rect);
     return w.tiles > 0;
 }
 

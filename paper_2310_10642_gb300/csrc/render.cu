@@ -41,6 +41,26 @@ __device__ __forceinline__ int find_view(const ViewSet& VS, uint32_t tile) {
     return lo;
 }
 
+// Thread block b composites one TS x TS tile of the binning tile it walks
+// the list of: binning tiles of side O.bin hold (O.bin / TS)^2 compositing
+// tiles, whose blocks are consecutive (they share the list's records in
+// L2).  Sets the binning tile, the view and the pixel origin (x0, y0) of
+// the block's tile; false when that tile lies outside the view.
+template <int TS>
+__device__ __forceinline__ bool block_tile(const ViewSet& VS, const DevOpts& O, uint32_t& tile, int& v, int& x0,
+                                           int& y0) {
+    const int fsh = __ffs(O.bin / TS) - 1;  // log2 of compositing tiles per binning tile side
+    tile = blockIdx.x >> (2 * fsh);
+    const uint32_t q = blockIdx.x & ((1u << (2 * fsh)) - 1u);
+    v = find_view(VS, tile);
+    const DevView& V = VS.v[v];
+    const uint32_t local = tile - V.tile_base;
+    const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
+    x0 = tx * O.bin + (int)(q & ((1u << fsh) - 1u)) * TS;
+    y0 = ty * O.bin + (int)(q >> fsh) * TS;
+    return x0 < V.width && y0 < V.height;
+}
+
 // How a staged splat evaluates log2 of its Gaussian factor at (dx, dy) from
 // three staged coefficients (X, Y, Z).
 template <class Rec>
@@ -135,6 +155,39 @@ struct TilePixels {
             if (yb >= y0 + (float)(4 * r) && yt <= y0 + (float)(4 * r + 3)) m |= row << row_shift(r);
         return m;
     }
+    // The bits of `box` (sub_masks) whose sub-region the support ellipse
+    // reaches: per band of 4 pixel rows, the columns the ellipse spans over
+    // those rows (the conservative spans the binning takes per tile row,
+    // taken here per band), for the tile with corner pixel (x0, y0).
+    __device__ __forceinline__ static uint32_t ellipse_masks(uint32_t box, const EllipseRows& e, const DevView& V,
+                                                             int x0, int y0) {
+        uint32_t all = 0;
+#pragma unroll
+        for (int c = 0; c < NC; c++) all |= 1u << col_bit(c);
+        uint32_t m = 0;
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            if (!((box >> row_shift(r)) & all)) continue;  // the box misses the band (or the band the image)
+            const int ry = y0 + 4 * r;
+            float px0, px1;
+            if (!ellipse_row_span(e, V, (float)ry, (float)min(ry + 3, V.height - 1), &px0, &px1)) continue;
+            const int c0 = max(((int)px0 - x0) >> 3, 0), c1 = min(((int)px1 - x0) >> 3, NC - 1);
+            uint32_t row = 0;
+#pragma unroll
+            for (int c = 0; c < NC; c++)
+                if (c >= c0 && c <= c1) row |= 1u << col_bit(c);
+            m |= row << row_shift(r);
+        }
+        return box & m;
+    }
+    // Sub-region mask of a staged splat: box test, narrowed by the ellipse.
+    __device__ __forceinline__ static uint32_t splat_mask(const SplatView& r, float ln_alpha_min, const DevView& V,
+                                                          int x0, int y0) {
+        const uint32_t box = sub_masks(r.u, r.v, r.hx, r.hy, (float)x0, (float)y0);
+        if (!box) return 0u;
+        const EllipseRows e = ellipse_rows(r, ln_alpha_min);
+        return e.exact ? ellipse_masks(box, e, V, x0, y0) : box;
+    }
 };
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(uint32_t x) {
@@ -171,25 +224,23 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
     __shared__ uint32_t s_m[kTilePix];  // sub-region mask of each staged splat
     const int tid = threadIdx.x, lane = tid & 31, wshift = (tid >> 5) * P;
     const unsigned F = 0xffffffffu;
-    const uint32_t tile = blockIdx.x;
-    const int v = find_view(VS, tile);
+    uint32_t tile;
+    int v, x0, y0;
+    if (!block_tile<TS>(VS, O, tile, v, x0, y0)) return;  // the whole block lies outside the view
     const DevView& V = VS.v[v];
-    const uint32_t local = tile - V.tile_base;
-    const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
-    const float fx0 = (float)(tx * TS), fy0 = (float)(ty * TS);
     float T[P], C0[P], C1[P], C2[P];
     int32_t last[P];
     // bit k of `inside`: pixel k lies in the image; of `live`: it has not stopped
     uint32_t inside = 0;
     uint32_t st_box = 0, st_blend = 0, st_eval = 0;
     int bpx, bpy;  // pixel 0 of this thread; pixel k lies at a constant offset
-    TP::coords(tid, tx * TS, ty * TS, 0, bpx, bpy);
+    TP::coords(tid, x0, y0, 0, bpx, bpy);
     const float fbx = (float)bpx, fby = (float)bpy;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         int px, py;
-        TP::coords(tid, tx * TS, ty * TS, k, px, py);
+        TP::coords(tid, x0, y0, k, px, py);
         if (px < V.width && py < V.height) inside |= 1u << k;
         T[k] = 1.0f;
         C0[k] = C1[k] = C2[k] = 0.0f;
@@ -205,7 +256,7 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
             if (sid < n_splats) {
                 const SplatView r = decode_record(rec[sid], O.ln_alpha_min);
                 stage_record<Rec>(r, s_a[tid], s_b[tid], s_c[tid]);
-                s_m[tid] = TP::sub_masks(r.u, r.v, r.hx, r.hy, fx0, fy0);
+                s_m[tid] = TP::splat_mask(r, O.ln_alpha_min, V, x0, y0);
                 if constexpr (kAux) s_x[tid] = aux_rec[sid];
             } else {  // never produced by bin_sort; an empty splat keeps the access in bounds
                 s_m[tid] = 0u;
@@ -351,13 +402,11 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     __shared__ int s_max;
     const int tid = threadIdx.x, lane = tid & 31, wshift = (tid >> 5) * P;
     const unsigned F = 0xffffffffu;
-    const uint32_t tile = blockIdx.x;
-    const int v = find_view(VS, tile);
+    uint32_t tile;
+    int v, x0, y0;
+    if (!block_tile<TS>(VS, O, tile, v, x0, y0)) return;  // the whole block lies outside the view
     const DevView& V = VS.v[v];
-    const uint32_t local = tile - V.tile_base;
-    const int ty = (int)(local / (uint32_t)V.tiles_x), tx = (int)local - ty * V.tiles_x;
     const uint2 range = ranges[tile];
-    const float fx0 = (float)(tx * TS), fy0 = (float)(ty * TS);
     const size_t npix = (size_t)V.width * V.height;
     const float* gimg = dL_dimage + 3 * (size_t)V.pix_base;
     // Per pixel: T (recovered back to front), dL/dC, and S = dL/dC . acc where
@@ -367,12 +416,12 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     int32_t last[P];
     int my_max = 0;
     int bpx, bpy;  // pixel 0 of this thread; pixel k lies at a constant offset
-    TP::coords(tid, tx * TS, ty * TS, 0, bpx, bpy);
+    TP::coords(tid, x0, y0, 0, bpx, bpy);
     const float fbx = (float)bpx, fby = (float)bpy;
 #pragma unroll
     for (int k = 0; k < P; k++) {
         int px, py;
-        TP::coords(tid, tx * TS, ty * TS, k, px, py);
+        TP::coords(tid, x0, y0, k, px, py);
         T[k] = 1.0f;
         dC0[k] = dC1[k] = dC2[k] = 0.0f;
         last[k] = 0;
@@ -408,7 +457,7 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
             float4 sc;
             stage_record<Rec>(r, s_a[tid], s_b[tid], sc);
             s_n[tid] = make_float4(r.a, r.b, r.c, sc.x);
-            s_m[tid] = TP::sub_masks(r.u, r.v, r.hx, r.hy, fx0, fy0);
+            s_m[tid] = TP::splat_mask(r, O.ln_alpha_min, V, x0, y0);
             s_sid[tid] = sid;
         }
         __syncthreads();
@@ -501,6 +550,12 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     }
 }
 
+// One thread block per compositing tile: (O.bin / O.tile)^2 per binning tile.
+static uint32_t blocks_for(const ViewSet& VS, const DevOpts& O) {
+    const int f = O.bin / O.tile;
+    return VS.total_tiles * (uint32_t)(f * f);
+}
+
 template <int kMode>
 static cudaError_t launch_fwd_tiles(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state,
                                     int pair_buf, float* image, float* final_T, int32_t* n_last,
@@ -512,7 +567,7 @@ static cudaError_t launch_fwd_tiles(const ViewSet& VS, const DevOpts& O, const S
     const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
     const auto* rech = reinterpret_cast<const SplatRecordH*>(state + lay.records);
     const uint32_t S = (uint32_t)lay.n_splats;
-    const dim3 grid(VS.total_tiles);
+    const dim3 grid(blocks_for(VS, O));
     if (O.tile == 32 && O.record_fp16)
         render_fwd_kernel<32, SplatRecordH, kMode>
             <<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, image, final_T, n_last, stats, aux, aux_image);
@@ -553,7 +608,7 @@ static cudaError_t launch_bwd_tiles(const ViewSet& VS, const DevOpts& O, const S
     const auto* rec = reinterpret_cast<const SplatRecord*>(state + lay.records);
     const auto* rech = reinterpret_cast<const SplatRecordH*>(state + lay.records);
     const uint32_t S = (uint32_t)lay.n_splats;
-    const dim3 grid(VS.total_tiles);
+    const dim3 grid(blocks_for(VS, O));
     if (O.tile == 32 && O.record_fp16)
         render_bwd_kernel<32, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, final_T, n_last,
                                                                        dL_dimage, g2);

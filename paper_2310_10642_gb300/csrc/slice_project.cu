@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
             const SplatRecordH h = encode_record_h(w.u, w.v, w.conic, w.cov[2], w.alpha_eff, col);
             // the box of the stored (16-bit) conic, exactly as bin_sort will decode it
             const SplatView d = decode_record(h, O.ln_alpha_min);
-            w.tiles = box_tiles(d.u, d.v, d.hx, d.hy, V, O.tile, w.rect);
+            w.tiles = box_tiles(d.u, d.v, d.hx, d.hy, V, O.bin, w.rect);
             if (w.tiles == 0) {
                 tiles_touched[idx] = 0u;
                 continue;

@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.fgs4d_abi_version() == 2
+    assert lib.fgs4d_abi_version() == 3
     for code in range(6):
         assert len(lib.fgs4d_status_string(code)) > 0
 
@@ -55,7 +55,7 @@ def test_default_options_match_readings(lib):
     assert abs(o.p_min - 0.05) < 1e-7 and abs(o.near_z - 0.2) < 1e-7
     assert abs(o.alpha_min - 1 / 255) < 1e-9 and abs(o.alpha_max - 0.99) < 1e-7
     assert abs(o.T_min - 1e-4) < 1e-10 and abs(o.dilation - 0.3) < 1e-7
-    assert o.tile_size == 16 and o.batch_depth == 256 and o.record_fp16 == 0
+    assert o.tile_size == 16 and o.batch_depth == 256 and o.record_fp16 == 0 and o.bin_size == 0
 
 
 def _views(k=2, w=100, h=60):
@@ -71,6 +71,9 @@ def test_state_size_grows_with_capacity(lib):
     info = N.fgs4d_state_layout(1000, v, 2, o, b)
     assert 100000 <= info.pair_capacity < 100000 + 64 and info.n_splats == 2000
     assert info.total_tiles == 2 * 7 * 4
+    # binning tiles of 64 pixels: 2 x 1 per 100 x 60 view
+    o64 = N.make_options(dict(tile_size=32, bin_size=64))
+    assert N.fgs4d_state_layout(1000, v, 2, o64, N.fgs4d_state_size(1000, v, 2, 100, o64)).total_tiles == 2 * 2 * 1
     assert N.fgs4d_total_pixels(v, 2) == 2 * 6000
 
 
@@ -85,10 +88,14 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.fgs4d_state_size(10, v, 2, -5, ctypes.byref(o), ctypes.byref(size)) == 1
     # bad options
     for field, val in (("alpha_max", 1.5), ("alpha_min", 0.0), ("near_z", 0.0), ("T_min", float("nan")),
-                       ("tile_size", 8), ("batch_depth", 100), ("batch_depth", 512), ("record_fp16", 2)):
+                       ("tile_size", 8), ("batch_depth", 100), ("batch_depth", 512), ("record_fp16", 2),
+                       ("bin_size", 8), ("bin_size", 48), ("bin_size", 128), ("bin_size", -16)):
         bad = N.fgs4d_default_options()
         setattr(bad, field, val)
         assert lib.fgs4d_state_size(10, v, 2, 10, ctypes.byref(bad), ctypes.byref(size)) == 1
+    # a binning tile smaller than the compositing tile
+    bad = N.make_options(dict(tile_size=32, bin_size=16))
+    assert lib.fgs4d_state_size(10, v, 2, 10, ctypes.byref(bad), ctypes.byref(size)) == 1
     # bad view sizes
     bv = _views(1, 0, 10)
     assert lib.fgs4d_state_size(10, bv, 1, 10, ctypes.byref(o), ctypes.byref(size)) == 1

@@ -64,13 +64,15 @@ def assert_image_parity(img, Tg, ref, tol=IMG_TOL, max_flag_frac=0.05):
 
 # ---------------------------------------------------------------------------- forward
 TILES = pytest.mark.parametrize("tile", [16, 32])
+# (compositing tile, binning tile): every binning factor the library accepts
+TILE_BINS = pytest.mark.parametrize("tile,bin", [(16, 16), (16, 32), (16, 64), (32, 32), (32, 64)])
 
 
-@TILES
-def test_forward_config0_full_frame(tile):
+@TILE_BINS
+def test_forward_config0_full_frame(tile, bin):
     c = I.config(0)
     G, views = c["gaussians"], c["views"]
-    fr, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
+    fr, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
     ref = O.render(G, views[0])
     assert fr.last_counters.n_visible == ref["n_visible"]
     assert_image_parity(imgs[0], Ts[0], ref)
@@ -85,14 +87,14 @@ def ragged_scene(n=3000, seed=11, L=3, K=2):
     return G, views
 
 
-@TILES
-def test_forward_ragged_multiview(tile):
+@TILE_BINS
+def test_forward_ragged_multiview(tile, bin):
     G, views = ragged_scene()
-    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
+    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
     for v, img, T in zip(views, imgs, Ts):
         ref = O.render(G, v)
         st = assert_image_parity(img, T, ref)
-        print(f"[parity] fp32 tile {tile} {v['width']}x{v['height']}: {st}")
+        print(f"[parity] fp32 tile {tile} bin {bin} {v['width']}x{v['height']}: {st}")
 
 
 def test_forward_bf16_coefficients_are_exact_inputs():
@@ -166,15 +168,17 @@ def test_slice_project_records_match_oracle():
         close(r[:, 9], ref["depth"][both], 1e-6, 1e-6, "depth")
 
 
-@TILES
-def test_tile_lists_are_depth_ordered_and_complete(tile):
-    """Every splat is listed in the tiles its support ellipse reaches (R7 with
-    slack): within its support box, once per tile, as many tiles as
+@TILE_BINS
+def test_tile_lists_are_depth_ordered_and_complete(tile, bin):
+    """Every splat is listed in the binning tiles its support ellipse reaches
+    (R7 with slack): within its support box, once per tile, as many tiles as
     slice/project counted, and in every tile holding a pixel where the
     record's own alpha (in FP64) clears alpha_min; each tile's list is in
-    (depth, index) order."""
+    (depth, index) order.  The lists are per binning tile (bin x bin
+    pixels), whatever the compositing tile."""
     G, views = ragged_scene(n=2500, seed=14)
-    fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile))
+    fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
+    tile = bin  # the geometry below is that of the binning tiles
     rec, tiles, ranges, vals = read_state(fr)
     n = G["logit"].shape[0]
     amin = 1.0 / 255.0
@@ -208,16 +212,16 @@ def test_tile_lists_are_depth_ordered_and_complete(tile):
             listed_total += len(got)
         tile_base += tx_n * ((v["height"] + tile - 1) // tile)
     assert tile_base == ranges.shape[0]
-    print(f"[bin] tile {tile}: {listed_total} pairs vs {box_total} box tiles ({listed_total / box_total:.3f})")
+    print(f"[bin] bin {tile}: {listed_total} pairs vs {box_total} box tiles ({listed_total / box_total:.3f})")
     assert listed_total < box_total  # the ellipse drops tiles the box would keep
 
 
-@TILES
-def test_batched_equals_one_by_one(tile):
+@TILE_BINS
+def test_batched_equals_one_by_one(tile, bin):
     G, views = ragged_scene(n=2000, seed=15)
-    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile))
+    _, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
     for v, img, T in zip(views, imgs, Ts):
-        _, _, im1, T1 = gpu_forward(G, [v], dict(tile_size=tile))
+        _, _, im1, T1 = gpu_forward(G, [v], dict(tile_size=tile, bin_size=bin))
         np.testing.assert_array_equal(img, im1[0])
         np.testing.assert_array_equal(T, T1[0])
 
@@ -327,18 +331,50 @@ def test_batch_depth_does_not_change_results(tile):
             assert rel < 1e-5, (B, k, rel)
 
 
+@TILES
+def test_bin_size_does_not_change_results(tile):
+    """bin_size only changes which list a compositing tile walks (its binning
+    tile's, holding the splats of every compositing tile inside it): images
+    and T are bit-identical, since a pixel composites the same splats in the
+    same order; n_last counts positions in the larger list, so it can only
+    grow; gradients differ only by the order of FP32 sums."""
+    from paper_2310_10642_gb300 import render as R
+    G, views = ragged_scene(n=2500, seed=21)
+    p = R.params_to_device(G)
+    dL = torch.randn(sum(3 * v["width"] * v["height"] for v in views), device="cuda",
+                     generator=torch.Generator(device="cuda").manual_seed(4))
+    out = {}
+    bins = [b for b in (16, 32, 64) if b >= tile]
+    for b in bins:
+        fr = R.Frame(G["logit"].shape[0], views, dict(tile_size=tile, bin_size=b))
+        fr.forward(p)
+        g = fr.backward(p, dL)
+        torch.cuda.synchronize()
+        assert fr.counters().status == 0
+        out[b] = (fr.image.clone(), fr.final_T.clone(), fr.n_last.clone(), {k: v.clone() for k, v in g.items()},
+                  int(fr.last_counters.n_pairs))
+    ref = out[tile]
+    for b in bins[1:]:
+        img, T, nl, g, npairs = out[b]
+        assert torch.equal(img, ref[0]) and torch.equal(T, ref[1])
+        assert bool((nl >= ref[2]).all())
+        assert npairs < ref[4]  # coarser bins: fewer (splat, tile) pairs
+        for k in R.PARAM_KEYS:
+            rel = float((g[k] - ref[3][k]).norm() / ref[3][k].norm())
+            assert rel < 1e-5, (b, k, rel)
+
+
 def test_autotune_returns_a_timed_candidate():
     from paper_2310_10642_gb300 import autotune as A
     from paper_2310_10642_gb300 import render as R
     G, views = ragged_scene(n=2000, seed=23)
     p = R.params_to_device(G)
-    cands = A.candidates((16, 32), (64, 256))
+    cands = A.candidates((16, 32), (64, 256), (1, 2))
     opts, table = A.tune(p, views, dict(record_fp16=0), cands=cands, reps=2, warmup=1, cache=None)
-    assert {"tile_size": opts["tile_size"], "batch_depth": opts["batch_depth"]} in cands
-    assert len(table) == 4 and all(t["ms"] > 0 for t in table)
-    assert min(t["ms"] for t in table) == [t["ms"] for t in table
-                                           if t["tile_size"] == opts["tile_size"]
-                                           and t["batch_depth"] == opts["batch_depth"]][0]
+    pick = {k: opts[k] for k in A.KNOBS}
+    assert pick in cands
+    assert len(table) == 8 and all(t["ms"] > 0 for t in table)
+    assert min(t["ms"] for t in table) == [t["ms"] for t in table if all(t[k] == pick[k] for k in A.KNOBS)][0]
 
 
 def test_fp64_fallback_for_ill_conditioned_slices():
