@@ -484,17 +484,25 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                 float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 float g_bl = 0.0f;
                 bool contrib = false;
+                // the Gaussian factor of every pixel first (independent chains), -1 where
+                // the pixel takes no part; then the adjoint updates in order
+                float Gv[P];
 #pragma unroll
                 for (int k = 0; k < P; k++) {
-                    if (!(sub >> k & 1u)) continue;
-                    if (pos >= last[k]) continue;
                     const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                     const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
-                    if (!(p2 <= 0.0f)) continue;
                     const float G = ex2_approx(p2);
+                    const bool on = (sub >> k & 1u) && pos < last[k] && p2 <= 0.0f &&
+                                    fminf(O.alpha_max, __fmul_rn(b.y, G)) >= O.alpha_min;
+                    Gv[k] = on ? G : -1.0f;
+                }
+#pragma unroll
+                for (int k = 0; k < P; k++) {
+                    const float G = Gv[k];
+                    if (G < 0.0f) continue;
+                    const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                     const float araw = __fmul_rn(b.y, G);
                     const float alpha = fminf(O.alpha_max, araw);
-                    if (alpha < O.alpha_min) continue;
                     contrib = true;
                     const float inv_om = rcp_approx(1.0f - alpha);
                     const float Ti = T[k] * inv_om;  // transmittance before this splat
