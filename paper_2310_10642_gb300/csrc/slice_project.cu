@@ -17,9 +17,19 @@
 
 namespace fgs4d {
 
+// One coefficient: from global memory through the read-only data cache, or
+// (kShared) a plain load from the shared-memory copy.
+template <bool kShared, class T>
+__device__ __forceinline__ float load_coef(const T* p) {
+    if constexpr (kShared)
+        return to_float(*p);
+    else
+        return to_float(__ldg(p));
+}
+
 // Coefficients of Gaussian g: row r at sh[r * n]; one address increment per
 // row (row stride n), the storage type resolved outside the loops.
-template <int L, class T>
+template <int L, bool kShared, class T>
 __device__ __forceinline__ void color_sum(const T* __restrict__ sh, size_t n, int K, float dt_scaled, const float* Y,
                                           float* raw) {
     constexpr int NB = (L + 1) * (L + 1);
@@ -30,26 +40,49 @@ __device__ __forceinline__ void color_sum(const T* __restrict__ sh, size_t n, in
 #pragma unroll
         for (int j = 0; j < NB; j++) {
             const float b = cf * Y[j];
-            raw[0] = fmaf(b, to_float(__ldg(row)), raw[0]);
-            raw[1] = fmaf(b, to_float(__ldg(row + n)), raw[1]);
-            raw[2] = fmaf(b, to_float(__ldg(row + 2 * n)), raw[2]);
+            raw[0] = fmaf(b, load_coef<kShared>(row), raw[0]);
+            raw[1] = fmaf(b, load_coef<kShared>(row + n), raw[1]);
+            raw[2] = fmaf(b, load_coef<kShared>(row + 2 * n), raw[2]);
             row += 3 * n;
         }
     }
 }
 
+constexpr int kSliceThreads = 128;
+// A block stages its Gaussians' 4DSH coefficients in shared memory (one
+// column per thread, rows as in global memory) when they fit in this many
+// bytes, so that the views after the first read them on chip.
+constexpr int kSliceStageBytes = 48 * 1024;
+
+// staged: the coefficients of this thread's Gaussian are column threadIdx.x
+// of a [rows][kSliceThreads] array in shared memory.
 template <int L>
 __device__ __forceinline__ void color_forward(const DevGauss& G, int g, const ViewGeom& w, const DevView& V,
-                                              float* raw) {
+                                              const void* staged, float* raw) {
     float d[3];
     view_dir(w, V, d);
     float Y[16];
     sh_eval(L, d[0], d[1], d[2], Y);
     const float dts = 2.0f * w.dt * G.inv_period;
-    if (G.shs_bf16)
-        color_sum<L>(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
-    else
-        color_sum<L>(reinterpret_cast<const float*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
+    if (staged) {
+        if (G.shs_bf16)
+            color_sum<L, true>(reinterpret_cast<const __nv_bfloat16*>(staged) + threadIdx.x, (size_t)kSliceThreads,
+                               G.K, dts, Y, raw);
+        else
+            color_sum<L, true>(reinterpret_cast<const float*>(staged) + threadIdx.x, (size_t)kSliceThreads, G.K, dts,
+                               Y, raw);
+    } else if (G.shs_bf16) {
+        color_sum<L, false>(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
+    } else {
+        color_sum<L, false>(reinterpret_cast<const float*>(G.shs) + g, (size_t)G.n, G.K, dts, Y, raw);
+    }
+}
+
+// Copies the coefficient rows of Gaussian g into column threadIdx.x of dst
+// (coalesced: row r of the block's Gaussians is contiguous in global memory).
+template <class T>
+__device__ __forceinline__ void stage_coefficients(const T* __restrict__ src, size_t n, int rows, T* dst) {
+    for (int r = 0; r < rows; r++) dst[r * kSliceThreads] = src[(size_t)r * n];
 }
 
 // Colour part of the adjoint for one splat (Eq. 11): per channel the raw
@@ -97,15 +130,25 @@ __device__ __forceinline__ void color_adjoint(const T* __restrict__ sh, size_t n
 }
 
 template <int L>
-__global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, const __grid_constant__ ViewSet VS,
-                                                            const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
-                                                            uint32_t* __restrict__ tiles_touched,
-                                                            uint32_t* __restrict__ depth_key,
-                                                            uint32_t* __restrict__ counters,
-                                                            float4* __restrict__ aux) {
+__global__ void __launch_bounds__(kSliceThreads) slice_project_kernel(
+    const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
+    uint32_t* __restrict__ tiles_touched, uint32_t* __restrict__ depth_key, uint32_t* __restrict__ counters,
+    float4* __restrict__ aux, int stage) {
+    extern __shared__ __align__(16) unsigned char s_coef[];  // [rows][kSliceThreads] when stage != 0
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= G.n) return;
+    if (g >= G.n) return;  // no barrier below: a thread reads only its own column
     const size_t n = (size_t)G.n;
+    const void* staged = nullptr;
+    if (stage) {
+        const int rows = 3 * (L + 1) * (L + 1) * (G.K + 1);
+        if (G.shs_bf16)
+            stage_coefficients(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, n, rows,
+                               reinterpret_cast<__nv_bfloat16*>(s_coef) + threadIdx.x);
+        else
+            stage_coefficients(reinterpret_cast<const float*>(G.shs) + g, n, rows,
+                               reinterpret_cast<float*>(s_coef) + threadIdx.x);
+        staged = s_coef;
+    }
     Core c;
     load_core(G, g, c);
     if (!c.ok) {
@@ -124,7 +167,7 @@ __global__ void __launch_bounds__(128) slice_project_kernel(const DevGauss G, co
             continue;
         }
         float raw[3];
-        color_forward<L>(G, g, w, V, raw);
+        color_forward<L>(G, g, w, V, staged, raw);
         float col[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ch++) col[ch] = fmaxf(raw[ch] + 0.5f, 0.0f);
@@ -541,17 +584,22 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (G.n == 0) return cudaSuccess;
-    const int threads = 128;
+    const int threads = kSliceThreads;
     const int blocks = (G.n + threads - 1) / threads;
+    // stage the coefficients on chip when more than one view reads them and they fit
+    const size_t stage_bytes = (size_t)3 * (G.L + 1) * (G.L + 1) * (G.K + 1) * threads *
+                               (G.shs_bf16 ? sizeof(__nv_bfloat16) : sizeof(float));
+    const int stage = VS.n > 1 && stage_bytes <= (size_t)kSliceStageBytes;
+    const size_t smem = stage ? stage_bytes : 0;
     auto* rec = reinterpret_cast<SplatRecord*>(state + lay.records);
     auto* tt = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
     auto* dk = reinterpret_cast<uint32_t*>(state + lay.depth_key);
     auto* aux = O.aux ? reinterpret_cast<float4*>(state + lay.aux) : nullptr;
     switch (G.L) {
-        case 0: slice_project_kernel<0><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
-        case 1: slice_project_kernel<1><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
-        case 2: slice_project_kernel<2><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
-        default: slice_project_kernel<3><<<blocks, threads, 0, st>>>(G, VS, O, rec, tt, dk, counters, aux); break;
+        case 0: slice_project_kernel<0><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
+        case 1: slice_project_kernel<1><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
+        case 2: slice_project_kernel<2><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
+        default: slice_project_kernel<3><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
     }
     count_launches(1);
     return cudaGetLastError();
