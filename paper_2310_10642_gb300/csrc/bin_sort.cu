@@ -361,114 +361,57 @@ static cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], const uint32
 // ---------------------------------------------------------------------------
 // Pair emission and tile ranges
 // ---------------------------------------------------------------------------
-// Warp-cooperative emission: the 32 lanes take 32 consecutive depth-sorted
-// splats, then write each splat's pairs together so that stores to the pair
-// arrays are contiguous.  Exactly tiles[sid] pairs are written per splat (the
-// count the offsets were built from); should the rect ever disagree, surplus
-// slots get the dump tile id VS.total_tiles, which no CTA renders.
-__global__ void __launch_bounds__(256) emit_pairs_kernel(const __grid_constant__ ViewSet VS, uint32_t n_gauss,
-                                                         const uint32_t* __restrict__ sorted_splats,
-                                                         const uint32_t* __restrict__ offsets,
-                                                         const uint32_t* __restrict__ tiles,
-                                                         const void* __restrict__ rec, int rec_fp16,
-                                                         float ln_alpha_min, uint32_t n_max,
-                                                         uint32_t* counters, uint32_t capacity, int tile,
-                                                         uint32_t* __restrict__ pair_keys,
-                                                         uint32_t* __restrict__ pair_vals) {
-    constexpr unsigned F = 0xffffffffu;
+// Pair emission, one thread per visible splat in depth order: the thread
+// walks its splat's tile rows (the same ellipse_row_tiles calls as the
+// count, so exactly tiles[sid] pairs) and writes (tile, splat) pairs from
+// the splat's offset on.  With 64-pixel binning tiles a splat reaches ~10
+// tiles, and a warp-cooperative walk (32 lanes over one splat's box tiles,
+// ballot-packed) spent more on broadcasting each splat than on its pairs.
+// Should the rows ever disagree with the count, surplus slots get the dump
+// tile id VS.total_tiles, which no block renders.
+__global__ void __launch_bounds__(256) emit_pairs_kernel(
+    const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted_splats,
+    const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tiles, const void* __restrict__ rec,
+    int rec_fp16, float ln_alpha_min, uint32_t n_max, uint32_t* counters, uint32_t capacity, int tile,
+    uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals) {
     const uint32_t n_vis = min(counters[0], n_max);
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     bool overflow = false;
-    for (uint32_t base = warp0 * 32; base < n_vis; base += n_warps * 32) {
-        // lane p prepares splat base + p: its box rect and its ellipse rows
-        const uint32_t p = base + lane;
-        uint32_t sid = 0, o = 0, cnt = 0, nbox = 0;
-        int rect[4] = {0, 0, -1, -1};
-        EllipseRows e{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, false};
-        int vw = 0;
-        if (p < n_vis) {
-            sid = sorted_splats[p];
-            vw = (int)(sid / n_gauss);
-            const DevView& V = VS.v[vw];
-            const SplatView r =
-                rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
-                         : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
-            nbox = (uint32_t)box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect);
-            if (nbox > 0) e = ellipse_rows(r, ln_alpha_min);
-            o = offsets[p];
-            cnt = tiles[sid];
-        }
-        // the warp walks each splat's box tiles row by row, 32 at a time; a lane keeps its tile
-        // when the ellipse's span of that row covers it, and a ballot packs the kept tiles into
-        // the splat's slots in the same order the count took them (row by row, left to right)
-        for (int s = 0; s < 32; s++) {
-            const uint32_t s_cnt = __shfl_sync(F, cnt, s);
-            if (s_cnt == 0) continue;
-            const uint32_t s_box = __shfl_sync(F, nbox, s);
-            const uint32_t s_sid = __shfl_sync(F, sid, s), s_o = __shfl_sync(F, o, s);
-            int s_rect[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) s_rect[q] = __shfl_sync(F, rect[q], s);
-            EllipseRows se;
-            se.u = __shfl_sync(F, e.u, s);
-            se.v = __shfl_sync(F, e.v, s);
-            se.ba = __shfl_sync(F, e.ba, s);
-            se.ia = __shfl_sync(F, e.ia, s);
-            se.ks = __shfl_sync(F, e.ks, s);
-            se.rys = __shfl_sync(F, e.rys, s);
-            se.irys = __shfl_sync(F, e.irys, s);
-            se.dyl = __shfl_sync(F, e.dyl, s);
-            se.exact = __shfl_sync(F, (int)e.exact, s) != 0;
-            const DevView& V = VS.v[__shfl_sync(F, vw, s)];
-            const uint32_t tb = V.tile_base, tiles_x = (uint32_t)V.tiles_x;
-            const uint32_t wx = (uint32_t)(s_rect[2] - s_rect[0] + 1);
-            const float inv_wx = 1.0f / (float)wx;
-            // spans of the first 32 rows, one per lane; rows beyond are computed where needed
-            int row_tx0 = 0, row_nr = 0;
-            if (s_rect[1] + lane <= s_rect[3])
-                row_nr = ellipse_row_tiles(se, V, tile, s_rect, s_rect[1] + lane, &row_tx0);
-            uint32_t written = 0;
-            for (uint32_t b0 = 0; b0 < s_box; b0 += 32) {  // uniform trip count
-                const uint32_t k = b0 + lane;
-                uint32_t r = (uint32_t)((float)k * inv_wx);  // k / wx, corrected to the exact quotient
-                if (r * wx > k) r--;
-                else if ((r + 1) * wx <= k) r++;
-                int tx0 = __shfl_sync(F, row_tx0, r & 31u), nr = __shfl_sync(F, row_nr, r & 31u);
-                bool keep = false;
-                uint32_t key = 0;
-                if (k < s_box) {
-                    const int ty = s_rect[1] + (int)r, tx = s_rect[0] + (int)(k - r * wx);
-                    if (r >= 32u) nr = ellipse_row_tiles(se, V, tile, s_rect, ty, &tx0);
-                    keep = tx >= tx0 && tx < tx0 + nr;
-                    key = tb + (uint32_t)ty * tiles_x + (uint32_t)tx;
-                }
-                const uint32_t kept = __ballot_sync(F, keep);
-                const uint32_t pos = written + (uint32_t)__popc(kept & lt);
-                if (keep && pos < s_cnt) {
-                    const uint32_t at = s_o + pos;
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_vis; p += gridDim.x * blockDim.x) {
+        const uint32_t sid = sorted_splats[p];
+        const uint32_t cnt = tiles[sid];
+        if (cnt == 0) continue;
+        const uint32_t o = offsets[p];
+        const DevView& V = VS.v[sid / n_gauss];
+        const SplatView r = rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
+                                     : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
+        int rect[4];
+        uint32_t written = 0;
+        if (box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect) > 0) {
+            const EllipseRows e = ellipse_rows(r, ln_alpha_min);
+            for (int ty = rect[1]; ty <= rect[3]; ty++) {
+                int tx0;
+                const int nr = ellipse_row_tiles(e, V, tile, rect, ty, &tx0);
+                const uint32_t row_key = V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x + (uint32_t)tx0;
+                for (int i = 0; i < nr && written < cnt; i++, written++) {
+                    const uint32_t at = o + written;
                     if (at >= capacity) {
                         overflow = true;
                     } else {
-                        pair_keys[at] = key;
-                        pair_vals[at] = s_sid;
+                        pair_keys[at] = row_key + (uint32_t)i;
+                        pair_vals[at] = sid;
                     }
                 }
-                written += (uint32_t)__popc(kept);
             }
-            // the count and the rows come from the same function on the same record, so this never
-            // runs; it keeps every slot of the splat defined (the dump tile sorts last)
-            for (uint32_t k = written + lane; k < s_cnt; k += 32) {
-                const uint32_t at = s_o + k;
-                if (at >= capacity) {
-                    overflow = true;
-                    break;
-                }
-                pair_keys[at] = VS.total_tiles;
-                pair_vals[at] = s_sid;
+        }
+        // the count came from the same rows, so this never runs; it keeps every slot defined
+        for (; written < cnt; written++) {
+            const uint32_t at = o + written;
+            if (at >= capacity) {
+                overflow = true;
+                break;
             }
+            pair_keys[at] = VS.total_tiles;
+            pair_vals[at] = sid;
         }
     }
     if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
@@ -612,8 +555,9 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
                     st);
     if (e != cudaSuccess) return e;
     // 4. emission
-    emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, O.record_fp16, O.ln_alpha_min, S,
-                                                       counters, cap, O.bin, pk[0], pv[0]);
+    emit_pairs_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(
+        VS, (uint32_t)(S / (uint32_t)VS.n), sorted, offsets, tiles, rec, O.record_fp16, O.ln_alpha_min, S, counters,
+        cap, O.bin, pk[0], pv[0]);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (cap == 0) return cudaSuccess;

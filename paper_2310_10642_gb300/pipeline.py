@@ -6,8 +6,11 @@ and whose outputs (image, gradients) go back to pinned host memory.  While
 step k computes on the current stream, the inputs of step k + 1 are copied
 in and the outputs of step k - 1 copied out on two copy streams, through two
 device buffer sets; CUDA events keep each buffer from being overwritten while
-a copy or a step still uses it.  Argument marshalling and stream ordering
-only: every step of the method runs in the library's kernels.
+a copy or a step still uses it.  With ``graphs`` (the default) the compute of
+each buffer set is captured as a CUDA graph after its first eager step and
+replayed from then on, so a step costs one launch on the host.  Argument
+marshalling and stream ordering only: every step of the method runs in the
+library's kernels.
 """
 from __future__ import annotations
 
@@ -17,10 +20,11 @@ from . import render as R
 
 
 class HostPipeline:
-    def __init__(self, frame: "R.Frame", params_like: dict, device="cuda"):
+    def __init__(self, frame: "R.Frame", params_like: dict, device="cuda", graphs: bool = True):
         """params_like: device parameters whose shapes and dtypes the host
         inputs have (sh_degree, n_freq and period are taken from it)."""
         self.frame = frame
+        self.graphs = bool(graphs)
         self.stream = torch.cuda.current_stream()
         self.s_in, self.s_out = torch.cuda.Stream(), torch.cuda.Stream()
         npix = frame.total_pixels
@@ -32,7 +36,8 @@ class HostPipeline:
                 dp["rotation"] = params_like["rotation"]
             sl = dict(p=dp, dL=torch.empty(3 * npix, device=device), img=torch.empty(3 * npix, device=device),
                       g={k: torch.empty(params_like[k].shape, device=device) for k in R.PARAM_KEYS},
-                      ev_in=torch.cuda.Event(), ev_used=torch.cuda.Event(), ev_out=torch.cuda.Event())
+                      ev_in=torch.cuda.Event(), ev_used=torch.cuda.Event(), ev_out=torch.cuda.Event(),
+                      graph=None, eager_steps=0)
             for ev in ("ev_in", "ev_used", "ev_out"):  # start recorded: the first waits do not block
                 sl[ev].record(self.stream)
             self.slots.append(sl)
@@ -45,16 +50,29 @@ class HostPipeline:
             sl["dL"].copy_(host_dL, non_blocking=True)
             sl["ev_in"].record(self.s_in)
 
-    def _compute(self, sl):
-        st = self.stream
-        st.wait_event(sl["ev_in"])
-        st.wait_event(sl["ev_out"])  # the outputs of this slot have left the device
+    def _step(self, sl):
         fr = self.frame
         fr.slice_project(sl["p"])
         fr.bin_sort()
         fr.render()
         fr.backward(sl["p"], sl["dL"], sl["g"])
         sl["img"].copy_(fr.image, non_blocking=True)
+
+    def _compute(self, sl):
+        st = self.stream
+        st.wait_event(sl["ev_in"])
+        st.wait_event(sl["ev_out"])  # the outputs of this slot have left the device
+        if self.graphs and sl["graph"] is None and sl["eager_steps"] > 0:
+            # every buffer the step touches is fixed per slot, so the step is captured once
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._step(sl)
+            sl["graph"] = g
+        if sl["graph"] is not None:
+            sl["graph"].replay()
+        else:
+            self._step(sl)
+            sl["eager_steps"] += 1
         sl["ev_used"].record(st)
 
     def _copy_out(self, sl, host_image: torch.Tensor, host_grads: dict):

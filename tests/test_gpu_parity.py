@@ -920,10 +920,12 @@ def test_config1_crops_and_gradients():
     assert_grad_parity(gg, go)
 
 
-def test_host_pipeline_equals_plain_steps():
+@pytest.mark.parametrize("graphs", [False, True])
+def test_host_pipeline_equals_plain_steps(graphs):
     """HostPipeline (copies of neighbouring steps overlapped with compute)
     returns, for each step's host inputs, what a plain forward + backward of
-    those inputs returns."""
+    those inputs returns, eagerly or replaying each slot's captured graph
+    (five steps: both slots replay)."""
     from paper_2310_10642_gb300 import render as R
     from paper_2310_10642_gb300.pipeline import HostPipeline
     G, views = ragged_scene(n=1500, seed=61)
@@ -933,7 +935,7 @@ def test_host_pipeline_equals_plain_steps():
     npix = fr.total_pixels
     gen = torch.Generator().manual_seed(2)
     inputs, outputs, want = [], [], []
-    for k in range(3):
+    for k in range(5):
         hp = {key: (p[key].cpu() + (0.01 * k if key == "mu" else 0.0)).pin_memory() for key in R.PARAM_KEYS}
         hd = torch.randn(3 * npix, generator=gen).pin_memory()
         inputs.append((hp, hd))
@@ -943,8 +945,10 @@ def test_host_pipeline_equals_plain_steps():
         fr.forward(dp, check=False)
         g = fr.backward(dp, hd.cuda())
         want.append((fr.image.cpu(), {key: v.cpu() for key, v in g.items()}))
-    HostPipeline(fr, p).run(inputs, outputs)
+    pipe = HostPipeline(fr, p, graphs=graphs)
+    pipe.run(inputs, outputs)
     torch.cuda.synchronize()
+    assert all((sl["graph"] is not None) == graphs for sl in pipe.slots)
     for (img, g), (wi, wg) in zip(outputs, want):
         assert torch.equal(img, wi)
         for key in R.PARAM_KEYS:
