@@ -526,10 +526,12 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                     }
                 }
                 if (__any_sync(F, contrib)) {
+                    // lane 4i holds the warp total of value i; lane 1 (a copy of value 0's)
+                    // carries the ninth, so one shared atomic instruction adds all nine
                     const float tot = warp_reduce8(gv, lane);
-                    if ((lane & 3) == 0) atomicAdd(&s_g[j * kGradStride + (lane >> 2)], tot);
                     const float tb = warp_sum(g_bl);
-                    if (lane == 0) atomicAdd(&s_g[j * kGradStride + 8], tb);
+                    if ((lane & 3) == 0 || lane == 1)
+                        atomicAdd(&s_g[j * kGradStride + (lane == 1 ? 8 : lane >> 2)], lane == 1 ? tb : tot);
                 }
             }
         }
