@@ -67,6 +67,8 @@ template <class Rec>
 struct Form;
 template <>
 struct Form<SplatRecord> {  // conic pre-scaled: X = -log2e/2 a, Y = -log2e b, Z = -log2e/2 c
+    // power2 can round to a positive value: pixels with power2 > 0 are skipped
+    static constexpr bool kNeverPositive = false;
     __device__ __forceinline__ static void stage(const SplatView& r, float& X, float& Y, float& Z) {
         X = __fmul_rn(-0.5f * kLog2e, r.a);
         Y = __fmul_rn(-kLog2e, r.b);
@@ -79,6 +81,8 @@ struct Form<SplatRecord> {  // conic pre-scaled: X = -log2e/2 a, Y = -log2e b, Z
 template <>
 struct Form<SplatRecordH> {  // Cholesky factor pre-scaled by kappa, kappa^2 = log2(e) / 2
     static constexpr float kKappa = 0.8493218002880191f;
+    // power2 is a negated sum of squares: never positive, NaN only from non-finite inputs
+    static constexpr bool kNeverPositive = true;
     __device__ __forceinline__ static void stage(const SplatView& r, float& X, float& Y, float& Z) {
         X = __fmul_rn(kKappa, r.l11);
         Y = __fmul_rn(kKappa, r.l21);
@@ -90,6 +94,15 @@ struct Form<SplatRecordH> {  // Cholesky factor pre-scaled by kappa, kappa^2 = l
         return -__fmaf_rn(t1, t1, __fmul_rn(t2, t2));
     }
 };
+
+// min(a, b) that returns NaN when b is NaN (fminf would return a): the alpha
+// clamp with it and the test alpha >= alpha_min reject a NaN power2 without
+// a test of its own.
+__device__ __forceinline__ float min_nan(float a, float b) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 
 // Shared-memory form of a record: a = (u, v, X, Y), b = (Z, alpha_eff, R, G),
 // c = (B, hx, hy, 0), with (X, Y, Z) as Form<Rec> stages them.
@@ -290,10 +303,10 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
                         st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
                     }
                     const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
-                    if (!(p2 <= 0.0f)) continue;
+                    if (!Form<Rec>::kNeverPositive && !(p2 <= 0.0f)) continue;
                     const float araw = __fmul_rn(b.y, ex2_approx(p2));
-                    const float alpha = fminf(O.alpha_max, araw);
-                    if (alpha < O.alpha_min) continue;
+                    const float alpha = min_nan(O.alpha_max, araw);
+                    if (!(alpha >= O.alpha_min)) continue;  // also a NaN power2
                     const float Tn = T[k] * (1.0f - alpha);
                     if (Tn < O.T_min) {
                         live &= ~(1u << k);
@@ -492,8 +505,8 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                     const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                     const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
                     const float G = ex2_approx(p2);
-                    const bool on = (sub >> k & 1u) && pos < last[k] && p2 <= 0.0f &&
-                                    fminf(O.alpha_max, __fmul_rn(b.y, G)) >= O.alpha_min;
+                    const bool on = (sub >> k & 1u) && pos < last[k] && (Form<Rec>::kNeverPositive || p2 <= 0.0f) &&
+                                    min_nan(O.alpha_max, __fmul_rn(b.y, G)) >= O.alpha_min;
                     Gv[k] = on ? G : -1.0f;
                 }
 #pragma unroll
