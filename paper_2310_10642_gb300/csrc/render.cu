@@ -77,6 +77,22 @@ struct Form<SplatRecord> {  // conic pre-scaled: X = -log2e/2 a, Y = -log2e b, Z
     __device__ __forceinline__ static float power2(float X, float Y, float Z, float dx, float dy) {
         return __fmaf_rn(__fmul_rn(X, dx), dx, __fmaf_rn(__fmul_rn(Z, dy), dy, __fmul_rn(__fmul_rn(Y, dx), dy)));
     }
+    // power2 split into a part of dx (one per pixel column of a lane) and a
+    // part of dy (one per pixel row), each computed once per visit;
+    // combine(col(dx), row(dy)) equals power2(X, Y, Z, dx, dy) bit for bit.
+    struct Col {
+        float dx, xdx, ydx;
+    };
+    struct Row {
+        float dy, zdy;
+    };
+    __device__ __forceinline__ static Col col(float X, float Y, float dx) {
+        return Col{dx, __fmul_rn(X, dx), __fmul_rn(Y, dx)};
+    }
+    __device__ __forceinline__ static Row row(float Y, float Z, float dy) { return Row{dy, __fmul_rn(Z, dy)}; }
+    __device__ __forceinline__ static float combine(float X, const Col& c, const Row& r) {
+        return __fmaf_rn(c.xdx, c.dx, __fmaf_rn(r.zdy, r.dy, __fmul_rn(c.ydx, r.dy)));
+    }
 };
 template <>
 struct Form<SplatRecordH> {  // Cholesky factor pre-scaled by kappa, kappa^2 = log2(e) / 2
@@ -92,6 +108,22 @@ struct Form<SplatRecordH> {  // Cholesky factor pre-scaled by kappa, kappa^2 = l
         const float t1 = __fmaf_rn(X, dx, __fmul_rn(Y, dy));
         const float t2 = __fmul_rn(Z, dy);
         return -__fmaf_rn(t1, t1, __fmul_rn(t2, t2));
+    }
+    // as for Form<SplatRecord>: combine(col(dx), row(dy)) equals power2 bit for bit
+    struct Col {
+        float dx;
+    };
+    struct Row {
+        float ydy, t22;  // Y dy and (Z dy)^2
+    };
+    __device__ __forceinline__ static Col col(float X, float Y, float dx) { return Col{dx}; }
+    __device__ __forceinline__ static Row row(float Y, float Z, float dy) {
+        const float t2 = __fmul_rn(Z, dy);
+        return Row{__fmul_rn(Y, dy), __fmul_rn(t2, t2)};
+    }
+    __device__ __forceinline__ static float combine(float X, const Col& c, const Row& r) {
+        const float t1 = __fmaf_rn(X, c.dx, r.ydy);
+        return -__fmaf_rn(t1, t1, r.t22);
     }
 };
 
@@ -294,15 +326,21 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
                 const float4 c = s_c[j];
                 const int32_t pos1 = (int32_t)(base - range.x) + j + 1;
                 const uint32_t act = sub & live;
+                // the lane's pixels share two columns and two rows (one each with
+                // 16x16 tiles): their parts of the quadratic form, once per visit
+                const auto col0 = Form<Rec>::col(a.z, a.w, __fsub_rn(fbx, a.x));
+                const auto row0 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby, a.y));
+                const auto col1 = Form<Rec>::col(a.z, a.w, __fsub_rn(fbx + TP::off_x(1), a.x));
+                const auto row1 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby + TP::off_y(2), a.y));
 #pragma unroll
                 for (int k = 0; k < P; k++) {
                     if (!(act >> k & 1u)) continue;
-                    const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                     if (kStats) {
+                        const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                         st_eval++;
                         st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
                     }
-                    const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
+                    const float p2 = Form<Rec>::combine(a.z, (k & 1) ? col1 : col0, (k >> 1) ? row1 : row0);
                     if (!Form<Rec>::kNeverPositive && !(p2 <= 0.0f)) continue;
                     const float araw = __fmul_rn(b.y, ex2_approx(p2));
                     const float alpha = min_nan(O.alpha_max, araw);
