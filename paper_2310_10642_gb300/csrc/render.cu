@@ -538,10 +538,13 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                 // the Gaussian factor of every pixel first (independent chains), -1 where
                 // the pixel takes no part; then the adjoint updates in order
                 float Gv[P];
+                const auto col0 = Form<Rec>::col(a.z, a.w, __fsub_rn(fbx, a.x));
+                const auto row0 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby, a.y));
+                const auto col1 = Form<Rec>::col(a.z, a.w, __fsub_rn(fbx + TP::off_x(1), a.x));
+                const auto row1 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby + TP::off_y(2), a.y));
 #pragma unroll
                 for (int k = 0; k < P; k++) {
-                    const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
-                    const float p2 = Form<Rec>::power2(a.z, a.w, b.x, dx, dy);
+                    const float p2 = Form<Rec>::combine(a.z, (k & 1) ? col1 : col0, (k >> 1) ? row1 : row0);
                     const float G = ex2_approx(p2);
                     const bool on = (sub >> k & 1u) && pos < last[k] && (Form<Rec>::kNeverPositive || p2 <= 0.0f) &&
                                     min_nan(O.alpha_max, __fmul_rn(b.y, G)) >= O.alpha_min;
