@@ -436,6 +436,18 @@ __device__ __forceinline__ float warp_reduce8(const float (&v)[8], int lane) {
 
 constexpr int kGradStride = 12;  // floats per staged splat in the shared gradient accumulator
 
+// One staged batch of the adjoint: records, sub-region masks, splat ids and
+// the per-splat gradient sums of the block.
+struct BwdStage {
+    float4 a[kTilePix];
+    float4 b[kTilePix];
+    float4 n[kTilePix];  // natural conic (a, b, c) for the flush, and the colour's B
+    uint32_t m[kTilePix];
+    uint32_t sid[kTilePix];
+    float g[kTilePix * kGradStride];
+};
+constexpr size_t kBwdSmem = 2 * sizeof(BwdStage);  // double-buffered: 53,248 bytes (dynamic)
+
 template <int TS, class Rec>
 __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     const __grid_constant__ ViewSet VS, const DevOpts O, const uint2* __restrict__ ranges,
@@ -444,12 +456,11 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     float4* __restrict__ grad2d) {
     using TP = TilePixels<TS>;
     constexpr int P = TP::P;
-    __shared__ float4 s_a[kTilePix];
-    __shared__ float4 s_b[kTilePix];
-    __shared__ float4 s_n[kTilePix];    // natural conic (a, b, c) for the flush, and the colour's B
-    __shared__ uint32_t s_m[kTilePix];  // sub-region mask of each staged splat
-    __shared__ uint32_t s_sid[kTilePix];
-    __shared__ __align__(16) float s_g[kTilePix * kGradStride];
+    // Two staging buffers: while the warps walk batch k in one, each thread
+    // flushes its slot of batch k - 1 and stages its slot of batch k + 1 in
+    // the other, so one barrier per batch separates the batches.
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    BwdStage* S = reinterpret_cast<BwdStage*>(s_dyn);
     __shared__ int s_max;
     const int tid = threadIdx.x, lane = tid & 31, wshift = (tid >> 5) * P;
     const unsigned F = 0xffffffffu;
@@ -490,35 +501,71 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
     const int warp_last = __reduce_max_sync(0xffffffffu, my_max);  // positions >= this: nothing in this warp
     if (tid == 0) s_max = 0;
 #pragma unroll
-    for (int k = 0; k < kGradStride; k++) s_g[tid * kGradStride + k] = 0.0f;
+    for (int k = 0; k < kGradStride; k++) {
+        S[0].g[tid * kGradStride + k] = 0.0f;
+        S[1].g[tid * kGradStride + k] = 0.0f;
+    }
     __syncthreads();
     if (lane == 0) atomicMax(&s_max, warp_last);
     __syncthreads();
     const int max_last = min(s_max, (int)(range.y - range.x));
     const int B = O.batch;  // records per batch, <= kTilePix
-    for (int end = max_last; end > 0; end -= B) {
-        const int cnt = min(end, B);
-        // No barrier before staging: thread tid stages slot tid, and the
-        // flush of the previous batch touched only slot tid too (same thread).
+    const int nb = (max_last + B - 1) / B;
+    // batch bi covers list positions [end - cnt, end), end = max_last - bi B, in slot order back to front
+    auto stage = [&](int bi, BwdStage& st) {
+        const int end = max_last - bi * B, cnt = min(end, B);
         if (tid < cnt) {
             const uint32_t idx = range.x + (uint32_t)(end - 1 - tid);
             uint32_t sid = pair_vals[idx];
             if (sid >= n_splats) sid = 0;  // never produced by bin_sort; keeps the access in bounds
             const SplatView r = decode_record(rec[sid], O.ln_alpha_min);
             float4 sc;
-            stage_record<Rec>(r, s_a[tid], s_b[tid], sc);
-            s_n[tid] = make_float4(r.a, r.b, r.c, sc.x);
-            s_m[tid] = TP::splat_mask(r, O.ln_alpha_min, V, x0, y0);
-            s_sid[tid] = sid;
+            stage_record<Rec>(r, st.a[tid], st.b[tid], sc);
+            st.n[tid] = make_float4(r.a, r.b, r.c, sc.x);
+            st.m[tid] = TP::splat_mask(r, O.ln_alpha_min, V, x0, y0);
+            st.sid[tid] = sid;
         }
-        __syncthreads();
+    };
+    auto flush = [&](int bi, BwdStage& st) {
+        const int end = max_last - bi * B, cnt = min(end, B);
+        if (tid < cnt) {
+            float4* sg = reinterpret_cast<float4*>(&st.g[tid * kGradStride]);
+            const float4 m0 = sg[0];
+            float4 q1 = sg[1];
+            const float q2 = st.g[tid * kGradStride + 8];
+            // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), dx = x - u, dy = y - v
+            const float4 nc = st.n[tid];
+            const float4 q0 = make_float4(fmaf(nc.x, m0.x, nc.y * m0.y), fmaf(nc.y, m0.x, nc.z * m0.y), -0.5f * m0.z,
+                                          -m0.w);
+            q1.x = -0.5f * q1.x;
+            if (q0.x != 0.f || q0.y != 0.f || q0.z != 0.f || q0.w != 0.f || q1.x != 0.f || q1.y != 0.f ||
+                q1.z != 0.f || q1.w != 0.f || q2 != 0.f) {
+                float4* dst = grad2d + 3 * (size_t)st.sid[tid];
+                atomicAdd(dst + 0, q0);
+                atomicAdd(dst + 1, q1);
+                atomicAdd(reinterpret_cast<float*>(dst + 2), q2);
+            }
+            sg[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sg[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            st.g[tid * kGradStride + 8] = 0.0f;
+        }
+    };
+    if (nb > 0) stage(0, S[0]);
+    __syncthreads();
+    for (int bi = 0; bi < nb; bi++) {
+        BwdStage& cur = S[bi & 1];
+        BwdStage& nxt = S[(bi & 1) ^ 1];
+        // the other buffer holds batch bi - 1, which every warp finished before the last barrier
+        if (bi > 0) flush(bi - 1, nxt);
+        if (bi + 1 < nb) stage(bi + 1, nxt);
+        const int end = max_last - bi * B, cnt = min(end, B);
         // The warp walks the batch 32 slots at a time (back to front); a
         // ballot picks the slots whose splat reaches one of its sub-regions
         // and lies in front of the warp's last blended position.
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             const int jl = c0 + lane;
             const uint32_t nib =
-                (jl < cnt && end - 1 - jl < warp_last) ? (s_m[jl] >> wshift) & (uint32_t)TP::kSubAll : 0u;
+                (jl < cnt && end - 1 - jl < warp_last) ? (cur.m[jl] >> wshift) & (uint32_t)TP::kSubAll : 0u;
             uint32_t hits = __ballot_sync(F, nib != 0u);
             while (hits) {
                 const int l = __ffs(hits) - 1;
@@ -526,9 +573,9 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                 const unsigned sub = __shfl_sync(F, nib, l);
                 const int j = c0 + l;
                 const int pos = end - 1 - j;  // 0-based position in the tile list
-                const float4 a = s_a[j];
-                const float4 b = s_b[j];
-                const float cB = s_n[j].w;
+                const float4 a = cur.a[j];
+                const float4 b = cur.b[j];
+                const float cB = cur.n[j].w;
                 // sums over the warp's pixels, with g = dL/dpower:
                 //   g dx, g dy, g dx^2, g dx dy, g dy^2, dL/dalpha_eff, dL/dR, dL/dG (and dL/dB);
                 // the flush turns the first five into dL/d(u, v, a, b, c) with the splat's conic
@@ -585,33 +632,13 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                     const float tot = warp_reduce8(gv, lane);
                     const float tb = warp_sum(g_bl);
                     if ((lane & 3) == 0 || lane == 1)
-                        atomicAdd(&s_g[j * kGradStride + (lane == 1 ? 8 : lane >> 2)], lane == 1 ? tb : tot);
+                        atomicAdd(&cur.g[j * kGradStride + (lane == 1 ? 8 : lane >> 2)], lane == 1 ? tb : tot);
                 }
             }
         }
         __syncthreads();
-        if (tid < cnt) {
-            float4* sg = reinterpret_cast<float4*>(&s_g[tid * kGradStride]);
-            const float4 m0 = sg[0];
-            float4 q1 = sg[1];
-            const float q2 = s_g[tid * kGradStride + 8];
-            // power = -1/2 (a dx^2 + 2 b dx dy + c dy^2), dx = x - u, dy = y - v
-            const float4 nc = s_n[tid];
-            const float4 q0 = make_float4(fmaf(nc.x, m0.x, nc.y * m0.y), fmaf(nc.y, m0.x, nc.z * m0.y), -0.5f * m0.z,
-                                          -m0.w);
-            q1.x = -0.5f * q1.x;
-            if (q0.x != 0.f || q0.y != 0.f || q0.z != 0.f || q0.w != 0.f || q1.x != 0.f || q1.y != 0.f ||
-                q1.z != 0.f || q1.w != 0.f || q2 != 0.f) {
-                float4* dst = grad2d + 3 * (size_t)s_sid[tid];
-                atomicAdd(dst + 0, q0);
-                atomicAdd(dst + 1, q1);
-                atomicAdd(reinterpret_cast<float*>(dst + 2), q2);
-            }
-            sg[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-            sg[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-            s_g[tid * kGradStride + 8] = 0.0f;
-        }
     }
+    if (nb > 0) flush(nb - 1, S[(nb - 1) & 1]);
 }
 
 // One thread block per compositing tile: (O.bin / O.tile)^2 per binning tile.
@@ -673,18 +700,31 @@ static cudaError_t launch_bwd_tiles(const ViewSet& VS, const DevOpts& O, const S
     const auto* rech = reinterpret_cast<const SplatRecordH*>(state + lay.records);
     const uint32_t S = (uint32_t)lay.n_splats;
     const dim3 grid(blocks_for(VS, O));
-    if (O.tile == 32 && O.record_fp16)
-        render_bwd_kernel<32, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, final_T, n_last,
-                                                                       dL_dimage, g2);
-    else if (O.tile == 32)
-        render_bwd_kernel<32, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
-                                                                      dL_dimage, g2);
-    else if (O.record_fp16)
-        render_bwd_kernel<16, SplatRecordH><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rech, S, final_T, n_last,
-                                                                       dL_dimage, g2);
-    else
-        render_bwd_kernel<16, SplatRecord><<<grid, kTilePix, 0, st>>>(VS, O, ranges, pv, rec, S, final_T, n_last,
-                                                                      dL_dimage, g2);
+    // the staging buffers exceed the 48 KB of static shared memory a block gets by default
+    auto smem = [](const void* k) {
+        cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBwdSmem);
+        if (r == cudaSuccess)  // four blocks per SM need the largest shared-memory carve-out
+            r = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        return r;
+    };
+    cudaError_t e;
+    if (O.tile == 32 && O.record_fp16) {
+        if ((e = smem((const void*)render_bwd_kernel<32, SplatRecordH>)) != cudaSuccess) return e;
+        render_bwd_kernel<32, SplatRecordH><<<grid, kTilePix, kBwdSmem, st>>>(VS, O, ranges, pv, rech, S, final_T,
+                                                                              n_last, dL_dimage, g2);
+    } else if (O.tile == 32) {
+        if ((e = smem((const void*)render_bwd_kernel<32, SplatRecord>)) != cudaSuccess) return e;
+        render_bwd_kernel<32, SplatRecord><<<grid, kTilePix, kBwdSmem, st>>>(VS, O, ranges, pv, rec, S, final_T,
+                                                                             n_last, dL_dimage, g2);
+    } else if (O.record_fp16) {
+        if ((e = smem((const void*)render_bwd_kernel<16, SplatRecordH>)) != cudaSuccess) return e;
+        render_bwd_kernel<16, SplatRecordH><<<grid, kTilePix, kBwdSmem, st>>>(VS, O, ranges, pv, rech, S, final_T,
+                                                                              n_last, dL_dimage, g2);
+    } else {
+        if ((e = smem((const void*)render_bwd_kernel<16, SplatRecord>)) != cudaSuccess) return e;
+        render_bwd_kernel<16, SplatRecord><<<grid, kTilePix, kBwdSmem, st>>>(VS, O, ranges, pv, rec, S, final_T,
+                                                                             n_last, dL_dimage, g2);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
