@@ -4,13 +4,17 @@
 // batch, Eq. 7-8 (covariance from the quaternion pair), Eq. 9-10 (conditional
 // 3D Gaussian, marginal p(t) and the p(t) < p_min filter of Sec. 4.2),
 // Eq. 11 (4D spherindrical-harmonic colour) and Eq. 3-4 (EWA projection),
-// written as one 48-byte splat record per (view, Gaussian).
+// written as one splat record per (view, Gaussian) (48 bytes, or 32 with
+// 16-bit conics).  One thread per Gaussian over all views; a block stages its
+// Gaussians' 4DSH coefficients in shared memory for the views to share.
 //
-// project_backward_kernel (adjoint): for each Gaussian, sums over the views
-// the chain rule from the per-splat 2D gradient (written by the compositing
-// adjoint) back to the raw parameters.  One thread owns one Gaussian, so no
-// atomics are needed; the 4DSH coefficient gradients are accumulated in
-// shared memory (one column per thread) and written once, coalesced.
+// project_backward_kernel (adjoint): the chain rule from the per-splat 2D
+// gradient (written by the compositing adjoint) back to the raw parameters,
+// one thread per visible splat of a Gaussian-major list; the splats of one
+// Gaussian sum their contributions over the warp and its first lane runs
+// Eq. 7-8 backwards once.  sh_backward_kernel then forms the 4DSH
+// coefficient gradients, one thread per (Gaussian, channel), from the colour
+// cotangents the adjoint leaves per splat.
 #include <algorithm>
 
 #include "fgs4d_internal.cuh"
@@ -533,7 +537,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
 // consecutive Gaussians, so every load and store is coalesced.
 template <int L, int K1>
 __global__ void __launch_bounds__(256) sh_backward_kernel(int n, int n_views, float inv_period,
-                                                          const uint32_t* __restrict__ tiles_touched,
                                                           const float4* __restrict__ grad2d, float* __restrict__ gshs) {
     constexpr int NB = (L + 1) * (L + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -544,9 +547,13 @@ __global__ void __launch_bounds__(256) sh_backward_kernel(int n, int n_views, fl
     for (int f = 0; f < K1; f++)
 #pragma unroll
         for (int j = 0; j < NB; j++) acc[f][j] = 0.0f;
+    // The 2D-gradient record of every splat is zeroed before the adjoint, and
+    // only the splats it reached get a non-zero colour cotangent, so the
+    // cotangent alone says which views to take (the loads of several views
+    // are in flight together).
+#pragma unroll 4
     for (int v = 0; v < n_views; v++) {
         const size_t idx = (size_t)v * n + g;
-        if (tiles_touched[idx] == 0u) continue;
         const float4 gr = grad2d[3 * idx + 1];
         const float graw = ch == 0 ? gr.x : (ch == 1 ? gr.y : gr.z);
         if (graw == 0.0f) continue;
@@ -606,21 +613,21 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
 }
 
 template <int L, int K1>
-static void launch_sh(const DevGauss& G, int n_views, const uint32_t* tt, const float4* g2, float* gshs,
+static void launch_sh(const DevGauss& G, int n_views, const float4* g2, float* gshs,
                       cudaStream_t st) {
     const dim3 grid((G.n + 255) / 256, 3);
-    sh_backward_kernel<L, K1><<<grid, 256, 0, st>>>(G.n, n_views, G.inv_period, tt, g2, gshs);
+    sh_backward_kernel<L, K1><<<grid, 256, 0, st>>>(G.n, n_views, G.inv_period, g2, gshs);
 }
 
 template <int L>
-static void launch_sh_k(const DevGauss& G, int n_views, const uint32_t* tt, const float4* g2, float* gshs,
+static void launch_sh_k(const DevGauss& G, int n_views, const float4* g2, float* gshs,
                         cudaStream_t st) {
     switch (G.K) {
-        case 0: launch_sh<L, 1>(G, n_views, tt, g2, gshs, st); break;
-        case 1: launch_sh<L, 2>(G, n_views, tt, g2, gshs, st); break;
-        case 2: launch_sh<L, 3>(G, n_views, tt, g2, gshs, st); break;
-        case 3: launch_sh<L, 4>(G, n_views, tt, g2, gshs, st); break;
-        default: launch_sh<L, 5>(G, n_views, tt, g2, gshs, st); break;
+        case 0: launch_sh<L, 1>(G, n_views, g2, gshs, st); break;
+        case 1: launch_sh<L, 2>(G, n_views, g2, gshs, st); break;
+        case 2: launch_sh<L, 3>(G, n_views, g2, gshs, st); break;
+        case 3: launch_sh<L, 4>(G, n_views, g2, gshs, st); break;
+        default: launch_sh<L, 5>(G, n_views, g2, gshs, st); break;
     }
 }
 
@@ -658,7 +665,7 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
     const uint64_t S = (uint64_t)n * VS.n;
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((S + kBwdThreads - 1) / kBwdThreads, 16ull * sms));
     project_backward_kernel<L><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads);
-    launch_sh_k<L>(G, VS.n, tt, g2, grads.shs, st);
+    launch_sh_k<L>(G, VS.n, g2, grads.shs, st);
     count_launches(2);
     return cudaGetLastError();
 }
