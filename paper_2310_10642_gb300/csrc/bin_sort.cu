@@ -364,54 +364,87 @@ static cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], const uint32
 // Pair emission, one thread per visible splat in depth order: the thread
 // walks its splat's tile rows (the same ellipse_row_tiles calls as the
 // count, so exactly tiles[sid] pairs) and writes (tile, splat) pairs from
-// the splat's offset on.  With 64-pixel binning tiles a splat reaches ~10
+// the splat's offset on, through its warp's shared buffer.  With 64-pixel binning tiles a splat reaches ~10
 // tiles, and a warp-cooperative walk (32 lanes over one splat's box tiles,
 // ballot-packed) spent more on broadcasting each splat than on its pairs.
 // Should the rows ever disagree with the count, surplus slots get the dump
 // tile id VS.total_tiles, which no block renders.
+constexpr int kEmitStage = 512;  // pairs a warp gathers in shared memory before writing them out
+
 __global__ void __launch_bounds__(256) emit_pairs_kernel(
     const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted_splats,
     const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ tiles, const void* __restrict__ rec,
     int rec_fp16, float ln_alpha_min, uint32_t n_max, uint32_t* counters, uint32_t capacity, int tile,
     uint32_t* __restrict__ pair_keys, uint32_t* __restrict__ pair_vals) {
+    constexpr unsigned F = 0xffffffffu;
+    // A warp takes 32 consecutive splats, whose pairs fill one contiguous
+    // range of the output (their offsets are consecutive in depth order):
+    // each thread writes its splat's pairs into the warp's shared buffer, then
+    // the warp copies the range out with coalesced stores.  A range larger
+    // than the buffer is written directly.
+    __shared__ uint32_t s_key[256 / 32][kEmitStage];
+    __shared__ uint32_t s_val[256 / 32][kEmitStage];
     const uint32_t n_vis = min(counters[0], n_max);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * blockDim.x) >> 5;
     bool overflow = false;
-    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_vis; p += gridDim.x * blockDim.x) {
-        const uint32_t sid = sorted_splats[p];
-        const uint32_t cnt = tiles[sid];
-        if (cnt == 0) continue;
-        const uint32_t o = offsets[p];
-        const DevView& V = VS.v[sid / n_gauss];
-        const SplatView r = rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
-                                     : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
-        int rect[4];
-        uint32_t written = 0;
-        if (box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect) > 0) {
-            const EllipseRows e = ellipse_rows(r, ln_alpha_min);
-            for (int ty = rect[1]; ty <= rect[3]; ty++) {
-                int tx0;
-                const int nr = ellipse_row_tiles(e, V, tile, rect, ty, &tx0);
-                const uint32_t row_key = V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x + (uint32_t)tx0;
-                for (int i = 0; i < nr && written < cnt; i++, written++) {
-                    const uint32_t at = o + written;
-                    if (at >= capacity) {
-                        overflow = true;
-                    } else {
-                        pair_keys[at] = row_key + (uint32_t)i;
-                        pair_vals[at] = sid;
-                    }
+    for (uint32_t base = warp0 * 32; base < n_vis; base += n_warps * 32) {  // warp-uniform
+        const uint32_t p = base + lane;
+        uint32_t sid = 0, cnt = 0, o = 0;
+        if (p < n_vis) {
+            sid = sorted_splats[p];
+            cnt = tiles[sid];
+            o = offsets[p];
+        }
+        const uint32_t o_first = __shfl_sync(F, o, 0);
+        const uint32_t total = __shfl_sync(F, o + cnt, (int)min(31u, n_vis - 1 - base)) - o_first;
+        const bool staged = total <= (uint32_t)kEmitStage;  // warp-uniform
+        // pair number `at` of the output: into the warp's buffer (its capacity is checked on the
+        // way out), or straight to the pair arrays
+        auto put = [&](uint32_t at, uint32_t key, uint32_t val) {
+            if (staged) {
+                s_key[w][at - o_first] = key;
+                s_val[w][at - o_first] = val;
+            } else if (at >= capacity) {
+                overflow = true;
+            } else {
+                pair_keys[at] = key;
+                pair_vals[at] = val;
+            }
+        };
+        if (cnt > 0) {
+            const DevView& V = VS.v[sid / n_gauss];
+            const SplatView r = rec_fp16
+                                    ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
+                                    : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
+            int rect[4];
+            uint32_t written = 0;
+            if (box_tiles(r.u, r.v, r.hx, r.hy, V, tile, rect) > 0) {
+                const EllipseRows e = ellipse_rows(r, ln_alpha_min);
+                for (int ty = rect[1]; ty <= rect[3]; ty++) {
+                    int tx0;
+                    const int nr = ellipse_row_tiles(e, V, tile, rect, ty, &tx0);
+                    const uint32_t row_key = V.tile_base + (uint32_t)ty * (uint32_t)V.tiles_x + (uint32_t)tx0;
+                    for (int i = 0; i < nr && written < cnt; i++, written++) put(o + written, row_key + (uint32_t)i, sid);
                 }
             }
+            // the count came from the same rows, so this never runs; it keeps every slot
+            // defined (the dump tile id VS.total_tiles sorts last and no block renders it)
+            for (; written < cnt; written++) put(o + written, VS.total_tiles, sid);
         }
-        // the count came from the same rows, so this never runs; it keeps every slot defined
-        for (; written < cnt; written++) {
-            const uint32_t at = o + written;
-            if (at >= capacity) {
-                overflow = true;
-                break;
+        if (staged) {
+            __syncwarp();
+            for (uint32_t k = (uint32_t)lane; k < total; k += 32) {
+                const uint32_t at = o_first + k;
+                if (at >= capacity) {
+                    overflow = true;
+                    break;
+                }
+                pair_keys[at] = s_key[w][k];
+                pair_vals[at] = s_val[w][k];
             }
-            pair_keys[at] = VS.total_tiles;
-            pair_vals[at] = sid;
+            __syncwarp();
         }
     }
     if (overflow) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
