@@ -168,16 +168,32 @@ def test_slice_project_records_match_oracle():
         close(r[:, 9], ref["depth"][both], 1e-6, 1e-6, "depth")
 
 
+def large_splat_scene():
+    """Splats from a few pixels to most of a 320x240 view: a warp's 32
+    consecutive splats then own more pairs than its emission buffer holds."""
+    G = I.gaussians(400, 31, 3, 2, log_s_xyz=(-2.0, 1.0))
+    views = [I.view((0.2, 0.1, 4.0), 320, 240, 0.4), I.view((-1.5, 0.5, 3.5), 200, 150, 0.6)]
+    return G, views
+
+
 @TILE_BINS
-def test_tile_lists_are_depth_ordered_and_complete(tile, bin):
+@pytest.mark.parametrize("scene", ["ragged", "large"])
+def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
     """Every splat is listed in the binning tiles its support ellipse reaches
     (R7 with slack): within its support box, once per tile, as many tiles as
     slice/project counted, and in every tile holding a pixel where the
     record's own alpha (in FP64) clears alpha_min; each tile's list is in
     (depth, index) order.  The lists are per binning tile (bin x bin
-    pixels), whatever the compositing tile."""
-    G, views = ragged_scene(n=2500, seed=14)
+    pixels), whatever the compositing tile.  The two scenes take both ways
+    out of the emission: on average a warp's 32 splats own fewer pairs than
+    its 512-pair buffer (ragged) or more (large splats at 16-pixel bins)."""
+    G, views = ragged_scene(n=2500, seed=14) if scene == "ragged" else large_splat_scene()
     fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
+    per_warp = 32 * fr.last_counters.n_pairs / max(fr.last_counters.n_visible, 1)
+    if scene == "ragged":
+        assert per_warp < 512  # some warp's pairs fit its buffer
+    elif bin == 16:
+        assert per_warp > 512  # some warp's pairs overflow it and are written directly
     tile = bin  # the geometry below is that of the binning tiles
     rec, tiles, ranges, vals = read_state(fr)
     n = G["logit"].shape[0]
