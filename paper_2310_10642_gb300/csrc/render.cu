@@ -1,17 +1,18 @@
 // render.cu -- tile-based front-to-back compositing (Eq. 6) and its adjoint.
 //
-// One CTA of 256 threads per screen tile.  With 16x16 tiles each thread owns
-// one pixel; with 32x32 tiles each thread owns a 2x2 block, which amortises
-// the shared-memory reads of a splat over four pixels and cuts the number of
-// (splat, tile) pairs the binning has to sort.  Each warp owns a compact
-// region of the tile (8x4 pixels, resp. 16x8 in four 8x4 sub-regions).  The
-// tile's depth-ordered splat list is walked in batches of up to 256: each
-// thread gathers one splat record into shared memory together with a mask of
-// the 8x4 sub-regions its support box reaches; each warp then ballots over
-// the masks and visits, in list order, only the splats that reach one of its
-// own sub-regions (most splats are small next to a 32x32 tile and reach one
-// or two of its 32 sub-regions).
-// A CTA stops as soon as all its pixels have terminated (__syncthreads_count).
+// One thread block of 256 threads per compositing tile (16x16 or 32x32
+// pixels).  It walks the depth-ordered splat list of the binning tile that
+// contains it (the same tile, or a 2x2 / 4x4 group of compositing tiles).
+// With 16x16 tiles each thread owns one pixel; with 32x32 tiles each thread
+// owns four, which amortises a splat's shared-memory reads over them.  Each
+// warp owns a compact region of the tile (8x4 pixels, resp. 16x8 in four 8x4
+// sub-regions).  The list is walked in batches of up to 256: each thread
+// stages one splat record into shared memory together with a mask of the
+// tile's 8x4 sub-regions the splat can reach (its support box, narrowed by
+// its support ellipse); each warp then ballots over the masks of 32 slots at
+// a time and visits, in list order, only the splats that reach one of its
+// own sub-regions.  The forward stops a block as soon as all its pixels have
+// terminated (__syncthreads_count); the adjoint double-buffers its batches.
 //
 // Per pixel and splat (readings R4-R6):
 //   power = -1/2 (a dx^2 + c dy^2) - b dx dy, dx = x - u, dy = y - v
@@ -24,9 +25,10 @@
 // a pixel to spare), so skipping a region that lies entirely outside the box
 // takes the same decision the per-pixel test would.
 //
-// The exponent is evaluated as exp2 of a conic pre-scaled by -log2(e)/2
-// (resp. -log2(e)) with explicitly rounded operations, so the forward and the
-// adjoint take bit-identical skip decisions.
+// The exponent is evaluated as exp2 of a quadratic form pre-scaled by log2(e)
+// (the conic, or with 16-bit records its Cholesky factor), with explicitly
+// rounded operations, so the forward and the adjoint take bit-identical skip
+// decisions.
 #include "fgs4d_internal.cuh"
 
 namespace fgs4d {
