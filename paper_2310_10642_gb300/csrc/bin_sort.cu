@@ -1,14 +1,16 @@
 // bin_sort.cu -- tile binning with a depth order, on the device.
 //
-// Each tile's list must be ordered by (depth, Gaussian index) (Sec. 3.1:
-// splats are blended in depth order; ties broken by index).  Instead of one
-// radix sort of 64-bit (tile | depth) keys over all (splat, tile) pairs, the
-// pipeline sorts the visible splats once by depth and then stable-sorts the
-// pairs by tile id alone:
+// "Tile" here is a binning tile (bin_size pixels square).  Each tile's list
+// must be ordered by (depth, Gaussian index) (Sec. 3.1: splats are blended in
+// depth order; ties broken by index).  Instead of one radix sort of 64-bit
+// (tile | depth) keys over all (splat, tile) pairs, the pipeline sorts the
+// visible splats once by depth and then stable-sorts the pairs by tile id
+// alone:
 //   1. compact the visible (view, Gaussian) splats in index order
 //   2. stable LSD radix sort of the compacted splats by depth (32-bit keys)
-//   3. exclusive scan of their tile counts in depth order -> pair offsets
-//   4. emit one (global tile id, splat id) pair per touched tile
+//   3. count the tiles each visible splat's support ellipse reaches, and an
+//      exclusive scan of the counts in depth order -> pair offsets
+//   4. emit one (global tile id, splat id) pair per reached tile
 //   5. stable LSD radix sort of the pairs by tile id (only the bits in use)
 //   6. per-tile [start, end) ranges
 // Stability of both sorts makes each tile's list come out in (depth, index)
