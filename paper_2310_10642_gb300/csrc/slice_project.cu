@@ -133,8 +133,9 @@ __device__ __forceinline__ void color_adjoint(const T* __restrict__ sh, size_t n
     }
 }
 
+// 5 blocks per SM (96 registers, no spills): one more than 128 registers allow
 template <int L>
-__global__ void __launch_bounds__(kSliceThreads) slice_project_kernel(
+__global__ void __launch_bounds__(kSliceThreads, 5) slice_project_kernel(
     const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
     uint32_t* __restrict__ tiles_touched, uint32_t* __restrict__ depth_key, uint32_t* __restrict__ counters,
     float4* __restrict__ aux, int stage) {
