@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
 // channel) keeps the (K+1) (L+1)^2 sums in registers; consecutive threads take
 // consecutive Gaussians, so every load and store is coalesced.
 template <int L, int K1>
-__global__ void __launch_bounds__(256) sh_backward_kernel(int n, int n_views, float inv_period,
+__global__ void __launch_bounds__(256, 4) sh_backward_kernel(int n, int n_views, float inv_period,
                                                           const float4* __restrict__ grad2d, float* __restrict__ gshs) {
     constexpr int NB = (L + 1) * (L + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
