@@ -150,6 +150,7 @@ fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int aux,
     L->ranges = take((size_t)VS.total_tiles * 8);
     L->grad2d = take(s * 48);
     L->aux = aux ? take(s * 16) : 0;
+    L->gsum = take((size_t)n * 11 * sizeof(float));
     L->fixed_bytes = off;
     if (capacity < 0) {
         if (state_bytes < L->fixed_bytes) return FGS4D_ERR_CAPACITY;

@@ -83,6 +83,7 @@ struct StateLayout {
     size_t ranges;         // uint2[total_tiles]
     size_t grad2d;         // float4[3 * V*n] per-splat 2D gradient
     size_t aux;            // float4[V*n] depth, flow u, flow v (0 when aux channels are off)
+    size_t gsum;           // float[11][n] per-Gaussian sums of the projection adjoint
     size_t pair_keys[2];   // uint32[capacity] double buffer
     size_t pair_vals[2];   // uint32[capacity]
     size_t fixed_bytes;    // everything above except the pair buffers

@@ -246,10 +246,101 @@ __device__ __forceinline__ float segment_sum(float x, int lane, int seg_last) {
 // replaced by its colour cotangent, read by sh_backward_kernel:
 //   slot[0] = (view direction d, dt),  slot[1] = (dL/draw_R, dL/draw_G, dL/draw_B, 0)
 // where dL/draw is dL/dcolour with the colour clamp max(raw + 0.5, 0) applied.
-template <int L>
+// Eq. 7-8 backwards for one Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r)
+// (or blockdiag(R3(q_l), 1) without 4D rotation).  GS: dL/dSigma with its
+// upper triangle filled (symmetrised here); galpha: dL/dsigmoid(logit).
+// Writes the gradients of log s, q_l, q_r and the opacity logit.
+__device__ __forceinline__ void covariance_chain(const DevGauss& G, const Core& cl, float* GS, float galpha,
+                                                 float* gls, float* gql, float* gqr, float& glogit) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) gls[i] = gql[i] = gqr[i] = 0.0f;
+    // symmetrise the accumulator (only the upper triangle was written)
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
+    float dR[16];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], cl.M[j * 4 + k], acc);
+            const float dM = 2.0f * acc;
+            dR[i * 4 + k] = dM * cl.s[k];
+            gls[k] = fmaf(dM, cl.R[i * 4 + k], gls[k]);
+        }
+#pragma unroll
+    for (int k = 0; k < 4; k++) gls[k] *= cl.s[k];
+    if (G.rot3) {
+        // R = blockdiag(R3(q), 1): dL/dq through the 3x3 block, then the normalisation
+        const float w = cl.qln[0], x = cl.qln[1], y = cl.qln[2], z = cl.qln[3];
+        const float* d = dR;
+        const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[4] - x * d[6] - y * d[8] + x * d[9]);
+        const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[4] - 2.0f * x * d[5] - w * d[6] + z * d[8] +
+                                 w * d[9] - 2.0f * x * d[10]);
+        const float gy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[4] + z * d[6] - w * d[8] +
+                                 z * d[9] - 2.0f * y * d[10]);
+        const float gz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[4] - 2.0f * z * d[5] +
+                                 y * d[6] + x * d[8] + y * d[9]);
+        const float gq[4] = {gw, gx, gy, gz};
+        float dq = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; i++) dq = fmaf(gq[i], cl.qln[i], dq);
+#pragma unroll
+        for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * cl.qln[i]) / cl.nl;
+    } else {
+        float Lm[16], Rm[16];
+        left_matrix(cl.qln, Lm);
+        right_matrix(cl.qrn, Rm);
+        float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float x = 0.0f, y = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
+                    y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
+                }
+                D[i * 4 + j] = x;
+                E[i * 4 + j] = y;
+            }
+        const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
+                             -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
+        const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
+                             -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
+        float dl = 0.0f, dr = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            dl = fmaf(gl[i], cl.qln[i], dl);
+            dr = fmaf(gr[i], cl.qrn[i], dr);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            gql[i] = (gl[i] - dl * cl.qln[i]) / cl.nl;
+            gqr[i] = (gr[i] - dr * cl.qrn[i]) / cl.nr;
+        }
+    }
+    glogit = galpha * cl.alpha * (1.0f - cl.alpha);
+}
+
+// Rows of the per-Gaussian scratch the deferred chain reads: the ten upper
+// entries of dL/dSigma (row i of kGsumEntry: Sigma element index) and
+// dL/dsigmoid(logit) in row 10.
+constexpr int kGsumRows = 11;
+__device__ constexpr int kGsumEntry[10] = {0, 1, 2, 3, 5, 6, 7, 10, 11, 15};
+
+// kDefer: add the per-Gaussian sums to gsum ([kGsumRows][n], zeroed) and
+// leave Eq. 7-8 to covariance_chain_kernel; else each segment's first lane
+// runs it (gsum unused).
+template <int L, bool kDefer>
 __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
     const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, float4* __restrict__ grad2d,
-    const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count, const fgs4d_gaussian_grads out) {
+    const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count, const fgs4d_gaussian_grads out,
+    float* __restrict__ gsum) {
     constexpr int NB = (L + 1) * (L + 1);
     const uint32_t count = *list_count;
     const int lane = threadIdx.x & 31;
@@ -434,6 +525,18 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         m2d = segment_sum(m2d, lane, seg_last);
         mt = segment_sum(mt, lane, seg_last);
         if (!(active && c.ok && lane == seg_first)) continue;
+        if constexpr (kDefer) {
+            // add the segment's sums; Eq. 7-8 runs once per Gaussian, with every lane busy, in
+            // covariance_chain_kernel (the sums of a Gaussian split over two warps add up there)
+#pragma unroll
+            for (int i = 0; i < 10; i++) atomicAdd(&gsum[i * n + g], GS[kGsumEntry[i]]);
+            atomicAdd(&gsum[10 * n + g], galpha);
+#pragma unroll
+            for (int i = 0; i < 4; i++) atomicAdd(&out.mu[i * n + g], gmu[i]);
+            if (out.mean2d_abs) atomicAdd(&out.mean2d_abs[g], m2d);
+            if (out.mu_t_abs) atomicAdd(&out.mu_t_abs[g], mt);
+            continue;  // the rest is not compiled into this instance
+        }
         // The leader rebuilds the rotation chain from the parameters, so that R, M and the
         // quaternions are not live across the per-splat part above.
         Core cl;
@@ -442,77 +545,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
         float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
         if (c.ok) {
-            // symmetrise the accumulator (only the upper triangle was written)
-    #pragma unroll
-            for (int i = 0; i < 4; i++)
-    #pragma unroll
-                for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
-            float dR[16];
-    #pragma unroll
-            for (int i = 0; i < 4; i++)
-    #pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    float acc = 0.0f;
-    #pragma unroll
-                    for (int j = 0; j < 4; j++) acc = fmaf(GS[i * 4 + j], cl.M[j * 4 + k], acc);
-                    const float dM = 2.0f * acc;
-                    dR[i * 4 + k] = dM * cl.s[k];
-                    gls[k] = fmaf(dM, cl.R[i * 4 + k], gls[k]);
-                }
-    #pragma unroll
-            for (int k = 0; k < 4; k++) gls[k] *= cl.s[k];
-            if (G.rot3) {
-                // R = blockdiag(R3(q), 1): dL/dq through the 3x3 block, then the normalisation
-                const float w = cl.qln[0], x = cl.qln[1], y = cl.qln[2], z = cl.qln[3];
-                const float* d = dR;
-                const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[4] - x * d[6] - y * d[8] + x * d[9]);
-                const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[4] - 2.0f * x * d[5] - w * d[6] + z * d[8] +
-                                         w * d[9] - 2.0f * x * d[10]);
-                const float gy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[4] + z * d[6] - w * d[8] +
-                                         z * d[9] - 2.0f * y * d[10]);
-                const float gz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[4] - 2.0f * z * d[5] +
-                                         y * d[6] + x * d[8] + y * d[9]);
-                const float gq[4] = {gw, gx, gy, gz};
-                float dq = 0.0f;
-#pragma unroll
-                for (int i = 0; i < 4; i++) dq = fmaf(gq[i], cl.qln[i], dq);
-#pragma unroll
-                for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * cl.qln[i]) / cl.nl;
-            } else {
-            float Lm[16], Rm[16];
-            left_matrix(cl.qln, Lm);
-            right_matrix(cl.qrn, Rm);
-            float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
-    #pragma unroll
-            for (int i = 0; i < 4; i++)
-    #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    float x = 0.0f, y = 0.0f;
-    #pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
-                        y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
-                    }
-                    D[i * 4 + j] = x;
-                    E[i * 4 + j] = y;
-                }
-            const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
-                                 -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
-            const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
-                                 -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
-            float dl = 0.0f, dr = 0.0f;
-    #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                dl = fmaf(gl[i], cl.qln[i], dl);
-                dr = fmaf(gr[i], cl.qrn[i], dr);
-            }
-    #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                gql[i] = (gl[i] - dl * cl.qln[i]) / cl.nl;
-                gqr[i] = (gr[i] - dr * cl.qrn[i]) / cl.nr;
-            }
-            }
-            glogit = galpha * cl.alpha * (1.0f - cl.alpha);
+            covariance_chain(G, cl, GS, galpha, gls, gql, gqr, glogit);
         } else {
     #pragma unroll
             for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
@@ -529,6 +562,37 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         if (out.mean2d_abs) atomicAdd(&out.mean2d_abs[g], m2d);
         if (out.mu_t_abs) atomicAdd(&out.mu_t_abs[g], mt);
     }
+}
+
+// Eq. 7-8 backwards, one thread per Gaussian, from the sums the projection
+// adjoint left in gsum (all zero: no visible splat, gradients stay zero).
+// The outputs were zeroed and each Gaussian has one thread: plain stores.
+__global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G, const float* __restrict__ gsum,
+                                                               const fgs4d_gaussian_grads out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G.n) return;
+    const size_t n = (size_t)G.n;
+    float GS[16];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 10; i++) {
+        GS[kGsumEntry[i]] = gsum[i * n + g];
+        any = any || GS[kGsumEntry[i]] != 0.0f;
+    }
+    const float galpha = gsum[10 * n + g];
+    if (!any && galpha == 0.0f) return;
+    Core cl;
+    load_core(G, g, cl);
+    if (!cl.ok) return;
+    float gls[4], gql[4], gqr[4], glogit;
+    covariance_chain(G, cl, GS, galpha, gls, gql, gqr, glogit);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        out.log_scale[i * n + g] = gls[i];
+        out.q_left[i * n + g] = gql[i];
+        if (!G.rot3) out.q_right[i * n + g] = gqr[i];
+    }
+    out.opacity_logit[g] = glogit;
 }
 
 // Coefficient part of the adjoint (Eq. 11): dL/dk[f][j][ch] = sum over the
@@ -650,7 +714,7 @@ static int local_sm_count() {
 // then the coefficient kernel.
 template <int L>
 static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt, float4* g2,
-                            uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp,
+                            uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp, float* gsum,
                             const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     const size_t n = (size_t)G.n;
     cudaError_t e = cudaSuccess;
@@ -659,26 +723,34 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
     for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaMemsetAsync(outs[i], 0, rows[i] * n * sizeof(float), st);
     if (e == cudaSuccess && grads.mean2d_abs) e = cudaMemsetAsync(grads.mean2d_abs, 0, n * sizeof(float), st);
     if (e == cudaSuccess && grads.mu_t_abs) e = cudaMemsetAsync(grads.mu_t_abs, 0, n * sizeof(float), st);
+    if (e == cudaSuccess && gsum) e = cudaMemsetAsync(gsum, 0, kGsumRows * n * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const int sms = local_sm_count();
     e = compact_visible_gaussian_major(tt, (uint32_t)n, (uint32_t)VS.n, list, list_count, scan_tmp, sms, st);
     if (e != cudaSuccess) return e;
     const uint64_t S = (uint64_t)n * VS.n;
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((S + kBwdThreads - 1) / kBwdThreads, 16ull * sms));
-    project_backward_kernel<L><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads);
+    if (gsum) {
+        project_backward_kernel<L, true><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, gsum);
+        covariance_chain_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, gsum, grads);
+        count_launches(1);
+    } else {
+        project_backward_kernel<L, false>
+            <<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, nullptr);
+    }
     launch_sh_k<L>(G, VS.n, g2, grads.shs, st);
     count_launches(2);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_pb_any(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
-                                 float4* g2, uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp,
+                                 float4* g2, uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp, float* gsum,
                                  const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     switch (G.L) {
-        case 0: return launch_pb<0>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
-        case 1: return launch_pb<1>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
-        case 2: return launch_pb<2>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
-        default: return launch_pb<3>(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+        case 0: return launch_pb<0>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
+        case 1: return launch_pb<1>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
+        case 2: return launch_pb<2>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
+        default: return launch_pb<3>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
     }
 }
 
@@ -692,7 +764,8 @@ cudaError_t launch_project_backward(const DevGauss& G, const ViewSet& VS, const 
     auto* list = reinterpret_cast<uint32_t*>(state + lay.offsets);
     auto* cnt = reinterpret_cast<uint32_t*>(state + lay.counters) + 4;
     auto* scan_tmp = reinterpret_cast<uint32_t*>(state + lay.scan_tmp);
-    return launch_pb_any(G, VS, O, tt, g2, list, cnt, scan_tmp, grads, st);
+    auto* gsum = reinterpret_cast<float*>(state + lay.gsum);
+    return launch_pb_any(G, VS, O, tt, g2, list, cnt, scan_tmp, gsum, grads, st);
 }
 
 // Same as launch_project_backward with the per-splat 2D gradient, the list,
@@ -704,7 +777,8 @@ cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, c
                                          const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     if (G.n == 0) return cudaSuccess;
     auto* tt = reinterpret_cast<const uint32_t*>(state + lay.tiles_touched);
-    return launch_pb_any(G, VS, O, tt, g2, list, list_count, scan_tmp, grads, st);
+    // the state is input only on this path: each segment's first lane runs Eq. 7-8 itself
+    return launch_pb_any(G, VS, O, tt, g2, list, list_count, scan_tmp, nullptr, grads, st);
 }
 
 // Split sampling in 4D (Sec. 3.4): new means drawn from a Gaussian's own 4D
