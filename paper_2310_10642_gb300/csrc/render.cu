@@ -561,6 +561,9 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
         if (bi > 0) flush(bi - 1, nxt);
         if (bi + 1 < nb) stage(bi + 1, nxt);
         const int end = max_last - bi * B, cnt = min(end, B);
+        // a reduced visit waiting for a second one to share its last reduction and atomic
+        int pend_j = -1;
+        float pend_tot = 0.0f, pend_9 = 0.0f;
         // The warp walks the batch 32 slots at a time (back to front); a
         // ballot picks the slots whose splat reaches one of its sub-regions
         // and lies in front of the warp's last blended position.
@@ -629,14 +632,37 @@ __global__ void __launch_bounds__(kTilePix, 4) render_bwd_kernel(
                     }
                 }
                 if (__any_sync(F, contrib)) {
-                    // lane 4i holds the warp total of value i; lane 1 (a copy of value 0's)
-                    // carries the ninth, so one shared atomic instruction adds all nine
+                    // lanes 4i..4i+3 hold the warp total of value i
                     const float tot = warp_reduce8(gv, lane);
-                    const float tb = warp_sum(g_bl);
-                    if ((lane & 3) == 0 || lane == 1)
-                        atomicAdd(&cur.g[j * kGradStride + (lane == 1 ? 8 : lane >> 2)], lane == 1 ? tb : tot);
+                    if (pend_j < 0) {
+                        pend_j = j;
+                        pend_tot = tot;
+                        pend_9 = g_bl;
+                    } else {
+                        // Two visits share the ninth values' reduction (lanes with bit 1 end
+                        // with this visit's, the others with the pending one's) and one shared
+                        // atomic instruction: lane 4i adds the pending visit's value i, lane
+                        // 4i + 2 this visit's, lanes 1 and 3 the two ninth values.
+                        const bool h1 = lane & 2;
+                        float n9 = (h1 ? g_bl : pend_9) + __shfl_xor_sync(F, h1 ? pend_9 : g_bl, 2);
+                        n9 += __shfl_xor_sync(F, n9, 16);
+                        n9 += __shfl_xor_sync(F, n9, 8);
+                        n9 += __shfl_xor_sync(F, n9, 4);
+                        n9 += __shfl_xor_sync(F, n9, 1);
+                        const bool odd = lane & 1;
+                        if (!odd || lane < 4)
+                            atomicAdd(&cur.g[(h1 ? j : pend_j) * kGradStride + (odd ? 8 : lane >> 2)],
+                                      odd ? n9 : (h1 ? tot : pend_tot));
+                        pend_j = -1;
+                    }
                 }
             }
+        }
+        if (pend_j >= 0) {  // a visit left without a partner: its ninth value alone (lane 1 adds it)
+            const float tb = warp_sum(pend_9);
+            if ((lane & 3) == 0 || lane == 1)
+                atomicAdd(&cur.g[pend_j * kGradStride + (lane == 1 ? 8 : lane >> 2)], lane == 1 ? tb : pend_tot);
+            pend_j = -1;
         }
         __syncthreads();
     }
