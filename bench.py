@@ -39,7 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(workload="4dgs-render-fwd+bwd", gaussians=1_000_000, clustered=True, sh_degree=3, n_freq=2,
-                views=20, width=1352, height=1014, frames=300, config_index=3)
+                views=20, width=1352, height=1014, frames=300)
 
 
 def parse():
@@ -228,8 +228,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU arm
 TRAIN_WORKLOAD = dict(workload="4dgs-train-step", gaussians=3_000_000, clustered=True, sh_degree=3, n_freq=2,
-                      views="4 x 1352x1014 + 4 x 800x800", loss="0.8 L1 + 0.2 (1 - SSIM)", optimizer="Adam",
-                      config_index=4)
+                      views="4 x 1352x1014 + 4 x 800x800", loss="0.8 L1 + 0.2 (1 - SSIM)", optimizer="Adam")
 
 
 def main_train(args):
