@@ -1,0 +1,71 @@
+"""bench.py's host logic without a GPU: the reference arm's JSON line (the
+FP64 oracle timed on the host cores), rank handling under torchrun, the
+whole-job throughput over ranks, and the DRAM-traffic line read from the
+committed ncu summary of the dominant kernel."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _run(args, env_extra=None):
+    env = dict(os.environ, **(env_extra or {}))
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                          env=env, cwd=ROOT, timeout=300)
+
+
+def test_reference_arm_prints_one_contract_line():
+    # a tiny cut of the workload (the line's keys do not depend on its size)
+    r = _run(["--impl", "reference", "--n", "2000", "--views", "1", "--steps", "2", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["higher_is_better"] is True
+    assert d["unit"] == "Mpix/s" and d["vs_baseline"] is None
+    assert d["config"]["workload"] == bench.WORKLOAD["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == dict(value=d["value"], unit=d["unit"], h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    assert d["gpu_launches"] == 0
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    r = _run(["--impl", "reference", "--n", "2000", "--views", "1", "--steps", "1"],
+             env_extra=dict(RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
+
+
+def test_job_throughput_counts_all_ranks_over_the_slowest():
+    # one process: pixels x steps over the timed region
+    v, ms = bench.job_throughput(1_000_000, 10, 20.0)
+    assert ms == 20.0
+    assert v == pytest.approx(1_000_000 * 10 / 0.020 / 1e6)
+
+
+def test_traffic_line_follows_the_kernel_sources(monkeypatch):
+    got, note = bench.profiled_traffic("render_backward_2d")
+    text = open(os.path.join(ROOT, "profiles", bench.STAGE_PROFILE["render_backward_2d"])).read()
+    assert "sources_sha1:" in text and "dram_bytes_per_launch_full_workload:" in text
+    if got is not None:  # the committed summary was taken on the current sources
+        assert got > 0 and "capture" in note
+    else:
+        assert "stale" in note
+    # any change to the hashed sources makes the line stale, so it is not reported
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", bench.KERNEL_SOURCES + ("bench.py",))
+    got2, note2 = bench.profiled_traffic("render_backward_2d")
+    assert got2 is None and "stale" in note2
+    assert bench.profiled_traffic("slice_project") == (None, "no ncu summary for this kernel")
