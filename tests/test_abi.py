@@ -1,4 +1,5 @@
-"""The C-ABI library loads, exports every function include/*.h declares, and
+"""The C-ABI library loads, exports every function include/*.h declares, the
+binding's ctypes structures have the header's layout, and
 rejects bad arguments on the host (no GPU needed for any of this)."""
 import ctypes
 import glob
@@ -118,3 +119,41 @@ def test_invalid_arguments_rejected_on_host(lib):
     # work counters: null and misaligned stats are rejected
     assert lib.fgs4d_render_stats(10, v, 2, ctypes.byref(o), 256, 1 << 30, 256, 512, 768, None, None) == 1
     assert lib.fgs4d_render_stats(10, v, 2, ctypes.byref(o), 256, 1 << 30, 256, 512, 768, 1028, None) == 1
+
+
+# ctypes mirror of each header struct: (binding class, C type name)
+STRUCTS = [("Gaussians", "fgs4d_gaussians"), ("View", "fgs4d_view"), ("Options", "fgs4d_options"),
+           ("GaussianGrads", "fgs4d_gaussian_grads"), ("Counters", "fgs4d_counters"),
+           ("AdamGroup", "fgs4d_adam_group"), ("StateLayoutInfo", "fgs4d_state_layout_info")]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size, field names and
+    field offsets that a C compiler gives the header's struct (compiled here
+    with the host gcc; the header is plain C)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fgs4d.h"', "int main(void) {"]
+    for cls, ctype in STRUCTS:
+        lines.append(f'  printf("{cls} size %zu\\n", sizeof({ctype}));')
+        for name, _ in getattr(N, cls)._fields_:
+            lines.append(f'  printf("{cls} {name} %zu\\n", offsetof({ctype}, {name}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        cls, name, val = line.split()
+        got[(cls, name)] = int(val)
+    for cls, ctype in STRUCTS:
+        s = getattr(N, cls)
+        assert ctypes.sizeof(s) == got[(cls, "size")], (cls, ctypes.sizeof(s), got[(cls, "size")])
+        for name, _ in s._fields_:
+            assert getattr(s, name).offset == got[(cls, name)], (cls, name)
