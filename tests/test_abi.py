@@ -127,10 +127,18 @@ STRUCTS = [("Gaussians", "fgs4d_gaussians"), ("View", "fgs4d_view"), ("Options",
            ("AdamGroup", "fgs4d_adam_group"), ("StateLayoutInfo", "fgs4d_state_layout_info")]
 
 
+# binding constants mirroring the header's: (name in native.py, C expression)
+CONSTANTS = [("MAX_VIEWS", "FGS4D_MAX_VIEWS"), ("TILE", "FGS4D_TILE"), ("F32", "FGS4D_F32"), ("BF16", "FGS4D_BF16"),
+             ("ROT_4D", "FGS4D_ROT_4D"), ("ROT_SPATIAL", "FGS4D_ROT_SPATIAL"),
+             ("STATUS_PAIR_OVERFLOW", "FGS4D_STATUS_PAIR_OVERFLOW"), ("STATUS_NONFINITE", "FGS4D_STATUS_NONFINITE"),
+             ("NOALLOC_MAX_SPLATS", "FGS4D_NOALLOC_MAX_SPLATS")]
+
+
 def test_binding_structs_match_the_header_layout(tmp_path):
     """Every ctypes structure of the binding has the size, field names and
-    field offsets that a C compiler gives the header's struct (compiled here
-    with the host gcc; the header is plain C)."""
+    field offsets that a C compiler gives the header's struct, and the
+    binding's constants the header's values (compiled here with the host
+    gcc; the header is plain C)."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -141,6 +149,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         lines.append(f'  printf("{cls} size %zu\\n", sizeof({ctype}));')
         for name, _ in getattr(N, cls)._fields_:
             lines.append(f'  printf("{cls} {name} %zu\\n", offsetof({ctype}, {name}));')
+    for py, c in CONSTANTS:
+        lines.append(f'  printf("const {py} %lld\\n", (long long)({c}));')
     lines += ["  return 0;", "}"]
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
@@ -152,6 +162,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
         cls, name, val = line.split()
         got[(cls, name)] = int(val)
+    for py, c in CONSTANTS:
+        assert getattr(N, py) == got[("const", py)], (py, c)
     for cls, ctype in STRUCTS:
         s = getattr(N, cls)
         assert ctypes.sizeof(s) == got[(cls, "size")], (cls, ctypes.sizeof(s), got[(cls, "size")])
