@@ -12,7 +12,6 @@ in the backward kernels rather than stored per splat.
 """
 from __future__ import annotations
 
-
 import torch
 
 from . import native as N
