@@ -305,23 +305,27 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view *views, int n_views,
 
 /* fgs4d_render_backward without caller-provided scratch.  The paper has no
    counterpart: this is an interface for callers that cannot call cudaMalloc
-   when they run the backward pass, e.g. code whose stream is being captured
-   into a CUDA graph, real-time loops that reserve all device memory once at
-   start-up, or plugins of an engine that owns the device allocator.
-   Same arguments, results and tolerance as fgs4d_render_backward; the
-   forward state is read as input but its per-splat gradient section is not
-   used.  That scratch (48 bytes per (view, Gaussian) splat) lives instead in
-   a static device array of the library, 13 MiB, which every GPU that loads
-   the library holds until the process exits:
+   when they run the backward pass, e.g. real-time loops that reserve all
+   device memory once at start-up and may not allocate afterwards, or plugins
+   hosted by an engine that owns the device allocator and forbids allocations
+   of its own.  Same arguments, results and tolerance as
+   fgs4d_render_backward; the forward state is read as input but its
+   per-splat gradient section is not used.  That scratch (48 bytes per (view,
+   Gaussian) splat, plus the list of visible splats) lives instead in a
+   static device array of the library, 13 MiB, which every GPU that loads the
+   library holds until the process exits:
    - n * n_views above FGS4D_NOALLOC_MAX_SPLATS returns FGS4D_ERR_CAPACITY
      before anything is enqueued;
    - the first call on a device looks up the array's device address (once per
      device, with that device current); make that first call before any
      stream capture;
+   - the looked-up address is kept for the life of the process: calls after
+     cudaDeviceReset() (or any other teardown of the device's primary
+     context) are not supported;
    - every call clears the part of the array it uses, then reuses it: calls
      that overlap on the GPU (other streams, other threads) race on it and
      must be serialised by the caller;
-   - nothing is allocated or freed. */
+   - nothing is allocated or freed, on the device or on the host. */
 fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians *g, const fgs4d_view *views, int n_views,
                                            const fgs4d_options *opt, void *state, size_t state_bytes,
                                            const float *final_T, const int32_t *n_last, const float *dL_dimage,

@@ -283,11 +283,10 @@ fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view* views, int n_views, i
     if (!bytes || pair_capacity < 0 || pair_capacity > 0xffffffffll) return FGS4D_ERR_INVALID_ARG;
     fgs4d_status s = check_options(opt);
     if (s != FGS4D_OK) return s;
-    ViewSet* VS = new ViewSet;
-    s = make_views(views, n_views, opt, VS);
+    ViewSet VS;
+    s = make_views(views, n_views, opt, &VS);
     StateLayout L;
-    if (s == FGS4D_OK) s = make_layout(n, *VS, opt->record_fp16, opt->aux_channels, pair_capacity, 0, &L);
-    delete VS;
+    if (s == FGS4D_OK) s = make_layout(n, VS, opt->record_fp16, opt->aux_channels, pair_capacity, 0, &L);
     if (s != FGS4D_OK) return s;
     *bytes = L.total;
     return FGS4D_OK;
@@ -298,7 +297,8 @@ fgs4d_status fgs4d_slice_project(const fgs4d_gaussians* g, const fgs4d_view* vie
     DevGauss G;
     fgs4d_status s = check_gaussians(g, &G);
     if (s != FGS4D_OK) return s;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK) {
         char* st = static_cast<char*>(state);
@@ -306,20 +306,19 @@ fgs4d_status fgs4d_slice_project(const fgs4d_gaussians* g, const fgs4d_view* vie
                                              (cudaStream_t)stream);
         s = cuda_status(e);
     }
-    delete P;
     return s;
 }
 
 fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
                             size_t state_bytes, fgs4d_stream stream) {
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK) {
         int buf = 0;
         s = cuda_status(launch_bin_sort(P->VS, P->O, P->L, static_cast<char*>(state), sm_count_cached(),
                                         (cudaStream_t)stream, &buf));
     }
-    delete P;
     return s;
 }
 
@@ -332,12 +331,12 @@ fgs4d_status fgs4d_render(int64_t n, const fgs4d_view* views, int n_views, const
                           size_t state_bytes, float* image, float* final_T, int32_t* n_last, fgs4d_stream stream) {
     if (!image || !final_T || !n_last) return FGS4D_ERR_INVALID_ARG;
     if (!aligned(image, 4) || !aligned(final_T, 4) || !aligned(n_last, 4)) return FGS4D_ERR_INVALID_ARG;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK)
         s = cuda_status(launch_render(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), image, final_T,
                                       n_last, (cudaStream_t)stream));
-    delete P;
     return s;
 }
 
@@ -354,12 +353,12 @@ fgs4d_status fgs4d_sample_split(const fgs4d_gaussians* g, const int64_t* index, 
 fgs4d_status fgs4d_render_aux(int64_t n, const fgs4d_view* views, int n_views, const fgs4d_options* opt, void* state,
                               size_t state_bytes, float* aux_image, fgs4d_stream stream) {
     if (!aux_image || !aligned(aux_image, 4) || !opt || opt->aux_channels != 1) return FGS4D_ERR_INVALID_ARG;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK)
         s = cuda_status(launch_render_aux(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), aux_image,
                                           (cudaStream_t)stream));
-    delete P;
     return s;
 }
 
@@ -369,13 +368,13 @@ fgs4d_status fgs4d_render_stats(int64_t n, const fgs4d_view* views, int n_views,
     if (!image || !final_T || !n_last || !stats) return FGS4D_ERR_INVALID_ARG;
     if (!aligned(image, 4) || !aligned(final_T, 4) || !aligned(n_last, 4) || !aligned(stats, 8))
         return FGS4D_ERR_INVALID_ARG;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK)
         s = cuda_status(launch_render_stats(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), image,
                                             final_T, n_last, reinterpret_cast<unsigned long long*>(stats),
                                             (cudaStream_t)stream));
-    delete P;
     return s;
 }
 
@@ -399,7 +398,8 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* v
     if (s != FGS4D_OK) return s;
     if (!final_T || !n_last || !dL_dimage) return FGS4D_ERR_INVALID_ARG;
     if ((s = check_grads(g, grads)) != FGS4D_OK) return s;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK) {
         char* st = static_cast<char*>(state);
@@ -408,7 +408,6 @@ fgs4d_status fgs4d_render_backward(const fgs4d_gaussians* g, const fgs4d_view* v
         if (e == cudaSuccess) e = launch_project_backward(G, P->VS, P->O, P->L, st, *grads, (cudaStream_t)stream);
         s = cuda_status(e);
     }
-    delete P;
     return s;
 }
 
@@ -417,12 +416,12 @@ fgs4d_status fgs4d_render_backward_2d(int64_t n, const fgs4d_view* views, int n_
                                       const float* dL_dimage, fgs4d_stream stream) {
     if (!final_T || !n_last || !dL_dimage) return FGS4D_ERR_INVALID_ARG;
     if (!aligned(final_T, 4) || !aligned(n_last, 4) || !aligned(dL_dimage, 4)) return FGS4D_ERR_INVALID_ARG;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     fgs4d_status s = prepare(n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK)
         s = cuda_status(launch_render_backward(P->VS, P->O, P->L, static_cast<char*>(state), pair_buffer(*P), final_T,
                                                n_last, dL_dimage, (cudaStream_t)stream));
-    delete P;
     return s;
 }
 
@@ -433,12 +432,12 @@ fgs4d_status fgs4d_project_backward(const fgs4d_gaussians* g, const fgs4d_view* 
     fgs4d_status s = check_gaussians(g, &G);
     if (s != FGS4D_OK) return s;
     if ((s = check_grads(g, grads)) != FGS4D_OK) return s;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK)
         s = cuda_status(launch_project_backward(G, P->VS, P->O, P->L, static_cast<char*>(state), *grads,
                                                 (cudaStream_t)stream));
-    delete P;
     return s;
 }
 
@@ -447,7 +446,8 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views,
     if (!out) return FGS4D_ERR_INVALID_ARG;
     fgs4d_status s = check_options(opt);
     if (s != FGS4D_OK) return s;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     s = make_views(views, n_views, opt, &P->VS);
     if (s == FGS4D_OK) s = make_layout(n, P->VS, opt->record_fp16, opt->aux_channels, -1, state_bytes, &P->L);
     if (s == FGS4D_OK) {
@@ -462,7 +462,6 @@ fgs4d_status fgs4d_state_layout(int64_t n, const fgs4d_view* views, int n_views,
         out->pair_capacity = (uint64_t)P->L.capacity;
         out->grad2d = P->L.grad2d;
     }
-    delete P;
     return s;
 }
 
@@ -485,16 +484,16 @@ fgs4d_status fgs4d_read_counters(const void* state, fgs4d_counters* out, fgs4d_s
 // fgs4d_render_backward_noalloc: the backward pass without caller scratch.
 //
 // Some callers cannot call cudaMalloc at the moment they need the backward
-// pass: code running while its stream is being captured into a CUDA graph,
-// real-time render loops that reserve every byte of device memory once at
-// start-up and forbid later allocations, and plugins hosted by an engine
+// pass: real-time render loops that reserve every byte of device memory once
+// at start-up and forbid later allocations, and plugins hosted by an engine
 // that owns the device allocator.  This entry point keeps its scratch -- the
 // per-splat 2D gradient (three float4 per (view, Gaussian) splat), the list
 // of visible splats (one word per splat), its length and the scan's block
 // sums -- in a static device array of this library instead of the caller's
 // state.  The state from the forward pass is only read.  The array holds
 // FGS4D_NOALLOC_MAX_SPLATS splats (13 MiB) and every GPU that loads this
-// library keeps it until the process exits.
+// library keeps it until the process exits.  The host side allocates
+// nothing either: the per-call view set and layout live on the stack.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -546,7 +545,8 @@ extern "C" fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians* g, 
             if (!p || !aligned(p, 4)) return FGS4D_ERR_INVALID_ARG;
     }
     if (n_views >= 1 && g->n * (int64_t)n_views > (int64_t)FGS4D_NOALLOC_MAX_SPLATS) return FGS4D_ERR_CAPACITY;
-    Prepared* P = new Prepared;
+    Prepared prep;
+    Prepared* P = &prep;
     s = prepare(g->n, views, n_views, opt, state, state_bytes, P);
     if (s == FGS4D_OK) {
         float4* g2 = nullptr;
@@ -562,6 +562,5 @@ extern "C" fgs4d_status fgs4d_render_backward_noalloc(const fgs4d_gaussians* g, 
                                              *grads, (cudaStream_t)stream);
         s = cuda_status(e);
     }
-    delete P;
     return s;
 }

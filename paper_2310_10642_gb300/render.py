@@ -137,10 +137,18 @@ class Frame:
     def counters(self, stream=None) -> N.Counters:
         return N.fgs4d_read_counters(self.state.data_ptr(), _stream(stream))
 
-    def forward(self, params: dict, stream=None, check: bool = True) -> torch.Tensor:
-        """slice_project -> bin_sort -> render.  With check=True, reads the
-        device counters (one synchronisation) and re-runs with a larger pair
-        capacity on overflow."""
+    def forward(self, params: dict, stream=None, check=True) -> torch.Tensor:
+        """slice_project -> bin_sort -> render.
+
+        check=True: reads the device counters (one synchronisation) and
+        re-runs with a larger pair capacity on overflow.  check=False: no
+        check.  check="deferred": no synchronisation once the capacity has
+        been sized (the first call sizes it like check=True); the counters
+        are copied to pinned host memory behind the render and inspected at
+        the next call, or by ``status()``.  A deferred overflow grows the
+        capacity for the following calls and is reported by ``status()``."""
+        if check == "deferred":
+            return self._forward_deferred(params, stream)
         for _ in range(4):
             self.slice_project(params, stream)
             self.bin_sort(stream)
@@ -154,6 +162,50 @@ class Frame:
             self.last_counters = c
             return self.image
         raise RuntimeError("pair capacity could not be sized")
+
+    def _forward_deferred(self, params: dict, stream=None) -> torch.Tensor:
+        if not hasattr(self, "last_counters"):
+            return self.forward(params, stream, check=True)
+        self._take_deferred(wait=False)
+        self.slice_project(params, stream)
+        self.bin_sort(stream)
+        self.render(stream)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        if not torch.cuda.is_current_stream_capturing():
+            if not hasattr(self, "_host_counters"):
+                self._host_counters = torch.empty(4, dtype=torch.int32).pin_memory()
+                self._counter_event = torch.cuda.Event()
+            with torch.cuda.stream(s):
+                self._host_counters.copy_(self.state[:16].view(torch.int32), non_blocking=True)
+            self._counter_event.record(s)
+            self._pending = True
+        return self.image
+
+    def _take_deferred(self, wait: bool):
+        """Reads the counters copied behind the last deferred forward once the
+        copy has landed (waiting for it only with wait=True)."""
+        if not getattr(self, "_pending", False):
+            return
+        if not wait and not self._counter_event.query():
+            return
+        self._counter_event.synchronize()
+        self._pending = False
+        h = [int(x) & 0xffffffff for x in self._host_counters.tolist()]
+        c = N.Counters(h[0], h[1], h[2], h[3])
+        self.last_counters = c
+        if c.status & N.STATUS_PAIR_OVERFLOW:
+            self.overflowed = True
+            self._alloc(int(c.n_pairs * 1.25) + 1024)
+
+    def status(self) -> N.Counters:
+        """Counters of the last forward (waits for a deferred copy); raises if a
+        deferred forward dropped (splat, tile) pairs since the last call."""
+        self._take_deferred(wait=True)
+        if getattr(self, "overflowed", False):
+            self.overflowed = False
+            raise RuntimeError("a deferred forward exceeded the pair capacity (its image lacks pairs); "
+                               f"the capacity has grown to {self.pair_capacity}")
+        return self.last_counters
 
     def _grads(self, params: dict, grads: dict | None, mean2d: bool):
         """mean2d: also the densification signals mean2d_abs (sum over views of
@@ -230,7 +282,8 @@ class Render4DGS(torch.autograd.Function):
     def forward(ctx, frame: Frame, mu, log_s, ql, qr, logit, shs, sh_degree: int, n_freq: int, period: float):
         params = dict(mu=mu.detach(), log_s=log_s.detach(), ql=ql.detach(), qr=qr.detach(), logit=logit.detach(),
                       shs=shs.detach(), sh_degree=sh_degree, n_freq=n_freq, period=period)
-        img = frame.forward(params).clone()
+        # no synchronisation: the pair-capacity check is deferred (Frame.status)
+        img = frame.forward(params, check="deferred").clone()
         ctx.frame = frame
         ctx.meta = (sh_degree, n_freq, period)
         ctx.save_for_backward(mu, log_s, ql, qr, logit, shs)

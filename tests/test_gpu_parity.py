@@ -3,9 +3,12 @@
 Images: max-abs <= 2e-4 per channel on every pixel the oracle does not flag
 (a flagged pixel has a discrete decision within rounding distance of its
 threshold, where FP32 may legitimately decide the other way; flagged pixels
-must stay rare).  Gradients: relative error <= 1e-3 per parameter group,
-with dL/dimage zero on flagged pixels so that both sides differentiate the
-same piecewise-smooth function.
+must stay rare).  Gradients: element by element, |g_gpu - g_oracle| <=
+1e-3 |g_oracle| + eps_k, where eps_k = 1e-3 times the 99th percentile of
+|g_oracle| over the entries of parameter group k (the FP32 rounding of a sum
+of per-pixel terms scales with the group's large entries, not with the
+entry's own, possibly cancelled, value); dL/dimage is zero on flagged pixels
+so that both sides differentiate the same piecewise-smooth function.
 """
 import math
 
@@ -465,14 +468,43 @@ def grads_gpu(fr, p, dL_list):
     return {k: v.double().cpu().numpy() for k, v in g.items()}
 
 
-def assert_grad_parity(gg, go, tol=GRAD_TOL):
-    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
-        a, b = gg[k], go[k]
-        nb = np.linalg.norm(b)
-        assert nb > 0, k
-        rel = np.linalg.norm(a - b) / nb
-        print(f"[parity] gradient {k}: relative error {rel:.3e}")
-        assert rel <= tol, f"{k}: relative error {rel:.3e}"
+GROUPS = ("mu", "log_s", "ql", "qr", "logit", "shs")
+
+
+def grad_floor(ref, tol=GRAD_TOL):
+    """eps_k of one parameter group: tol x the 99th percentile of |reference|
+    over its non-zero entries."""
+    mag = np.abs(np.asarray(ref, dtype=np.float64)).ravel()
+    mag = mag[mag > 0]
+    return tol * float(np.percentile(mag, 99)) if mag.size else 0.0
+
+
+def assert_elementwise(a, b, tol, name, floor=None):
+    """|a - b| <= tol |b| + eps element by element (eps = grad_floor(b, tol)
+    unless given); returns the worst entry's ratio to its bound and the
+    worst relative error among the entries above eps."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (name, a.shape, b.shape)
+    assert np.all(np.isfinite(a)), f"{name}: non-finite GPU gradient"
+    eps = grad_floor(b, tol) if floor is None else floor
+    assert eps > 0, f"{name}: reference gradient is zero"
+    err = np.abs(a - b)
+    ratio = err / (tol * np.abs(b) + eps)
+    i = np.unravel_index(int(np.argmax(ratio)), ratio.shape)
+    big = np.abs(b) > eps
+    rel_big = float((err[big] / np.abs(b[big])).max()) if big.any() else 0.0
+    print(f"[parity] gradient {name}: worst entry {tuple(int(x) for x in i)} gpu {a[i]:.6e} oracle {b[i]:.6e} "
+          f"(|err| / bound {ratio[i]:.3f}, eps {eps:.3e}); worst rel. error above eps {rel_big:.3e} "
+          f"over {int(big.sum())} of {b.size} entries")
+    assert ratio[i] <= 1.0, (f"{name}: entry {tuple(int(x) for x in i)} gpu {a[i]:.9e} oracle {b[i]:.9e} "
+                             f"beyond {tol:g} relative + {eps:.3e}")
+    return float(ratio[i]), rel_big
+
+
+def assert_grad_parity(gg, go, tol=GRAD_TOL, keys=GROUPS, what=""):
+    """Element-wise parity of every parameter group (see module docstring)."""
+    return {k: assert_elementwise(gg[k], go[k], tol, f"{what}{k}") for k in keys}
 
 
 def masked_dL(views, refs, seed):
@@ -516,14 +548,12 @@ def test_backward_in_two_steps(tile, mixed):
     for k in g1:
         rel = float((g1[k] - g2[k]).norm() / g1[k].norm())
         assert rel < 1e-5, (k, rel)
-    tol = 1e-2 if mixed else GRAD_TOL
+    tol = MIXED_GRAD_TOL if mixed else GRAD_TOL
     for vi, v in enumerate(views):
         want = O.backward(Gr, v, dL[vi])["grad2d"]
         got = g2d[vi]
         for c, name in enumerate(("u", "v", "a", "b", "c", "alpha_eff", "R", "G", "B")):
-            nb = np.linalg.norm(want[:, c])
-            rel = np.linalg.norm(got[:, c] - want[:, c]) / nb
-            assert nb > 0 and rel <= tol, (vi, name, rel)
+            assert_elementwise(got[:, c], want[:, c], tol, f"view {vi} dL/d{name}")
 
 
 @TILES
@@ -537,9 +567,11 @@ def test_backward_config0(tile):
 
 
 def test_backward_central_differences():
-    """GPU gradient vs central differences of the GPU forward on 64 random
-    parameters whose stencil changes no discrete decision (checked on the
-    oracle's per-pixel contributor sequences: same splats in the same order)."""
+    """GPU gradient vs FP64 central differences of the oracle's forward on 64
+    random parameters with a non-negligible gradient, whose stencil changes no
+    discrete decision (the oracle's per-pixel contributor sequences, an
+    order-sensitive hash, are the same at x - h, x and x + h), element by
+    element at 1e-3 relative plus the group's floor eps_k."""
     G, views = ragged_scene(n=600, seed=31, L=2, K=1)
     G["log_s"][:3] += 0.7
     views = views[:2]
@@ -547,69 +579,78 @@ def test_backward_central_differences():
     refs = [O.render(G, v) for v in views]
     dL = masked_dL(views, refs, 7)
     gg = grads_gpu(fr, p, dL)
-    w = [torch.as_tensor(d) for d in dL]
+    go = O.backward_views(G, views, dL)
+    floors = {k: grad_floor(go[k]) for k in GROUPS}
+    G64 = {k: (np.asarray(v, dtype=np.float64) if isinstance(v, np.ndarray) else v) for k, v in G.items()}
 
-    def loss(Gx):
-        _, _, imgs, _ = gpu_forward(Gx, views)
-        return sum(float((torch.as_tensor(im) * wi).sum()) for im, wi in zip(imgs, w))
+    def loss(Gx):  # sum over views and pixels of dL * image, in FP64
+        return sum(float(np.sum(d * O.render(Gx, v)["image"])) for v, d in zip(views, dL))
 
     rng = np.random.default_rng(8)
-    checked, tried = 0, 0
-    keys = ("mu", "log_s", "ql", "qr", "logit", "shs")
-    while checked < 64 and tried < 400:
+    checked, tried, worst = 0, 0, 0.0
+    while checked < 64 and tried < 2000:
         tried += 1
-        key = keys[tried % len(keys)]
-        arr = G[key]
+        key = GROUPS[tried % len(GROUPS)]
+        arr = G64[key]
         idx = tuple(int(rng.integers(0, s)) for s in arr.shape)
-        gi = idx[-1]
-        if abs(gg[key][idx]) < 1e-2:
-            continue  # too small to resolve against FP32 rendering noise
+        if abs(gg[key][idx]) < 10 * floors[key]:
+            continue  # a gradient this small only tests the floor
         x0 = float(arr[idx])
-        h = 2e-3 * max(1.0, abs(x0))
-        Gp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G.items()}
-        Gm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G.items()}
+        h = 1e-6 * max(1.0, abs(x0))
+        Gp = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G64.items()}
+        Gm = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in G64.items()}
         Gp[key][idx] = x0 + h
         Gm[key][idx] = x0 - h
-        # same discrete decisions on both sides of the stencil (oracle, FP64)
-        same = True
-        for v, ref in zip(views, refs):
-            a, b = O.render(Gp, v), O.render(Gm, v)
-            if not (np.array_equal(a["seq_hash"], ref["seq_hash"]) and np.array_equal(b["seq_hash"], ref["seq_hash"])):
-                same = False
-                break
+        same = all(np.array_equal(O.render(Gx, v)["seq_hash"], ref["seq_hash"])
+                   for Gx in (Gp, Gm) for v, ref in zip(views, refs))
         if not same:
             continue
-        h_eff = (np.float32(x0 + h) - np.float32(x0 - h))
-        fd = (loss(Gp) - loss(Gm)) / float(h_eff)
-        an = gg[key][idx]
-        # FP32 rendering noise over the few hundred pixels a stencil changes is ~1e-6 in the
-        # loss, i.e. ~1e-3 after division by 2h; the relative bar applies above that floor
-        assert abs(fd - an) <= GRAD_TOL * abs(an) + 2e-3, (key, idx, an, fd)
+        fd = (loss(Gp) - loss(Gm)) / (2.0 * h)
+        an = float(gg[key][idx])
+        r = abs(fd - an) / (GRAD_TOL * abs(fd) + floors[key])
+        worst = max(worst, r)
+        assert r <= 1.0, (key, idx, an, fd, floors[key])
         checked += 1
-    assert checked >= 32
+    print(f"[parity] central differences (FP64 oracle): {checked} parameters, worst |err| / bound {worst:.3f}")
+    assert checked >= 48
 
 
 def test_autograd_function_l1_loss():
+    """Render4DGS through torch.autograd on an L1 loss whose per-pixel terms
+    are masked where the oracle flags a decision within rounding distance of
+    its threshold (both sides then differentiate the same function); the
+    gradients of all raw parameters match the oracle's element by element.
+    The forward does not synchronise: with the device kept busy, the call
+    returns before the GPU has rendered."""
     from paper_2310_10642_gb300 import render as R
     G, views = ragged_scene(n=1200, seed=41, L=1, K=1)
     p = R.params_to_device(G)
-    leaves = {k: p[k].clone().requires_grad_(True) for k in R.PARAM_KEYS}
-    params = dict(leaves, sh_degree=p["sh_degree"], n_freq=p["n_freq"], period=p["period"])
-    imgs, fr = R.render(params, views)
-    targets = [torch.as_tensor(t).cuda() for t in I.random_target(views, 77)]
-    loss = sum((im - t).abs().mean() for im, t in zip(imgs, targets))
-    loss.backward()
-    # same gradient through the oracle: dL/dimage = sign(im - t) / numel
     refs = [O.render(G, v) for v in views]
-    dL = [np.sign(im.detach().cpu().numpy() - t.cpu().numpy()) / im.numel() for im, t in zip(imgs, targets)]
-    for d, ref in zip(dL, refs):
-        assert (ref["flags"] != 0).mean() < 0.02
+    masks = [torch.as_tensor(r["flags"] == 0, dtype=torch.float32).cuda() for r in refs]
+    for r in refs:
+        assert (r["flags"] != 0).mean() < 0.02
+    targets = [torch.as_tensor(t).cuda() for t in I.random_target(views, 77)]
+
+    def run():
+        leaves = {k: p[k].clone().requires_grad_(True) for k in R.PARAM_KEYS}
+        params = dict(leaves, sh_degree=p["sh_degree"], n_freq=p["n_freq"], period=p["period"])
+        imgs, fr = R.render(params, views, frame=frame)
+        return leaves, imgs, fr
+
+    frame = R.Frame(G["logit"].shape[0], views)
+    run()  # the first call sizes the pair capacity (one synchronisation)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(200_000_000)  # keeps the stream busy for ~0.1 s
+    leaves, imgs, fr = run()
+    assert not torch.cuda.current_stream().query(), "the differentiable forward synchronised"
+    loss = sum(((im - t).abs() * m).mean() for im, t, m in zip(imgs, targets, masks))
+    loss.backward()
+    assert fr.status().status == 0
+    dL = [np.sign(im.detach().cpu().numpy() - t.cpu().numpy()) * m.cpu().numpy() / im.numel()
+          for im, t, m in zip(imgs, targets, masks)]
     go = O.backward_views(G, views, dL)
     gg = {k: leaves[k].grad.double().cpu().numpy() for k in R.PARAM_KEYS}
-    # flagged pixels are not masked here (the loss is fixed); allow their share
-    for k in R.PARAM_KEYS:
-        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
-        assert rel < 2e-2, (k, rel)
+    assert_grad_parity(gg, go, what="autograd ")
 
 
 # ---------------------------------------------------------------------------- mixed precision
@@ -644,10 +685,7 @@ def test_mixed_precision_against_fp64_oracle(tile):
     dL = masked_dL(views, refs16, 9)
     gg = grads_gpu(fr, p, dL)
     go = O.backward_views(G16, views, dL)
-    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
-        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
-        print(f"[parity] mixed tile {tile} gradient {k}: relative error {rel:.3e}")
-        assert rel <= MIXED_GRAD_TOL, (k, rel)
+    assert_grad_parity(gg, go, MIXED_GRAD_TOL, what=f"mixed tile {tile} ")
 
 
 # ---------------------------------------------------------------------------- full size
@@ -691,10 +729,7 @@ def test_full_size_workload_crops(mixed):
     dL[picks[2]][:] = 0.0
     gg = grads_gpu(fr, p, dL)
     gtol = MIXED_GRAD_TOL if mixed else GRAD_TOL
-    for k in ("mu", "log_s", "ql", "qr", "logit", "shs"):
-        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
-        print(f"[parity] full-size {'mixed' if mixed else 'fp32'} gradient {k}: relative error {rel:.3e}")
-        assert rel <= gtol, (k, rel)
+    assert_grad_parity(gg, go, gtol, what=f"full-size {'mixed' if mixed else 'fp32'} ")
 
 
 # ---------------------------------------------------------------------------- densification (Sec. 3.4)
@@ -716,10 +751,7 @@ def test_densification_statistics_match_oracle():
         m2d_want += np.hypot(o["grad2d"][:, 0], o["grad2d"][:, 1])
         mt_want += np.abs(o["mu"][3])
     for key, want in (("mean2d_abs", m2d_want), ("mu_t_abs", mt_want)):
-        got = g[key].double().cpu().numpy()
-        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
-        print(f"[parity] {key}: relative error {rel:.3e}")
-        assert np.linalg.norm(want) > 0 and rel <= GRAD_TOL, (key, rel)
+        assert_elementwise(g[key].double().cpu().numpy(), want, GRAD_TOL, key)
 
 
 def test_split_sampler_draws_from_the_4d_density():
@@ -825,15 +857,14 @@ def test_no_4drot_variant_against_oracle():
     dL = masked_dL(views, refs, 14)
     gg = grads_gpu(fr, p, dL)
     go = O.backward_views(Go, views, dL)
-    for k in ("mu", "log_s", "logit", "shs"):
-        rel = np.linalg.norm(gg[k] - go[k]) / np.linalg.norm(go[k])
-        assert rel <= GRAD_TOL, (k, rel)
+    assert_grad_parity(gg, go, keys=("mu", "log_s", "logit", "shs"), what="No-4DRot ")
     assert np.all(gg["qr"] == 0.0)
     # dL/dq_left by central differences of the oracle (loss = sum dL * image)
     def loss(q):
         Gq = oracle_params(q)
         return sum(float(np.sum(d * O.render(Gq, v)["image"])) for v, d in zip(views, dL))
     top = np.argsort(-np.abs(gg["ql"]).sum(0))[:8]
+    eps = grad_floor(gg["ql"])
     for g in top:
         for i in range(4):
             h = 1e-6
@@ -841,7 +872,7 @@ def test_no_4drot_variant_against_oracle():
             qp[i, g] += h
             qm[i, g] -= h
             fd = (loss(qp) - loss(qm)) / (2 * h)
-            assert abs(fd - gg["ql"][i, g]) <= 2e-3 * np.abs(gg["ql"][:, g]).max() + 1e-7, (g, i, fd, gg["ql"][i, g])
+            assert abs(fd - gg["ql"][i, g]) <= GRAD_TOL * abs(fd) + eps, (g, i, fd, gg["ql"][i, g], eps)
     # no motion: the projected means do not depend on t
     v0, v1 = dict(views[0], t=0.2), dict(views[0], t=0.7)
     f0 = R.Frame(n, [v0, v1], dict(tile_size=32))

@@ -292,6 +292,140 @@ def test_ambiguity_bound_covers_flipped_decisions(oracle):
     assert moved["alpha_min"] > 0 and moved["T_min"] > 0
 
 
+def _point_at(v, px, py, d):
+    """World point seen at pixel (px, py) at camera depth d, for a view whose
+    camera sits at (0, 0, 4) and looks at the origin (+x right, +y down)."""
+    return [(px - v["cx"]) * d / v["fx"], -(py - v["cy"]) * d / v["fy"], 4.0 - d]
+
+
+def _flip_check(oracle, G, v, base, opts, moved_key, moved):
+    r = oracle.render(G, v, opts)
+    d = np.abs(r["image"] - base["image"]).max(axis=0)
+    dT = np.abs(r["T"] - base["T"])
+    moved[moved_key] += int((d > 1e-12).sum())
+    assert np.all(d <= 1.01 * base["amb_image"] + 1e-12), (moved_key, float((d - base["amb_image"]).max()))
+    assert np.all(dT <= 1.01 * base["amb_T"] + 1e-12), moved_key
+
+
+def test_ambiguity_bound_covers_borderline_culls(oracle):
+    """The bound's Gaussian-level terms, pinned by flipping the culls that lie
+    inside their margins: Gaussians planted with p(t) (Sec. 4.2 filter), the
+    camera depth (near plane) or alpha_eff (R7) within half a margin of the
+    threshold, over a sparse random scene; moving p_min, near_z or alpha_min
+    by 0.9 of its margin culls or keeps each of them the other way, and
+    image and T may move by no more than the bounds."""
+    o = oracle.DEFAULT_OPTIONS
+    t = 0.5
+    v = I.view((0.0, 0.0, 4.0), 80, 64, t, bg=(0.3, 0.6, 0.9))
+    rng = np.random.default_rng(71)
+    planted = []
+    amin = o["alpha_min"]
+    for k in range(72):
+        kind = k % 3
+        sign = 1.0 if (k // 3) % 2 == 0 else -1.0
+        px, py = rng.uniform(4, 76), rng.uniform(4, 60)
+        if kind == 0:  # p(t) = p_min (1 +- 0.5e-4) with Sigma_44 = s_t^2 (identity rotation pair)
+            st = 0.1
+            dt = st * math.sqrt(-2.0 * math.log(o["p_min"] * (1.0 + sign * 0.5e-4)))
+            g = one_gaussian(_point_at(v, px, py, 3.0) + [t - dt], np.log([0.03, 0.03, 0.03, st]), logit=2.0,
+                             shs=rng.normal(0, 1, 3))
+        elif kind == 1:  # camera depth = near_z (1 +- 0.5e-4)
+            d = o["near_z"] * (1.0 + sign * 0.5e-4)
+            g = one_gaussian(_point_at(v, px, py, d) + [t], np.log([0.002, 0.002, 0.002, 1.0]), logit=2.0,
+                             shs=rng.normal(0, 1, 3))
+        else:  # alpha_eff = sigmoid(logit) p = alpha_min (1 +- 0.5e-4), p = 1
+            a = amin * (1.0 + sign * 0.5e-4)
+            g = one_gaussian(_point_at(v, px, py, 2.5) + [t], np.log([0.03, 0.03, 0.03, 1.0]),
+                             logit=math.log(a / (1.0 - a)), shs=rng.normal(0, 1, 3))
+        planted.append(g)
+    bgG = I.gaussians(1500, 62, 0, 0)
+    bgG["mu"][3] = t
+    G = concat([{k: (bgG[k] if k in ("sh_degree", "n_freq", "period") else bgG[k].astype(np.float64))
+                 for k in bgG}] + planted)
+    base = oracle.render(G, v)
+    flagged_cull = (base["flags"] & 32) != 0
+    assert flagged_cull.sum() > 20  # the planted culls are flagged where they could be blended
+    moved = {"p_min": 0, "near_z": 0, "alpha_min": 0}
+    for key in moved:
+        for f in (1 + 0.9e-4, 1 - 0.9e-4):
+            _flip_check(oracle, G, v, base, {key: o[key] * f}, key, moved)
+    assert all(m > 0 for m in moved.values()), moved  # each kind of cull did flip
+    assert (base["amb_image"] > 0).mean() < 0.3
+
+
+def test_ambiguity_bound_covers_depth_ties(oracle):
+    """The bound's depth near-tie term (R8: equal depths are ordered by
+    index), pinned by swapping the order of overlapping splats of equal
+    depth: each pair sits at one world z in front of a camera looking down
+    -z (so both depths are the same double), and the scene is rendered with
+    the pair's indices in both orders.  The image moves by no more than the
+    bound of either render, T does not move (both orders remove the same
+    light), and the tie is flagged as such (cause bit 4)."""
+    t = 0.5
+    v = I.view((0.0, 0.0, 4.0), 64, 48, t, bg=(0.2, 0.2, 0.2))
+    rng = np.random.default_rng(72)
+    pairs = []
+    for k in range(24):
+        px, py = rng.uniform(6, 56), rng.uniform(6, 42)
+        d = 2.0 + 0.05 * k  # pairs at distinct depths: only the two splats of a pair are tied
+        pairs.append([one_gaussian(_point_at(v, px + dx, py, d) + [t], np.log([0.02, 0.02, 0.02, 1.0]), logit=1.5,
+                                   shs=rng.normal(0, 1.5, 3)) for dx in (0.0, 1.5)])
+    rf = oracle.render(concat([g for a, b in pairs for g in (a, b)]), v)
+    rb = oracle.render(concat([g for a, b in pairs for g in (b, a)]), v)
+    d = np.abs(rf["image"] - rb["image"]).max(axis=0)
+    assert (d > 1e-6).sum() > 50  # the order matters on many pixels
+    assert np.all(((rf["flags"] & 4) != 0)[d > 1e-5]) and np.all(((rb["flags"] & 4) != 0)[d > 1e-5])
+    for r in (rf, rb):
+        assert np.all(d <= 1.01 * r["amb_image"] + 1e-12), float((d - r["amb_image"]).max())
+    assert np.abs(rf["T"] - rb["T"]).max() < 1e-12
+
+
+def test_eq4_off_axis_jacobian_by_differences(oracle):
+    """Eq. 3-4 off the optical axis, against the mathematics rather than a
+    restated Jacobian: J = d(u, v)/d(X, Y, Z) taken by central differences of
+    the pinhole map (u, v) = (fx X/Z + cx, fy Y/Z + cy), and the 2D mean by
+    the homogeneous product K (W x + tau); the oracle's 2D covariance must
+    equal J W Sigma_{xyz|t} W^T J^T + dilation I (clamp off) at points up to
+    ~30 degrees off axis in every direction, with a full 4D rotation."""
+    rng = np.random.default_rng(73)
+    v = I.view((0.7, -0.4, 3.6), 120, 90, 0.4)
+    vm = np.asarray(v["viewmat"]).reshape(3, 4)
+    W, tau = vm[:, :3], vm[:, 3]
+    Kmat = np.array([[v["fx"], 0, v["cx"]], [0, v["fy"], v["cy"]], [0, 0, 1.0]])
+    opts = dict(clamp_fov=0.0, dilation=0.3)
+
+    def pinhole(xc):
+        return np.array([v["fx"] * xc[0] / xc[2] + v["cx"], v["fy"] * xc[1] / xc[2] + v["cy"]])
+
+    checked = 0
+    for k in range(40):
+        # a camera-space point well off axis, mapped back to world coordinates
+        Z = rng.uniform(1.5, 5.0)
+        xc = np.array([rng.uniform(-0.6, 0.6) * Z, rng.uniform(-0.6, 0.6) * Z, Z])
+        xw = W.T @ (xc - tau)
+        g = one_gaussian(list(xw) + [0.4 + rng.uniform(-0.05, 0.05)], rng.normal(-2.5, 0.3, 4),
+                         ql=unit(rng), qr=unit(rng), logit=3.0)
+        s = oracle.project(g, 0, v, opts)
+        if s.depth <= 0.0 or s.cull in (2, 4):
+            continue
+        x3 = np.array(s.xc)
+        J = np.zeros((2, 3))
+        for i in range(3):
+            h = 1e-6 * max(1.0, abs(x3[i]))
+            e = np.zeros(3)
+            e[i] = h
+            J[:, i] = (pinhole(x3 + e) - pinhole(x3 - e)) / (2 * h)
+        S3 = np.array(s.Sigma3).reshape(3, 3)
+        want = J @ W @ S3 @ W.T @ J.T + 0.3 * np.eye(2)
+        got = np.array([[s.cov2d[0], s.cov2d[1]], [s.cov2d[1], s.cov2d[2]]])
+        np.testing.assert_allclose(got, want, rtol=1e-7, atol=1e-9 * np.abs(want).max())
+        hom = Kmat @ (W @ np.array(s.mu3) + tau)
+        np.testing.assert_allclose([s.u, s.v], hom[:2] / hom[2], rtol=1e-12, atol=1e-9)
+        assert abs(x3[0] / x3[2]) > 0.05 or abs(x3[1] / x3[2]) > 0.05  # off axis
+        checked += 1
+    assert checked >= 30
+
+
 def test_temporal_filter_culls_below_threshold(oracle):
     """p(t) < 0.05 removes the Gaussian entirely (Sec. 4.2)."""
     st = 0.1
