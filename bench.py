@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="image scale (smoke runs only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step key of the default run")
+    ap.add_argument("--no-aux", action="store_true", help="skip the depth/flow-map key of the default run")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the No-4DRot / static-3DGS stage times of the default run")
     ap.add_argument("--workload", default="render", choices=["render", "train"],
                     help="render: forward+backward of the 1M-Gaussian batch (the headline); train: the full "
                          "training step (loss, adjoint, Adam) on 3M Gaussians x 8 views")
@@ -178,27 +182,77 @@ def workload_inputs(n=None, views=None, scale=1.0):
     return c["gaussians"], vs, c["options"]
 
 
-def oracle_sample(G, views, budget_s=20.0, crop=32):
-    """FP64 oracle forward+backward on crop x crop windows at the centre of
-    successive views until ~budget_s of CPU work; returns (Mpix/s, sample)."""
+def host_cpu() -> dict:
+    """Core count and CPU model of the host running the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(cores=int(cores), model=model)
+
+
+def _as_f64(G):
+    """The parameters in float64 once, so that every oracle call reads them in place."""
+    import numpy as np
+    return {k: (np.ascontiguousarray(v, dtype=np.float64) if isinstance(v, np.ndarray) else v) for k, v in G.items()}
+
+
+def _oracle_crop(G64, v, crop, seed):
+    """One oracle forward + backward on the crop x crop window at the view's centre."""
     import numpy as np
     from oracle import oracle as O
+    x0 = v["width"] // 2 - crop // 2
+    y0 = v["height"] // 2 - crop // 2
+    win = (x0, y0, crop, crop)
+    O.render(G64, v, window=win, prefilter=True)
+    O.backward(G64, v, np.random.default_rng(seed).normal(size=(3, crop, crop)), window=win, prefilter=True)
+    return crop * crop
+
+
+def oracle_sample(G, views, budget_s=20.0, crop=32, threads=1):
+    """FP64 oracle forward+backward on crop x crop windows at the centre of
+    successive views until ~budget_s of wall time; returns (Mpix/s, sample).
+    threads > 1 splits the work over pixels: each thread renders whole
+    windows (one oracle call at a time per thread; the C oracle has no shared
+    mutable state and ctypes releases the interpreter lock during its calls)."""
+    from concurrent.futures import ThreadPoolExecutor
+    G64 = _as_f64(G)
     t0 = time.perf_counter()
-    pix = 0
-    done = 0
-    rng = np.random.default_rng(0)
-    for v in views:
-        x0 = v["width"] // 2 - crop // 2
-        y0 = v["height"] // 2 - crop // 2
-        win = (x0, y0, crop, crop)
-        O.render(G, v, window=win, prefilter=True)
-        O.backward(G, v, rng.normal(size=(3, crop, crop)), window=win, prefilter=True)
-        pix += crop * crop
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+    pix = done = 0
+    if threads <= 1:
+        for v in views:
+            pix += _oracle_crop(G64, v, crop, done)
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            while time.perf_counter() - t0 <= budget_s and done < 64 * threads:
+                batch = [views[(done + i) % len(views)] for i in range(threads)]
+                pix += sum(ex.map(lambda a: _oracle_crop(G64, a[1], crop, a[0]), enumerate(batch, done)))
+                done += threads
     dt = time.perf_counter() - t0
-    return pix / dt / 1e6, f"{done} views x {crop}x{crop} centre crop, forward+backward, {G['logit'].shape[0]} Gaussians"
+    return pix / dt / 1e6, (f"{done} views x {crop}x{crop} centre crop, forward+backward, "
+                            f"{G['logit'].shape[0]} Gaussians, {threads} thread{'s' if threads > 1 else ''}")
+
+
+def cpu_baseline_both(G, views, budget_s=12.0) -> dict:
+    """The oracle on one host core and on all of them, in the same run."""
+    host = host_cpu()
+    v1, s1 = oracle_sample(G, views, budget_s=budget_s, threads=1)
+    vn, sn = oracle_sample(G, views, budget_s=budget_s, threads=host["cores"])
+    return dict(value=vn, unit="Mpix/s", cores=host["cores"], kind="oracle", sample=sn, cpu_model=host["model"],
+                single_thread=dict(value=v1, unit="Mpix/s", cores=1, sample=s1))
 
 
 def run_reference(args):
@@ -208,11 +262,12 @@ def run_reference(args):
     G, views, _ = workload_inputs(args.n, args.views, args.scale)
     vals = []
     sample = ""
+    host = host_cpu()
     for _ in range(args.warmup):
         oracle_sample(G, views[:1], budget_s=0.0, crop=16)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, sample = oracle_sample(G, views, budget_s=15.0 / max(1, args.steps), crop=32)
+        v, sample = oracle_sample(G, views, budget_s=30.0 / max(1, args.steps), crop=32, threads=host["cores"])
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
@@ -220,7 +275,8 @@ def run_reference(args):
                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, ms_per_step=wall * 1e3 / args.steps,
                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                config=dict(WORKLOAD, l2="inputs larger than L2"), impl="reference",
-               cpu_baseline=dict(value=value, unit="Mpix/s", cores=1, kind="oracle", sample=sample),
+               cpu_baseline=dict(value=value, unit="Mpix/s", cores=host["cores"], kind="oracle", sample=sample,
+                                 cpu_model=host["model"]),
                e2e=dict(value=value, unit="Mpix/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0), gpu_launches=0)
     print(json.dumps(out))
     return 0
@@ -231,22 +287,16 @@ TRAIN_WORKLOAD = dict(workload="4dgs-train-step", gaussians=3_000_000, clustered
                       views="4 x 1352x1014 + 4 x 800x800", loss="0.8 L1 + 0.2 (1 - SSIM)", optimizer="Adam")
 
 
-def main_train(args):
-    """Training-step throughput: one CUDA-graph replay = forward, loss, adjoint
-    and Adam over all parameters for a batch of 8 views."""
+def measure_train(args, dist=None, world=1, rank=0, steps=None, per_view=True, e2e=True) -> dict:
+    """Training-step throughput on the 3M-Gaussian, 8-view workload: one CUDA
+    graph replay = forward, loss, adjoint and Adam over all parameters.
+    Returns the numbers; the caller prints them."""
     import torch
     from paper_2310_10642_gb300 import inputs as I
     from paper_2310_10642_gb300 import native as N
     from paper_2310_10642_gb300 import render as R
     from paper_2310_10642_gb300.train import TrainStep
-    N.build()
-    N.lib()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    steps = steps or args.steps
     c = I.config(4, n=args.n, n_views=args.views, scale=args.scale)
     G, views = c["gaussians"], c["views"]
     n = G["logit"].shape[0]
@@ -278,19 +328,19 @@ def main_train(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ts.replay()
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    value, total_ms = job_throughput(npix, args.steps, e0.elapsed_time(e1), dist, device="cuda")
+    value, total_ms = job_throughput(npix, steps, e0.elapsed_time(e1), dist, device="cuda")
     status = ts.frame.counters().status
 
     # end to end: this step's targets copied in from pinned host memory, the loss read back
-    e2e = None
-    if not args.no_e2e:
+    e2e_d = None
+    if e2e:
         loss_host = torch.empty(1, dtype=torch.float32).pin_memory()
-        ks = max(1, min(args.steps, 5))
+        ks = max(1, min(steps, 5))
         e0.record(stream)
         for _ in range(ks):
             ts.targets.copy_(tg_host, non_blocking=True)
@@ -299,13 +349,13 @@ def main_train(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / ks
-        e2e = dict(value=npix * world / (ms * 1e-3) / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(tg_host.numel() * 4),
-                   d2h_bytes_per_step=4, ms_per_step=ms)
+        e2e_d = dict(value=npix * world / (ms * 1e-3) / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(tg_host.numel() * 4),
+                     d2h_bytes_per_step=4, ms_per_step=ms)
 
     # plain FP32 per-view path: each view rendered, scored and differentiated on its own (gradients
     # summed over views), then one Adam step
     single = None
-    if not dist or dist.get_rank() == 0:
+    if per_view and rank == 0:
         p32 = R.params_to_device(G)
         tsv = [TrainStep(p32, [v], tgv.reshape(-1).cuda(), dict(opts, record_fp16=0), mixed=False)
                for v, tgv in zip(views, [torch.as_tensor(t) for t in I.random_target(views, 44)])]
@@ -341,20 +391,45 @@ def main_train(args):
         ms1 = e0.elapsed_time(e1) / 3
         single = dict(mpix_s=round(npix / (ms1 * 1e-3) / 1e6, 3), ms_per_step=round(ms1, 3),
                       path="plain FP32, one view per call (render, loss, adjoint), gradients summed, one Adam step")
+        del tsv, acc, p32
+    out = dict(value=round(value, 3), ms_per_step=round(total_ms / steps, 4),
+               steps_per_s=round(1e3 * steps / total_ms, 3), pixels_per_step=npix,
+               config=dict(TRAIN_WORKLOAD, n=n, n_views=len(views), tile=tile, bin=binsz, batch_depth=depth,
+                           precision="BF16 4DSH copy + 16-bit conic records, FP32 master weights" if mixed
+                           else "FP32", cuda_graph=True, pixels_per_step=npix,
+                           l2="inputs larger than L2 (1.9 GB FP32 parameters + Adam state)",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+               per_view_fp32=single,
+               train_vs_per_view_fp32=round(value / world / single["mpix_s"], 3) if single else None,
+               final_loss=float(ts.loss.item()), status=int(status), e2e=e2e_d, clocks=clk,
+               gpu_launches=int(per_step * steps))
+    del ts, p, tg
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
-    if not dist or dist.get_rank() == 0:
-        out = dict(metric="Mpix/s training step (4DGS, 3M Gaussians, 8 views)", value=round(value, 3), unit="Mpix/s",
-                   n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4),
-                   steps_per_s=round(1e3 * args.steps / total_ms, 3), higher_is_better=True, scaling="weak",
-                   vs_baseline=None, dtype="f32", data="synthetic",
-                   config=dict(TRAIN_WORKLOAD, n=n, n_views=len(views), tile=tile, bin=binsz, batch_depth=depth,
-                               precision="BF16 4DSH copy + 16-bit conic records, FP32 master weights" if mixed
-                               else "FP32", cuda_graph=True, pixels_per_step=npix,
-                               l2="inputs larger than L2 (1.9 GB FP32 parameters + Adam state)",
-                               parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-                   per_view_fp32=single, train_vs_per_view_fp32=round(value / world / single["mpix_s"], 3) if single
-                   else None, final_loss=float(ts.loss.item()), status=int(status), e2e=e2e, clocks=clk,
-                   gpu_launches=int(per_step * args.steps))
+
+def main_train(args):
+    """Training-step throughput as the headline (``--workload train``)."""
+    import torch
+    from paper_2310_10642_gb300 import native as N
+    N.build()
+    N.lib()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    r = measure_train(args, dist, world, rank, e2e=not args.no_e2e)
+    if rank == 0:
+        out = dict(metric="Mpix/s training step (4DGS, 3M Gaussians, 8 views)", value=r["value"], unit="Mpix/s",
+                   n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=r["ms_per_step"],
+                   steps_per_s=r["steps_per_s"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                   dtype="f32", data="synthetic", config=r["config"], per_view_fp32=r["per_view_fp32"],
+                   train_vs_per_view_fp32=r["train_vs_per_view_fp32"], final_loss=r["final_loss"],
+                   status=r["status"], e2e=r["e2e"], clocks=r["clocks"], gpu_launches=r["gpu_launches"])
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -416,7 +491,9 @@ def main():
             fr.forward(params, check=True)
         return fr
 
-    def make_step(fr, params, dLv, events=None):
+    def make_step(fr, params, dLv, events=None, gr=None):
+        gr = grads if gr is None else gr
+
         def step():
             if events is not None:
                 events[0].record(stream)
@@ -430,11 +507,11 @@ def main():
             if events is not None:
                 events[3].record(stream)
             if events is None:
-                fr.backward(params, dLv, grads)  # both adjoint steps in one call
+                fr.backward(params, dLv, gr)  # both adjoint steps in one call
             else:
                 fr.backward_2d(dLv)
                 events[4].record(stream)
-                fr.project_backward(params, grads)
+                fr.project_backward(params, gr)
                 events[5].record(stream)
         return step
 
@@ -615,11 +692,85 @@ def main():
                    pipeline="inputs of step k+1 in and outputs of step k-1 out on copy streams while step k "
                             "computes (each buffer set's step replayed as a CUDA graph)")
 
+    # ---- rotation variants on the same Gaussians and views: the No-4DRot fast path (spatial rotation
+    # from q_left, block-diagonal Sigma: no Schur complement, no velocity term) and static 3DGS (no time
+    # axis, plain SH colour: the first (L+1)^2 coefficient rows); eager stage times as for the 4D path
+    variants = None
+    if rank == 0 and not args.no_variants:
+        def stage_times(params):
+            fr = sized_frame(views, opts, params)
+            gr = {k: torch.empty(params[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
+            evv = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)] for _ in range(3)]
+            for _ in range(2):
+                make_step(fr, params, dL, gr=gr)()
+            for e in evv:
+                make_step(fr, params, dL, e, gr)()
+            torch.cuda.synchronize()
+            st = {s_: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in evv) for i, s_ in enumerate(stages)}
+            st = {k: round(v, 4) for k, v in st.items()}
+            total = sum(st.values())
+            out_ = dict(stage_ms=st, ms_per_step=round(total, 4), mpix_s=round(npix / (total * 1e-3) / 1e6, 3),
+                        visible_splats=fr.last_counters.n_visible, pairs=fr.last_counters.n_pairs)
+            del fr, gr
+            return out_
+
+        nb3 = 3 * (G["sh_degree"] + 1) ** 2
+        variants = {
+            "4d": dict(stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                       ms_per_step=round(sum(stage_ms.values()), 4),
+                       mpix_s=round(npix / (sum(stage_ms.values()) * 1e-3) / 1e6, 3), visible_splats=nvis,
+                       pairs=npairs),
+            "no_4drot": stage_times(dict(p, rotation=N.ROT_SPATIAL)),
+            "static_3dgs": stage_times(dict(p, shs=p["shs"][:nb3].contiguous(), n_freq=0,
+                                            rotation=N.ROT_STATIC)),
+            "note": "eager stage times, same Gaussians, views and launch shape; no_4drot: q_left as the spatial "
+                    "rotation, q_right unused; static_3dgs: no time axis, SH degree 3 colour without Fourier "
+                    "orders (the images differ, so do the splat and pair counts)",
+        }
+
+    # ---- depth and optical-flow maps (f2) through the same lists: eager stage times
+    aux = None
+    if rank == 0 and not args.no_aux:
+        fra = sized_frame(views, dict(opts, aux_channels=1), p)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(2):
+            fra.slice_project(p)
+            fra.bin_sort()
+            fra.render()
+            fra.render_aux()
+        reps, t_sp, t_r, t_a = 5, 0.0, 0.0, 0.0
+        for _ in range(reps):
+            evs[0].record(stream)
+            fra.slice_project(p)
+            evs[1].record(stream)
+            fra.bin_sort()
+            fra.render()
+            evs[2].record(stream)
+            fra.render_aux()
+            evs[3].record(stream)
+            torch.cuda.synchronize()
+            t_sp += evs[0].elapsed_time(evs[1])
+            t_r += evs[1].elapsed_time(evs[2])
+            t_a += evs[2].elapsed_time(evs[3])
+        aux = dict(render_aux_ms=round(t_a / reps, 4), mpix_s=round(npix / (t_a / reps * 1e-3) / 1e6, 3),
+                   slice_project_ms_with_aux=round(t_sp / reps, 4), bin_sort_plus_render_ms=round(t_r / reps, 4),
+                   what="fgs4d_render_aux: accumulated depth and the flow of the projected conditional means "
+                        "over one frame (flow_dt 1/300), composited through the image's sorted lists")
+        del fra
+
+    # ---- training step (config 4: 3M Gaussians, 8 views), one CUDA graph per step
+    train = None
+    if rank == 0 and world == 1 and not args.no_train:
+        r = measure_train(args, steps=5, per_view=True, e2e=False)
+        train = {k: r[k] for k in ("value", "ms_per_step", "steps_per_s", "pixels_per_step", "per_view_fp32",
+                                   "train_vs_per_view_fp32", "final_loss", "status", "clocks", "gpu_launches")}
+        train["unit"] = "Mpix/s"
+        train["config"] = r["config"]
+
     # ---- CPU baseline (oracle on the host cores, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sample = oracle_sample(G, views, budget_s=15.0)
-        cpu = dict(value=v, unit="Mpix/s", cores=1, kind="oracle", sample=sample)
+        cpu = cpu_baseline_both(G, views)
 
     if rank == 0:
         out = dict(metric="Mpix/s fwd+bwd (4DGS render, 1M Gaussians, 1352x1014)", value=round(value, 3),
@@ -638,6 +789,7 @@ def main():
                    single_view=single, batched_fp32=batched_fp32,
                    batched_vs_single_fp32=round(value / world / single["mpix_s"], 3) if single else None,
                    roofline=roofline, stage_roofline=stage_roof, work=work, cpu_baseline=cpu, e2e=e2e, clocks=clk,
+                   rotation_variants=variants, depth_flow_maps=aux, train_step=train,
                    gpu_launches=int(launches))
         print(json.dumps(out))
     if dist:

@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define FGS4D_ABI_VERSION 3
+#define FGS4D_ABI_VERSION 4
 #define FGS4D_MAX_VIEWS 128   /* views per call */
 #define FGS4D_MAX_SH_DEGREE 3 /* L */
 #define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
@@ -74,8 +74,15 @@ typedef enum { FGS4D_F32 = 0, FGS4D_BF16 = 1 } fgs4d_dtype;
    of a unit quaternion (w, x, y, z); Sigma is block-diagonal, so the slice
    at t leaves the mean and the spatial covariance unchanged (no motion) and
    p(t) depends on s_t alone.  q_right is not read (may be NULL) and its
-   gradient is zero. */
-typedef enum { FGS4D_ROT_4D = 0, FGS4D_ROT_SPATIAL = 1 } fgs4d_rotation;
+   gradient is zero.  The kernels take the short path: no Schur complement,
+   no velocity term, and neither in the adjoint.
+   FGS4D_ROT_STATIC: the special case of a static 3D Gaussian (3D Gaussian
+   splatting, the model 4DGS extends in Sec. 3.1): as FGS4D_ROT_SPATIAL with
+   no time axis at all.  mu_t and s_t are not read, p(t) = 1 for every view,
+   and the 4DSH time basis is evaluated at dt = 0 (every Fourier order counts
+   with cos 0 = 1; n_freq = 0 gives plain SH colour).  The gradients of
+   q_right, mu_t and log s_t are zero. */
+typedef enum { FGS4D_ROT_4D = 0, FGS4D_ROT_SPATIAL = 1, FGS4D_ROT_STATIC = 2 } fgs4d_rotation;
 
 /* Device status bits written into the state (see fgs4d_counters.status). */
 #define FGS4D_STATUS_PAIR_OVERFLOW 1u  /* more (splat, tile) pairs than capacity */

@@ -177,7 +177,8 @@ fgs4d_status check_gaussians(const fgs4d_gaussians* g, DevGauss* d) {
         return FGS4D_ERR_INVALID_ARG;
     if (!(g->period > 0.0f) || !isfinite(g->period)) return FGS4D_ERR_INVALID_ARG;
     if (g->shs_dtype != FGS4D_F32 && g->shs_dtype != FGS4D_BF16) return FGS4D_ERR_INVALID_ARG;
-    if (g->rotation != FGS4D_ROT_4D && g->rotation != FGS4D_ROT_SPATIAL) return FGS4D_ERR_INVALID_ARG;
+    if (g->rotation != FGS4D_ROT_4D && g->rotation != FGS4D_ROT_SPATIAL && g->rotation != FGS4D_ROT_STATIC)
+        return FGS4D_ERR_INVALID_ARG;
     if (g->n > 0) {
         const void* ptrs[] = {g->mu, g->log_scale, g->q_left, g->opacity_logit, g->shs};
         for (const void* p : ptrs)
@@ -195,7 +196,7 @@ fgs4d_status check_gaussians(const fgs4d_gaussians* g, DevGauss* d) {
     d->K = g->n_freq;
     d->inv_period = 1.0f / g->period;
     d->shs_bf16 = g->shs_dtype == FGS4D_BF16;
-    d->rot3 = g->rotation == FGS4D_ROT_SPATIAL;
+    d->rot = g->rotation;
     return FGS4D_OK;
 }
 

@@ -64,8 +64,17 @@ struct DevGauss {
     int K;
     float inv_period;
     int shs_bf16;
-    int rot3;  // No-4DRot variant: q_left rotates x, y, z only; q_right is not read
+    int rot;  // fgs4d_rotation: how Sigma is formed and sliced (RotMode)
 };
+
+// fgs4d_rotation as a compile-time kernel parameter.  kRot4D: R = L(q_l) R(q_r)
+// (Eq. 8) and the slice of Eq. 9-10.  kRotSpatial (No-4DRot): R =
+// blockdiag(R3(q_l), 1), so Sigma is block-diagonal and the slice reduces to
+// mu_{xyz|t} = mu_xyz, Sigma_{xyz|t} = Sigma_xyz, p(t) from s_t alone: no
+// Schur complement, no velocity term.  kRotStatic (3D Gaussian splatting):
+// as kRotSpatial with no time axis at all: mu_t and s_t are not read, p = 1
+// and the 4DSH time basis is evaluated at dt = 0.
+enum RotMode : int { kRot4D = 0, kRotSpatial = 1, kRotStatic = 2 };
 
 // ---------------------------------------------------------------------------
 // Per-frame state layout (byte offsets into the caller's state buffer).
@@ -327,15 +336,18 @@ __device__ __forceinline__ void spatial_rotation(const T* q, T* R) {
     R[12] = T(0);                       R[13] = T(0);                       R[14] = T(0);                       R[15] = one;
 }
 
+template <int kMode>
 __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
+    constexpr bool k4D = kMode == kRot4D, kStatic = kMode == kRotStatic;
     const size_t n = (size_t)G.n;
     float ls[4], ql[4], qr[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        c.mu[i] = __ldg(G.mu + i * n + g);
-        ls[i] = __ldg(G.log_s + i * n + g);
+        // a static Gaussian has no time axis: mu_t and s_t are not read
+        c.mu[i] = (kStatic && i == 3) ? 0.0f : __ldg(G.mu + i * n + g);
+        ls[i] = (kStatic && i == 3) ? 0.0f : __ldg(G.log_s + i * n + g);
         ql[i] = __ldg(G.ql + i * n + g);
-        qr[i] = G.rot3 ? (i == 0 ? 1.0f : 0.0f) : __ldg(G.qr + i * n + g);
+        qr[i] = k4D ? __ldg(G.qr + i * n + g) : (i == 0 ? 1.0f : 0.0f);
     }
     const float logit = __ldg(G.logit + g);
     c.alpha = 1.0f / (1.0f + expf(-logit));
@@ -352,12 +364,28 @@ __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
         c.qrn[i] = qr[i] / c.nr;
     }
     c.ok = finite && nl2 > 1e-24f && nr2 > 1e-24f;
-    if (G.rot3) {
+    if constexpr (!k4D) {
+        // Sigma = blockdiag(R3 diag(s_xyz^2) R3^T, s_t^2): the 3x3 block only
         spatial_rotation(c.qln, c.R);
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < 16; i++) c.M[i] = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 4; j++) c.M[i * 4 + j] = c.R[i * 4 + j] * c.s[j];
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) c.M[i * 4 + j] = c.R[i * 4 + j] * c.s[j];
+        c.M[15] = kStatic ? 0.0f : c.s[3];
+#pragma unroll
+        for (int i = 0; i < 16; i++) c.S[i] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = i; j < 3; j++) {
+                const float acc = fmaf(c.M[i * 4 + 0], c.M[j * 4 + 0],
+                                       fmaf(c.M[i * 4 + 1], c.M[j * 4 + 1], c.M[i * 4 + 2] * c.M[j * 4 + 2]));
+                c.S[i * 4 + j] = acc;
+                c.S[j * 4 + i] = acc;
+            }
+        c.S[15] = c.M[15] * c.M[15];
     } else {
         float Lm[16], Rm[16];
         left_matrix(c.qln, Lm);
@@ -372,26 +400,27 @@ __device__ __forceinline__ void load_core(const DevGauss& G, int g, Core& c) {
                 c.R[i * 4 + j] = acc;
                 c.M[i * 4 + j] = acc * c.s[j];
             }
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = i; j < 4; j++) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) acc = fmaf(c.M[i * 4 + k], c.M[j * 4 + k], acc);
+                c.S[i * 4 + j] = acc;
+                c.S[j * 4 + i] = acc;
+            }
     }
-#pragma unroll
-    for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int j = i; j < 4; j++) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < 4; k++) acc = fmaf(c.M[i * 4 + k], c.M[j * 4 + k], acc);
-            c.S[i * 4 + j] = acc;
-            c.S[j * 4 + i] = acc;
-        }
 }
 
-// Same Sigma in double precision (fallback for ill-conditioned slices).
+// Same Sigma in double precision (fallback for ill-conditioned slices of
+// the 4D rotation; the block-diagonal modes form no Schur complement).
 static __device__ __noinline__ void core_sigma_f64(const DevGauss& G, int g, double* Sd) {
     const size_t n = (size_t)G.n;
     double ql[4], qr[4], s[4], nl = 0.0, nr = 0.0;
     for (int i = 0; i < 4; i++) {
         ql[i] = (double)G.ql[i * n + g];
-        qr[i] = G.rot3 ? (i == 0 ? 1.0 : 0.0) : (double)G.qr[i * n + g];
+        qr[i] = (double)G.qr[i * n + g];
         s[i] = exp((double)G.log_s[i * n + g]);
         nl += ql[i] * ql[i];
         nr += qr[i] * qr[i];
@@ -403,22 +432,16 @@ static __device__ __noinline__ void core_sigma_f64(const DevGauss& G, int g, dou
         qr[i] /= nr;
     }
     double M[16];
-    if (G.rot3) {
-        spatial_rotation(ql, M);
-        for (int i = 0; i < 4; i++)
-            for (int j = 0; j < 4; j++) M[i * 4 + j] *= s[j];
-    } else {
-        const double a = ql[0], b = ql[1], c = ql[2], d = ql[3];
-        const double Lm[16] = {a, -b, -c, -d, b, a, -d, c, c, d, a, -b, d, -c, b, a};
-        const double p = qr[0], q = qr[1], r = qr[2], t = qr[3];
-        const double Rm[16] = {p, -q, -r, -t, q, p, t, -r, r, -t, p, q, t, r, -q, p};
-        for (int i = 0; i < 4; i++)
-            for (int j = 0; j < 4; j++) {
-                double acc = 0.0;
-                for (int k = 0; k < 4; k++) acc += Lm[i * 4 + k] * Rm[k * 4 + j];
-                M[i * 4 + j] = acc * s[j];
-            }
-    }
+    const double a = ql[0], b = ql[1], c = ql[2], d = ql[3];
+    const double Lm[16] = {a, -b, -c, -d, b, a, -d, c, c, d, a, -b, d, -c, b, a};
+    const double p = qr[0], q = qr[1], r = qr[2], t = qr[3];
+    const double Rm[16] = {p, -q, -r, -t, q, p, t, -r, r, -t, p, q, t, r, -q, p};
+    for (int i = 0; i < 4; i++)
+        for (int j = 0; j < 4; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < 4; k++) acc += Lm[i * 4 + k] * Rm[k * 4 + j];
+            M[i * 4 + j] = acc * s[j];
+        }
     for (int i = 0; i < 4; i++)
         for (int j = 0; j < 4; j++) {
             double acc = 0.0;
@@ -447,8 +470,24 @@ struct ViewGeom {
     int tiles;       // number of touched tiles (0 = invisible)
 };
 
+template <int kMode>
 __device__ __forceinline__ void slice_view(const Core& c, const DevView& V, const DevOpts& O, const DevGauss& G, int g,
                                            ViewGeom& w, bool allow_f64) {
+    if constexpr (kMode != kRot4D) {
+        // block-diagonal Sigma: nothing to condition on; p(t) from s_t alone (static: p = 1)
+        w.dt = kMode == kRotStatic ? 0.0f : V.t - c.mu[3];
+        w.p = kMode == kRotStatic ? 1.0f : expf(-0.5f * w.dt * w.dt / c.S[15]);
+        w.mu3[0] = c.mu[0];
+        w.mu3[1] = c.mu[1];
+        w.mu3[2] = c.mu[2];
+        w.S3[0] = c.S[0];
+        w.S3[1] = c.S[1];
+        w.S3[2] = c.S[2];
+        w.S3[3] = c.S[5];
+        w.S3[4] = c.S[6];
+        w.S3[5] = c.S[10];
+        return;
+    }
     const float sig = c.S[15];
     w.dt = V.t - c.mu[3];
     w.p = expf(-0.5f * w.dt * w.dt / sig);

@@ -134,7 +134,7 @@ __device__ __forceinline__ void color_adjoint(const T* __restrict__ sh, size_t n
 }
 
 // 5 blocks per SM (96 registers, no spills): one more than 128 registers allow
-template <int L>
+template <int L, int kMode>
 __global__ void __launch_bounds__(kSliceThreads, 5) slice_project_kernel(
     const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, SplatRecord* __restrict__ rec,  // or SplatRecordH
     uint32_t* __restrict__ tiles_touched, uint32_t* __restrict__ depth_key, uint32_t* __restrict__ counters,
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kSliceThreads, 5) slice_project_kernel(
         staged = s_coef;
     }
     Core c;
-    load_core(G, g, c);
+    load_core<kMode>(G, g, c);
     if (!c.ok) {
         atomicOr(&counters[2], FGS4D_STATUS_NONFINITE);
         for (int v = 0; v < VS.n; v++) tiles_touched[(size_t)v * n + g] = 0u;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kSliceThreads, 5) slice_project_kernel(
         const DevView& V = VS.v[v];
         const size_t idx = (size_t)v * n + g;
         ViewGeom w;
-        slice_view(c, V, O, G, g, w, true);
+        slice_view<kMode>(c, V, O, G, g, w, true);
         const bool vis = (w.p >= O.p_min) && project_view(c, V, O, w, true);
         if (!vis) {
             tiles_touched[idx] = 0u;
@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(kSliceThreads, 5) slice_project_kernel(
         }
         tiles_touched[idx] = (uint32_t)w.tiles;
         depth_key[idx] = __float_as_uint(w.xc[2]);
-        if (aux) {
+        if (aux && kMode != kRot4D) {  // block-diagonal Sigma: the conditional mean does not move
+            aux[idx] = make_float4(w.xc[2], 0.0f, 0.0f, 0.0f);
+        } else if (aux) {
             // Eq. 9: mu_{xyz|t} moves by Sigma_{xyz,t} / Sigma_tt per unit of t; the flow is the
             // displacement of its projection over flow_dt (0 where the moved mean is behind the camera)
             const float k = O.flow_dt / c.S[15];
@@ -250,6 +252,7 @@ __device__ __forceinline__ float segment_sum(float x, int lane, int seg_last) {
 // (or blockdiag(R3(q_l), 1) without 4D rotation).  GS: dL/dSigma with its
 // upper triangle filled (symmetrised here); galpha: dL/dsigmoid(logit).
 // Writes the gradients of log s, q_l, q_r and the opacity logit.
+template <int kMode>
 __device__ __forceinline__ void covariance_chain(const DevGauss& G, const Core& cl, float* GS, float galpha,
                                                  float* gls, float* gql, float* gqr, float& glogit) {
 #pragma unroll
@@ -259,6 +262,40 @@ __device__ __forceinline__ void covariance_chain(const DevGauss& G, const Core& 
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < i; j++) GS[i * 4 + j] = GS[j * 4 + i];
+    if constexpr (kMode != kRot4D) {
+        // Sigma = blockdiag(M3 M3^T, s_t^2), M3 = R3(q) diag(s_xyz): the 3x3 block,
+        // then dL/dlog s_t = 2 s_t^2 dL/dSigma_tt (zero without a time axis)
+        float dR[9];
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float dM = 2.0f * fmaf(GS[i * 4 + 0], cl.M[0 * 4 + k],
+                                             fmaf(GS[i * 4 + 1], cl.M[1 * 4 + k], GS[i * 4 + 2] * cl.M[2 * 4 + k]));
+                dR[i * 3 + k] = dM * cl.s[k];
+                gls[k] = fmaf(dM, cl.R[i * 4 + k], gls[k]);
+            }
+#pragma unroll
+        for (int k = 0; k < 3; k++) gls[k] *= cl.s[k];
+        gls[3] = kMode == kRotStatic ? 0.0f : 2.0f * GS[15] * cl.M[15] * cl.M[15];
+        const float w = cl.qln[0], x = cl.qln[1], y = cl.qln[2], z = cl.qln[3];
+        const float* d = dR;  // row-major 3x3
+        const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
+        const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[3] - 2.0f * x * d[4] - w * d[5] + z * d[6] +
+                                 w * d[7] - 2.0f * x * d[8]);
+        const float gy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] +
+                                 z * d[7] - 2.0f * y * d[8]);
+        const float gz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.0f * z * d[4] +
+                                 y * d[5] + x * d[6] + y * d[7]);
+        const float gq[4] = {gw, gx, gy, gz};
+        float dq = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; i++) dq = fmaf(gq[i], cl.qln[i], dq);
+#pragma unroll
+        for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * cl.qln[i]) / cl.nl;
+        glogit = galpha * cl.alpha * (1.0f - cl.alpha);
+        return;
+    }
     float dR[16];
 #pragma unroll
     for (int i = 0; i < 4; i++)
@@ -273,56 +310,37 @@ __device__ __forceinline__ void covariance_chain(const DevGauss& G, const Core& 
         }
 #pragma unroll
     for (int k = 0; k < 4; k++) gls[k] *= cl.s[k];
-    if (G.rot3) {
-        // R = blockdiag(R3(q), 1): dL/dq through the 3x3 block, then the normalisation
-        const float w = cl.qln[0], x = cl.qln[1], y = cl.qln[2], z = cl.qln[3];
-        const float* d = dR;
-        const float gw = 2.0f * (-z * d[1] + y * d[2] + z * d[4] - x * d[6] - y * d[8] + x * d[9]);
-        const float gx = 2.0f * (y * d[1] + z * d[2] + y * d[4] - 2.0f * x * d[5] - w * d[6] + z * d[8] +
-                                 w * d[9] - 2.0f * x * d[10]);
-        const float gy = 2.0f * (-2.0f * y * d[0] + x * d[1] + w * d[2] + x * d[4] + z * d[6] - w * d[8] +
-                                 z * d[9] - 2.0f * y * d[10]);
-        const float gz = 2.0f * (-2.0f * z * d[0] - w * d[1] + x * d[2] + w * d[4] - 2.0f * z * d[5] +
-                                 y * d[6] + x * d[8] + y * d[9]);
-        const float gq[4] = {gw, gx, gy, gz};
-        float dq = 0.0f;
+    float Lm[16], Rm[16];
+    left_matrix(cl.qln, Lm);
+    right_matrix(cl.qrn, Rm);
+    float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
 #pragma unroll
-        for (int i = 0; i < 4; i++) dq = fmaf(gq[i], cl.qln[i], dq);
+    for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int i = 0; i < 4; i++) gql[i] = (gq[i] - dq * cl.qln[i]) / cl.nl;
-    } else {
-        float Lm[16], Rm[16];
-        left_matrix(cl.qln, Lm);
-        right_matrix(cl.qrn, Rm);
-        float D[16], E[16];  // D = dR Rm^T, E = Lm^T dR
+        for (int j = 0; j < 4; j++) {
+            float x = 0.0f, y = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                float x = 0.0f, y = 0.0f;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
-                    y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
-                }
-                D[i * 4 + j] = x;
-                E[i * 4 + j] = y;
+            for (int k = 0; k < 4; k++) {
+                x = fmaf(dR[i * 4 + k], Rm[j * 4 + k], x);
+                y = fmaf(Lm[k * 4 + i], dR[k * 4 + j], y);
             }
-        const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
-                             -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
-        const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
-                             -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
-        float dl = 0.0f, dr = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            dl = fmaf(gl[i], cl.qln[i], dl);
-            dr = fmaf(gr[i], cl.qrn[i], dr);
+            D[i * 4 + j] = x;
+            E[i * 4 + j] = y;
         }
+    const float gl[4] = {D[0] + D[5] + D[10] + D[15], -D[1] + D[4] - D[11] + D[14],
+                         -D[2] + D[7] + D[8] - D[13], -D[3] - D[6] + D[9] + D[12]};
+    const float gr[4] = {E[0] + E[5] + E[10] + E[15], -E[1] + E[4] + E[11] - E[14],
+                         -E[2] - E[7] + E[8] + E[13], -E[3] + E[6] - E[9] + E[12]};
+    float dl = 0.0f, dr = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            gql[i] = (gl[i] - dl * cl.qln[i]) / cl.nl;
-            gqr[i] = (gr[i] - dr * cl.qrn[i]) / cl.nr;
-        }
+    for (int i = 0; i < 4; i++) {
+        dl = fmaf(gl[i], cl.qln[i], dl);
+        dr = fmaf(gr[i], cl.qrn[i], dr);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        gql[i] = (gl[i] - dl * cl.qln[i]) / cl.nl;
+        gqr[i] = (gr[i] - dr * cl.qrn[i]) / cl.nr;
     }
     glogit = galpha * cl.alpha * (1.0f - cl.alpha);
 }
@@ -336,7 +354,7 @@ __device__ constexpr int kGsumEntry[10] = {0, 1, 2, 3, 5, 6, 7, 10, 11, 15};
 // kDefer: add the per-Gaussian sums to gsum ([kGsumRows][n], zeroed) and
 // leave Eq. 7-8 to covariance_chain_kernel; else each segment's first lane
 // runs it (gsum unused).
-template <int L, bool kDefer>
+template <int L, bool kDefer, int kMode>
 __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
     const DevGauss G, const __grid_constant__ ViewSet VS, const DevOpts O, float4* __restrict__ grad2d,
     const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count, const fgs4d_gaussian_grads out,
@@ -364,14 +382,13 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         float galpha = 0.0f, m2d = 0.0f, mt = 0.0f;
         Core c;
         c.ok = false;
-        if (active) load_core(G, g, c);
+        if (active) load_core<kMode>(G, g, c);
         if (active && c.ok) {
             const float sig = c.S[15];
-            const float b[3] = {c.S[3], c.S[7], c.S[11]};
             const size_t idx = sid;
             const DevView& V = VS.v[v];
             ViewGeom w;
-            slice_view(c, V, O, G, g, w, true);
+            slice_view<kMode>(c, V, O, G, g, w, true);
             if (!project_view(c, V, O, w, true)) {  // cannot happen for a binned splat; keep the slot defined
                 grad2d[3 * idx + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
@@ -392,7 +409,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 for (int j = 0; j < NB; j++) wsum[j] = 0.0f;
                 float ddt = 0.0f;
                 float graws[3];
-                const float arg1 = 2.0f * w.dt * G.inv_period;
+                const float arg1 = 2.0f * w.dt * G.inv_period;  // 0 for a static Gaussian
                 const float c1 = cospif(arg1), s1 = sinpif(arg1);
                 if (G.shs_bf16)
                     color_adjoint<L>(reinterpret_cast<const __nv_bfloat16*>(G.shs) + g, n, G.K, c1, s1,
@@ -479,23 +496,36 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 // ---- Eq. 9, Eq. 10 ----
                 const float dp = dae * c.alpha;
                 galpha += dae * w.p;
-                const float isig = 1.0f / sig;
-                float G3b[3];
-                G3b[0] = G3[0] * b[0] + G3[1] * b[1] + G3[2] * b[2];
-                G3b[1] = G3[1] * b[0] + G3[3] * b[1] + G3[4] * b[2];
-                G3b[2] = G3[2] * b[0] + G3[4] * b[1] + G3[5] * b[2];
-                const float mb = dmu3[0] * b[0] + dmu3[1] * b[1] + dmu3[2] * b[2];
-                const float bGb = b[0] * G3b[0] + b[1] * G3b[1] + b[2] * G3b[2];
-                const float dt = w.dt;
-                const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
-                ddt += mb * isig - dp * w.p * dt * isig;
+                if constexpr (kMode == kRot4D) {
+                    const float b[3] = {c.S[3], c.S[7], c.S[11]};
+                    const float isig = 1.0f / sig;
+                    float G3b[3];
+                    G3b[0] = G3[0] * b[0] + G3[1] * b[1] + G3[2] * b[2];
+                    G3b[1] = G3[1] * b[0] + G3[3] * b[1] + G3[4] * b[2];
+                    G3b[2] = G3[2] * b[0] + G3[4] * b[1] + G3[5] * b[2];
+                    const float mb = dmu3[0] * b[0] + dmu3[1] * b[1] + dmu3[2] * b[2];
+                    const float bGb = b[0] * G3b[0] + b[1] * G3b[1] + b[2] * G3b[2];
+                    const float dt = w.dt;
+                    const float dsig = (-mb * dt + bGb + dp * w.p * 0.5f * dt * dt) * isig * isig;
+                    ddt += mb * isig - dp * w.p * dt * isig;
+    #pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
+                        GS[i * 4 + 3] += 0.5f * dbi;
+                    }
+                    GS[15] += dsig;
+                } else if constexpr (kMode == kRotSpatial) {
+                    // no coupling: the mean and the spatial covariance do not depend on t;
+                    // p = exp(-dt^2 / (2 s_t^2)) alone carries the time
+                    const float isig = 1.0f / sig, dt = w.dt;
+                    GS[15] += dp * w.p * 0.5f * dt * dt * isig * isig;
+                    ddt += -dp * w.p * dt * isig;
+                } else {
+                    ddt = 0.0f;  // static: no time axis
+                }
                 mt = fabsf(ddt);  // this view's |dL/dmu_t|
     #pragma unroll
-                for (int i = 0; i < 3; i++) {
-                    const float dbi = (dmu3[i] * dt - 2.0f * G3b[i]) * isig;
-                    GS[i * 4 + 3] += 0.5f * dbi;
-                    gmu[i] += dmu3[i];
-                }
+                for (int i = 0; i < 3; i++) gmu[i] += dmu3[i];
                 gmu[3] -= ddt;
                 GS[0] += G3[0];
                 GS[1] += G3[1];
@@ -503,7 +533,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
                 GS[5] += G3[3];
                 GS[6] += G3[4];
                 GS[10] += G3[5];
-                GS[15] += dsig;
             }
         }
         // ---- sum the segment (all visible views of this Gaussian in this warp) ----
@@ -540,12 +569,12 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
         // The leader rebuilds the rotation chain from the parameters, so that R, M and the
         // quaternions are not live across the per-splat part above.
         Core cl;
-        load_core(G, g, cl);
+        load_core<kMode>(G, g, cl);
 
         // ---- Eq. 7-8 once per Gaussian: Sigma = M M^T, M = R S, R = L(q_l) R(q_r) ----
         float gls[4] = {0, 0, 0, 0}, gql[4] = {0, 0, 0, 0}, gqr[4] = {0, 0, 0, 0}, glogit = 0.0f;
         if (c.ok) {
-            covariance_chain(G, cl, GS, galpha, gls, gql, gqr, glogit);
+            covariance_chain<kMode>(G, cl, GS, galpha, gls, gql, gqr, glogit);
         } else {
     #pragma unroll
             for (int i = 0; i < 4; i++) gmu[i] = 0.0f;
@@ -556,7 +585,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
             atomicAdd(&out.mu[i * n + g], gmu[i]);
             atomicAdd(&out.log_scale[i * n + g], gls[i]);
             atomicAdd(&out.q_left[i * n + g], gql[i]);
-            if (!G.rot3) atomicAdd(&out.q_right[i * n + g], gqr[i]);
+            if (kMode == kRot4D) atomicAdd(&out.q_right[i * n + g], gqr[i]);
         }
         atomicAdd(&out.opacity_logit[g], glogit);
         if (out.mean2d_abs) atomicAdd(&out.mean2d_abs[g], m2d);
@@ -567,6 +596,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
 // Eq. 7-8 backwards, one thread per Gaussian, from the sums the projection
 // adjoint left in gsum (all zero: no visible splat, gradients stay zero).
 // The outputs were zeroed and each Gaussian has one thread: plain stores.
+template <int kMode>
 __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G, const float* __restrict__ gsum,
                                                                const fgs4d_gaussian_grads out) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -582,15 +612,15 @@ __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G,
     const float galpha = gsum[10 * n + g];
     if (!any && galpha == 0.0f) return;
     Core cl;
-    load_core(G, g, cl);
+    load_core<kMode>(G, g, cl);
     if (!cl.ok) return;
     float gls[4], gql[4], gqr[4], glogit;
-    covariance_chain(G, cl, GS, galpha, gls, gql, gqr, glogit);
+    covariance_chain<kMode>(G, cl, GS, galpha, gls, gql, gqr, glogit);
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         out.log_scale[i * n + g] = gls[i];
         out.q_left[i * n + g] = gql[i];
-        if (!G.rot3) out.q_right[i * n + g] = gqr[i];
+        if (kMode == kRot4D) out.q_right[i * n + g] = gqr[i];
     }
     out.opacity_logit[g] = glogit;
 }
@@ -667,11 +697,20 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
     auto* tt = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
     auto* dk = reinterpret_cast<uint32_t*>(state + lay.depth_key);
     auto* aux = O.aux ? reinterpret_cast<float4*>(state + lay.aux) : nullptr;
-    switch (G.L) {
-        case 0: slice_project_kernel<0><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
-        case 1: slice_project_kernel<1><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
-        case 2: slice_project_kernel<2><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
-        default: slice_project_kernel<3><<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); break;
+    auto go = [&](auto kernel) { kernel<<<blocks, threads, smem, st>>>(G, VS, O, rec, tt, dk, counters, aux, stage); };
+    switch (G.L * 3 + G.rot) {
+        case 0: go(slice_project_kernel<0, kRot4D>); break;
+        case 1: go(slice_project_kernel<0, kRotSpatial>); break;
+        case 2: go(slice_project_kernel<0, kRotStatic>); break;
+        case 3: go(slice_project_kernel<1, kRot4D>); break;
+        case 4: go(slice_project_kernel<1, kRotSpatial>); break;
+        case 5: go(slice_project_kernel<1, kRotStatic>); break;
+        case 6: go(slice_project_kernel<2, kRot4D>); break;
+        case 7: go(slice_project_kernel<2, kRotSpatial>); break;
+        case 8: go(slice_project_kernel<2, kRotStatic>); break;
+        case 9: go(slice_project_kernel<3, kRot4D>); break;
+        case 10: go(slice_project_kernel<3, kRotSpatial>); break;
+        default: go(slice_project_kernel<3, kRotStatic>); break;
     }
     count_launches(1);
     return cudaGetLastError();
@@ -712,7 +751,7 @@ static int local_sm_count() {
 // Adjoint of slice/project/4DSH: Gaussian-major list of the visible splats,
 // geometry kernel over that list (outputs accumulated, so cleared first),
 // then the coefficient kernel.
-template <int L>
+template <int L, int kMode>
 static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt, float4* g2,
                             uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp, float* gsum,
                             const fgs4d_gaussian_grads& grads, cudaStream_t st) {
@@ -731,11 +770,12 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
     const uint64_t S = (uint64_t)n * VS.n;
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((S + kBwdThreads - 1) / kBwdThreads, 16ull * sms));
     if (gsum) {
-        project_backward_kernel<L, true><<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, gsum);
-        covariance_chain_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, gsum, grads);
+        project_backward_kernel<L, true, kMode>
+            <<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, gsum);
+        covariance_chain_kernel<kMode><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, gsum, grads);
         count_launches(1);
     } else {
-        project_backward_kernel<L, false>
+        project_backward_kernel<L, false, kMode>
             <<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, nullptr);
     }
     launch_sh_k<L>(G, VS.n, g2, grads.shs, st);
@@ -746,12 +786,22 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
 static cudaError_t launch_pb_any(const DevGauss& G, const ViewSet& VS, const DevOpts& O, const uint32_t* tt,
                                  float4* g2, uint32_t* list, uint32_t* list_count, uint32_t* scan_tmp, float* gsum,
                                  const fgs4d_gaussian_grads& grads, cudaStream_t st) {
-    switch (G.L) {
-        case 0: return launch_pb<0>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
-        case 1: return launch_pb<1>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
-        case 2: return launch_pb<2>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
-        default: return launch_pb<3>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st);
+#define FGS4D_PB(l, m) return launch_pb<l, m>(G, VS, O, tt, g2, list, list_count, scan_tmp, gsum, grads, st)
+    switch (G.L * 3 + G.rot) {
+        case 0: FGS4D_PB(0, kRot4D);
+        case 1: FGS4D_PB(0, kRotSpatial);
+        case 2: FGS4D_PB(0, kRotStatic);
+        case 3: FGS4D_PB(1, kRot4D);
+        case 4: FGS4D_PB(1, kRotSpatial);
+        case 5: FGS4D_PB(1, kRotStatic);
+        case 6: FGS4D_PB(2, kRot4D);
+        case 7: FGS4D_PB(2, kRotSpatial);
+        case 8: FGS4D_PB(2, kRotStatic);
+        case 9: FGS4D_PB(3, kRot4D);
+        case 10: FGS4D_PB(3, kRotSpatial);
+        default: FGS4D_PB(3, kRotStatic);
     }
+#undef FGS4D_PB
 }
 
 // The list of visible splats goes to the state's pair-offset section (free
@@ -786,6 +836,7 @@ cudaError_t launch_project_backward_from(const DevGauss& G, const ViewSet& VS, c
 // and z ~ N(0, I) supplied by the caller.  One thread per sample; index[j]
 // names the Gaussian, z and out are [4][m].  A Gaussian with non-finite or
 // zero-norm parameters yields NaN.
+template <int kMode>
 __global__ void __launch_bounds__(256) sample_split_kernel(const DevGauss G, const int64_t* __restrict__ index,
                                                            const float* __restrict__ z, int64_t m,
                                                            float* __restrict__ out) {
@@ -798,7 +849,7 @@ __global__ void __launch_bounds__(256) sample_split_kernel(const DevGauss G, con
         return;
     }
     Core c;
-    load_core(G, (int)gi, c);
+    load_core<kMode>(G, (int)gi, c);
     float zz[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) zz[k] = z[k * m + j];
@@ -814,7 +865,13 @@ __global__ void __launch_bounds__(256) sample_split_kernel(const DevGauss G, con
 cudaError_t launch_sample_split(const DevGauss& G, const int64_t* index, const float* z, int64_t m, float* out,
                                 cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
-    sample_split_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(G, index, z, m, out);
+    const unsigned blocks = (unsigned)((m + 255) / 256);
+    if (G.rot == kRot4D)
+        sample_split_kernel<kRot4D><<<blocks, 256, 0, st>>>(G, index, z, m, out);
+    else if (G.rot == kRotSpatial)
+        sample_split_kernel<kRotSpatial><<<blocks, 256, 0, st>>>(G, index, z, m, out);
+    else
+        sample_split_kernel<kRotStatic><<<blocks, 256, 0, st>>>(G, index, z, m, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -29,7 +29,7 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-r
 MAX_VIEWS = 128
 TILE = 16
 F32, BF16 = 0, 1
-ROT_4D, ROT_SPATIAL = 0, 1
+ROT_4D, ROT_SPATIAL, ROT_STATIC = 0, 1, 2
 STATUS_PAIR_OVERFLOW = 1
 STATUS_NONFINITE = 2
 
@@ -199,7 +199,7 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                        "fgs4d_render_backward", "fgs4d_read_counters", "fgs4d_state_layout",
                        "fgs4d_render_backward_2d", "fgs4d_project_backward"):
                 getattr(L, fn).restype = ci
-            assert L.fgs4d_abi_version() == 3, "libfgs4d ABI version mismatch"
+            assert L.fgs4d_abi_version() == 4, "libfgs4d ABI version mismatch"
             _lib = L
     return _lib
 

@@ -111,6 +111,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.fgs4d_slice_project(ctypes.byref(g5), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     g6 = N.Gaussians(16, 32, 48, None, 80, 96, 10, 1, 1, 1.0, 0, N.ROT_4D)  # 4D rotation needs q_right
     assert lib.fgs4d_slice_project(ctypes.byref(g6), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
+    g7 = N.Gaussians(16, 32, 48, None, 80, 96, 10, 1, 1, 1.0, 0, N.ROT_STATIC + 1)  # one past the last mode
+    assert lib.fgs4d_slice_project(ctypes.byref(g7), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     g4 = N.Gaussians(16, 32, 48, 64, 80, 97, 10, 1, 1, 1.0, 0)  # misaligned shs
     assert lib.fgs4d_slice_project(ctypes.byref(g4), v, 2, ctypes.byref(o), 256, 1 << 20, None) == 1
     # state smaller than the fixed part
@@ -129,7 +131,7 @@ STRUCTS = [("Gaussians", "fgs4d_gaussians"), ("View", "fgs4d_view"), ("Options",
 
 # binding constants mirroring the header's: (name in native.py, C expression)
 CONSTANTS = [("MAX_VIEWS", "FGS4D_MAX_VIEWS"), ("TILE", "FGS4D_TILE"), ("F32", "FGS4D_F32"), ("BF16", "FGS4D_BF16"),
-             ("ROT_4D", "FGS4D_ROT_4D"), ("ROT_SPATIAL", "FGS4D_ROT_SPATIAL"),
+             ("ROT_4D", "FGS4D_ROT_4D"), ("ROT_SPATIAL", "FGS4D_ROT_SPATIAL"), ("ROT_STATIC", "FGS4D_ROT_STATIC"),
              ("STATUS_PAIR_OVERFLOW", "FGS4D_STATUS_PAIR_OVERFLOW"), ("STATUS_NONFINITE", "FGS4D_STATUS_NONFINITE"),
              ("NOALLOC_MAX_SPLATS", "FGS4D_NOALLOC_MAX_SPLATS")]
 

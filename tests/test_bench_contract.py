@@ -69,3 +69,16 @@ def test_traffic_line_follows_the_kernel_sources(monkeypatch):
     got2, note2 = bench.profiled_traffic("render_backward_2d")
     assert got2 is None and "stale" in note2
     assert bench.profiled_traffic("slice_project") == (None, "no ncu summary for this kernel")
+
+
+def test_cpu_baseline_reports_one_core_and_all_cores():
+    """The CPU baseline times the oracle single-threaded and split over all
+    host cores in the same run, with the core count and the CPU model."""
+    from paper_2310_10642_gb300 import inputs as I
+    c = I.config(3, n=2000, n_views=2, scale=0.05)
+    cb = bench.cpu_baseline_both(c["gaussians"], c["views"], budget_s=0.5)
+    host = bench.host_cpu()
+    assert cb["cores"] == host["cores"] >= 1 and isinstance(cb["cpu_model"], str) and cb["cpu_model"]
+    assert cb["kind"] == "oracle" and cb["value"] > 0 and f"{host['cores']} thread" in cb["sample"]
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "1 thread" in st["sample"]
