@@ -46,7 +46,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.fgs4d_abi_version() == 3
+    assert lib.fgs4d_abi_version() == 4
     for code in range(6):
         assert len(lib.fgs4d_status_string(code)) > 0
 
