@@ -152,6 +152,49 @@ def profiled_traffic(stage: str):
     return int(fields["dram_bytes_per_launch_full_workload"]), f"profiles/{name} (2-view capture scaled to 20 views)"
 
 
+def block_diagonal_pair(q):
+    """Per Gaussian the quaternion pair (q_l, q_r) whose rotation
+    L(q_l) R(q_r) (Eq. 8) is blockdiag(R3(q), 1), R3 the usual rotation of the
+    unit quaternion q = (w, x, y, z): the No-4DRot model written as a general
+    4D one, so that the 4D kernels render exactly the scene of the spatial
+    fast path.  With x -> q_l x q_r and e0 = its image of 1, x -> q_l x
+    conj(q_l) is x -> (M x) conj(e0), a conjugation whose 3x3 block gives q_l
+    (Shepperd's method); then q_r = conj(q_l) e0.  Host-side input
+    preparation for a timing comparison, float64 numpy."""
+    import numpy as np
+
+    def ham(p_, q_):
+        a1, b1, c1, d1 = p_
+        a2, b2, c2, d2 = q_
+        return np.stack([a1 * a2 - b1 * b2 - c1 * c2 - d1 * d2, a1 * b2 + b1 * a2 + c1 * d2 - d1 * c2,
+                         a1 * c2 - b1 * d2 + c1 * a2 + d1 * b2, a1 * d2 + b1 * c2 - c1 * b2 + d1 * a2])
+
+    conj = np.array([1.0, -1.0, -1.0, -1.0])[:, None]
+    q = np.asarray(q, np.float64)
+    w, x, y, z = q / np.linalg.norm(q, axis=0)
+    n = q.shape[1]
+    M = np.zeros((4, 4, n))
+    M[:3, :3] = [[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                 [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                 [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]]
+    M[3, 3] = 1.0
+    e0 = M[:, 0]
+    R = np.stack([ham(M[:, k], e0 * conj)[1:] for k in (1, 2, 3)], axis=1)
+    tr = R[0, 0] + R[1, 1] + R[2, 2]
+    s_ = [2 * np.sqrt(np.maximum(v, 1e-30)) for v in (tr + 1, 1 + R[0, 0] - R[1, 1] - R[2, 2],
+                                                      1 + R[1, 1] - R[0, 0] - R[2, 2], 1 + R[2, 2] - R[0, 0] - R[1, 1])]
+    cand = [np.stack([s_[0] / 4, (R[2, 1] - R[1, 2]) / s_[0], (R[0, 2] - R[2, 0]) / s_[0], (R[1, 0] - R[0, 1]) / s_[0]]),
+            np.stack([(R[2, 1] - R[1, 2]) / s_[1], s_[1] / 4, (R[0, 1] + R[1, 0]) / s_[1], (R[0, 2] + R[2, 0]) / s_[1]]),
+            np.stack([(R[0, 2] - R[2, 0]) / s_[2], (R[0, 1] + R[1, 0]) / s_[2], s_[2] / 4, (R[1, 2] + R[2, 1]) / s_[2]]),
+            np.stack([(R[1, 0] - R[0, 1]) / s_[3], (R[0, 2] + R[2, 0]) / s_[3], (R[1, 2] + R[2, 1]) / s_[3], s_[3] / 4])]
+    pick = np.where(tr > 0, 0, np.where((R[0, 0] > R[1, 1]) & (R[0, 0] > R[2, 2]), 1,
+                                        np.where(R[1, 1] > R[2, 2], 2, 3)))
+    a = np.zeros((4, n))
+    for k in range(4):
+        a[:, pick == k] = cand[k][:, pick == k]
+    return a, ham(a * conj, e0)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -715,17 +758,27 @@ def main():
             return out_
 
         nb3 = 3 * (G["sh_degree"] + 1) ** 2
+        ql_eq, qr_eq = block_diagonal_pair(G["ql"])
+        p_eq = dict(p, ql=torch.as_tensor(ql_eq, dtype=torch.float32).cuda(),
+                    qr=torch.as_tensor(qr_eq, dtype=torch.float32).cuda(), rotation=N.ROT_4D)
+        fast = stage_times(dict(p, rotation=N.ROT_SPATIAL))
+        general = stage_times(p_eq)
+        per_g = ("slice_project", "project_backward")
         variants = {
             "4d": dict(stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
                        ms_per_step=round(sum(stage_ms.values()), 4),
                        mpix_s=round(npix / (sum(stage_ms.values()) * 1e-3) / 1e6, 3), visible_splats=nvis,
                        pairs=npairs),
-            "no_4drot": stage_times(dict(p, rotation=N.ROT_SPATIAL)),
+            "no_4drot": fast,
+            "no_4drot_through_4d_kernels": general,
+            "no_4drot_saved_ms": dict({k: round(general["stage_ms"][k] - fast["stage_ms"][k], 4) for k in per_g},
+                                      step=round(general["ms_per_step"] - fast["ms_per_step"], 4)),
             "static_3dgs": stage_times(dict(p, shs=p["shs"][:nb3].contiguous(), n_freq=0,
                                             rotation=N.ROT_STATIC)),
-            "note": "eager stage times, same Gaussians, views and launch shape; no_4drot: q_left as the spatial "
-                    "rotation, q_right unused; static_3dgs: no time axis, SH degree 3 colour without Fourier "
-                    "orders (the images differ, so do the splat and pair counts)",
+            "note": "eager stage times, same Gaussians, views and launch shape.  no_4drot: q_left as the spatial "
+                    "rotation (block-diagonal Sigma), rendered by the fast path and, as the same scene, by the 4D "
+                    "kernels through the equivalent quaternion pair of Eq. 8 (identical splats and pairs); "
+                    "static_3dgs: no time axis, SH degree 3 colour without Fourier orders",
         }
 
     # ---- depth and optical-flow maps (f2) through the same lists: eager stage times

@@ -82,3 +82,20 @@ def test_cpu_baseline_reports_one_core_and_all_cores():
     assert cb["kind"] == "oracle" and cb["value"] > 0 and f"{host['cores']} thread" in cb["sample"]
     st = cb["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0 and "1 thread" in st["sample"]
+
+
+def test_block_diagonal_pair_reproduces_the_spatial_rotation(oracle):
+    """The quaternion pair the bench uses to render the No-4DRot scene
+    through the 4D kernels gives, under the oracle's Eq. 8, exactly
+    blockdiag(R3(q), 1) with R3 the textbook rotation of the unit quaternion."""
+    import numpy as np
+    q = np.random.default_rng(5).normal(size=(4, 300))
+    a, b = bench.block_diagonal_pair(q)
+    for g in range(300):
+        w, x, y, z = q[:, g] / np.linalg.norm(q[:, g])
+        R3 = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                       [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                       [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        want = np.eye(4)
+        want[:3, :3] = R3
+        np.testing.assert_allclose(oracle.rotation4(a[:, g], b[:, g]), want, atol=1e-13)
