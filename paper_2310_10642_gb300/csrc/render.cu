@@ -334,36 +334,26 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
                 const auto row0 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby, a.y));
                 const auto col1 = Form<Rec>::col(a.z, a.w, __fsub_rn(fbx + TP::off_x(1), a.x));
                 const auto row1 = Form<Rec>::row(a.w, b.x, __fsub_rn(fby + TP::off_y(2), a.y));
-                // alpha of every pixel of the lane the visit reaches, 0 where the pixel
-                // takes no part: independent chains, interleaved by the scheduler
-                float al[P];
 #pragma unroll
                 for (int k = 0; k < P; k++) {
-                    al[k] = 0.0f;
-                    if (!(sub >> k & 1u)) continue;  // warp-uniform
-                    if (kStats && (act >> k & 1u)) {
+                    if (!(act >> k & 1u)) continue;
+                    if (kStats) {
                         const float dx = __fsub_rn(fbx + TP::off_x(k), a.x), dy = __fsub_rn(fby + TP::off_y(k), a.y);
                         st_eval++;
                         st_box += (fabsf(dx) <= c.y && fabsf(dy) <= c.z);
                     }
                     const float p2 = Form<Rec>::combine(a.z, (k & 1) ? col1 : col0, (k >> 1) ? row1 : row0);
-                    const float alpha = min_nan(O.alpha_max, __fmul_rn(b.y, ex2_approx(p2)));
-                    const bool ok = (act >> k & 1u) && (Form<Rec>::kNeverPositive || p2 <= 0.0f) &&
-                                    alpha >= O.alpha_min;  // also rejects a NaN power2
-                    al[k] = ok ? alpha : 0.0f;
-                }
-                // the in-order updates, with selects: a pixel that takes no part keeps its
-                // state bit for bit (its weight is 0)
-#pragma unroll
-                for (int k = 0; k < P; k++) {
-                    if (!(sub >> k & 1u)) continue;  // warp-uniform
-                    const float alpha = al[k];
+                    if (!Form<Rec>::kNeverPositive && !(p2 <= 0.0f)) continue;
+                    const float araw = __fmul_rn(b.y, ex2_approx(p2));
+                    const float alpha = min_nan(O.alpha_max, araw);
+                    if (!(alpha >= O.alpha_min)) continue;  // also a NaN power2
                     const float Tn = T[k] * (1.0f - alpha);
-                    const bool stop = alpha > 0.0f && Tn < O.T_min;
-                    const bool blend = alpha > 0.0f && !stop;
-                    live &= stop ? ~(1u << k) : 0xffffffffu;
-                    if (kStats) st_blend += blend;
-                    const float w = blend ? alpha * T[k] : 0.0f;
+                    if (Tn < O.T_min) {
+                        live &= ~(1u << k);
+                        continue;
+                    }
+                    if (kStats) st_blend++;
+                    const float w = alpha * T[k];
                     if constexpr (kAux) {
                         const float4 x = s_x[j];
                         C0[k] = fmaf(x.x, w, C0[k]);
@@ -374,8 +364,8 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
                         C1[k] = fmaf(b.w, w, C1[k]);
                         C2[k] = fmaf(c.x, w, C2[k]);
                     }
-                    T[k] = blend ? Tn : T[k];
-                    last[k] = blend ? pos1 : last[k];
+                    T[k] = Tn;
+                    last[k] = pos1;
                 }
                 // a pixel stopped: the warp is done once all of its pixels have
                 if (__any_sync(F, act & ~live) && __all_sync(F, live == 0u)) hits = 0u;
