@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
                     help="mixed: BF16 4DSH coefficients + 16-bit conic records; fp32: plain FP32 storage")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly, not as a CUDA graph")
+    ap.add_argument("--groups", type=int, default=2,
+                    help="view groups of the timed step, each on a stream of its own (1: one batch on one stream)")
     ap.add_argument("--tile", default="auto", choices=["auto", "16", "32"],
                     help="compositing tile side; auto: the autotuner times both on this workload")
     ap.add_argument("--bin-size", default="auto", choices=["auto", "16", "32", "64"],
@@ -594,8 +596,25 @@ def main():
     torch.cuda.synchronize()
     stage_ms = {s: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, s in enumerate(stages)}
 
-    # headline: K whole steps, replayed as one CUDA graph each (or launched eagerly with --no-graph)
-    step = make_step(frame, p, dL)
+    # headline: K whole steps, replayed as one CUDA graph each (or launched eagerly with --no-graph).
+    # With groups > 1 the step runs the views as contiguous groups on as many streams, so that one
+    # group's latency-bound stages overlap another's compositing kernels (same images; gradients
+    # summed group after group)
+    if args.groups > 1:
+        sframe = R.SplitFrame(n, views, opts, groups=args.groups)
+        sframe.forward(p, check=True)
+        for fr_ in sframe.frames:
+            c_ = fr_.last_counters
+            if c_.n_pairs * 1.1 > fr_.pair_capacity:
+                fr_._alloc(int(c_.n_pairs * 1.15) + 4096)
+        sframe.forward(p, check=True)
+        run_frame = sframe
+
+        def step():
+            sframe.step(p, dL, grads)
+    else:
+        run_frame = frame
+        step = make_step(frame, p, dL)
     graph, per_step = (None, 0) if args.no_graph else capture(step)
     run = step if graph is None else graph.replay
     for _ in range(max(3, args.warmup)):
@@ -720,7 +739,7 @@ def main():
         # pipelined across steps (HostPipeline): the inputs of step k + 1 go in and the outputs of
         # step k - 1 come out on copy streams while step k computes
         from paper_2310_10642_gb300.pipeline import HostPipeline
-        pipe = HostPipeline(frame, p)
+        pipe = HostPipeline(run_frame, p)
         pipe.run([(host_p, host_dL)] * 4, [(host_img, host_g)] * 4)  # both slots captured before timing
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -832,6 +851,7 @@ def main():
                    dtype="f32", data="synthetic",
                    config=dict(WORKLOAD, n=n, views=V, tile=opts["tile_size"], bin=opts["bin_size"],
                                batch_depth=opts["batch_depth"],
+                               view_groups=[list(g) for g in run_frame.parts] if args.groups > 1 else [[0, V]],
                                autotune=tune_table, precision=(
                        "BF16 4DSH coefficients, 16-bit Cholesky conics; FP32 arithmetic" if mixed else "FP32"),
                        cuda_graph=graph is not None,

@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define FGS4D_ABI_VERSION 4
+#define FGS4D_ABI_VERSION 5
 #define FGS4D_MAX_VIEWS 128   /* views per call */
 #define FGS4D_MAX_SH_DEGREE 3 /* L */
 #define FGS4D_MAX_FREQ 4      /* K: Fourier orders 0..K */
@@ -151,10 +151,16 @@ typedef struct {
                          tile) pairs to sort when splats span several compositing tiles;
                          results do not depend on it.  "Tile" in the counters, the state
                          layout and fgs4d_bin_sort means a binning tile. */
+    int accumulate_grads; /* 0: the backward calls overwrite grads; 1: they add to grads'
+                         current contents (nothing is zeroed), so that the adjoints of
+                         several view batches of one parameter set sum into one set of
+                         gradients, one call after another on the same stream (calls that
+                         overlap on the GPU race on the outputs) */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but
-   always float32.  Overwritten (not accumulated) by fgs4d_render_backward. */
+   always float32.  Overwritten by fgs4d_render_backward, or added to with the
+   option accumulate_grads. */
 typedef struct {
     float *mu;
     float *log_scale;

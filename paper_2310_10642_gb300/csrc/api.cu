@@ -44,6 +44,7 @@ fgs4d_status check_options(const fgs4d_options* o) {
         return FGS4D_ERR_INVALID_ARG;
     if (o->aux_channels != 0 && o->aux_channels != 1) return FGS4D_ERR_INVALID_ARG;
     if (!isfinite(o->flow_dt)) return FGS4D_ERR_INVALID_ARG;
+    if (o->accumulate_grads != 0 && o->accumulate_grads != 1) return FGS4D_ERR_INVALID_ARG;
     return FGS4D_OK;
 }
 
@@ -64,6 +65,7 @@ DevOpts dev_options(const fgs4d_options* o) {
     d.batch = o->batch_depth;
     d.aux = o->aux_channels;
     d.flow_dt = o->flow_dt;
+    d.accumulate = o->accumulate_grads;
     return d;
 }
 
@@ -270,6 +272,7 @@ void fgs4d_default_options(fgs4d_options* o) {
     o->aux_channels = 0;
     o->flow_dt = 1.0f / 300.0f;
     o->bin_size = 0;
+    o->accumulate_grads = 0;
 }
 
 int64_t fgs4d_total_pixels(const fgs4d_view* views, int n_views) {

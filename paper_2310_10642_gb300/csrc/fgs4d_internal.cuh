@@ -49,6 +49,7 @@ struct DevOpts {
     int batch;  // records staged per shared-memory batch while compositing: 32..256
     int aux;    // store per-splat depth and flow (fgs4d_render_aux)
     float flow_dt;
+    int accumulate;  // backward: add to the gradient outputs instead of overwriting them
 };
 
 // Gaussian parameters (SoA) as the kernels see them.

@@ -595,10 +595,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) project_backward_kernel(
 
 // Eq. 7-8 backwards, one thread per Gaussian, from the sums the projection
 // adjoint left in gsum (all zero: no visible splat, gradients stay zero).
-// The outputs were zeroed and each Gaussian has one thread: plain stores.
+// The outputs were zeroed (or hold the sums to add to) and each Gaussian has
+// one thread.
 template <int kMode>
 __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G, const float* __restrict__ gsum,
-                                                               const fgs4d_gaussian_grads out) {
+                                                               const fgs4d_gaussian_grads out, int accumulate) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G.n) return;
     const size_t n = (size_t)G.n;
@@ -616,13 +617,15 @@ __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G,
     if (!cl.ok) return;
     float gls[4], gql[4], gqr[4], glogit;
     covariance_chain<kMode>(G, cl, GS, galpha, gls, gql, gqr, glogit);
+    // one thread per Gaussian: plain stores, or read-add-write when accumulating
+    auto put = [accumulate](float* p, float v) { *p = accumulate ? *p + v : v; };
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        out.log_scale[i * n + g] = gls[i];
-        out.q_left[i * n + g] = gql[i];
-        if (kMode == kRot4D) out.q_right[i * n + g] = gqr[i];
+        put(&out.log_scale[i * n + g], gls[i]);
+        put(&out.q_left[i * n + g], gql[i]);
+        if (kMode == kRot4D) put(&out.q_right[i * n + g], gqr[i]);
     }
-    out.opacity_logit[g] = glogit;
+    put(&out.opacity_logit[g], glogit);
 }
 
 // Coefficient part of the adjoint (Eq. 11): dL/dk[f][j][ch] = sum over the
@@ -632,7 +635,8 @@ __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G,
 // consecutive Gaussians, so every load and store is coalesced.
 template <int L, int K1>
 __global__ void __launch_bounds__(256, 4) sh_backward_kernel(int n, int n_views, float inv_period,
-                                                          const float4* __restrict__ grad2d, float* __restrict__ gshs) {
+                                                          const float4* __restrict__ grad2d, float* __restrict__ gshs,
+                                                          int accumulate) {
     constexpr int NB = (L + 1) * (L + 1);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int ch = blockIdx.y;
@@ -665,7 +669,10 @@ __global__ void __launch_bounds__(256, 4) sh_backward_kernel(int n, int n_views,
 #pragma unroll
     for (int f = 0; f < K1; f++)
 #pragma unroll
-        for (int j = 0; j < NB; j++) gshs[(size_t)((f * NB + j) * 3 + ch) * n + g] = acc[f][j];
+        for (int j = 0; j < NB; j++) {
+            float* dst = gshs + (size_t)((f * NB + j) * 3 + ch) * n + g;
+            *dst = accumulate ? *dst + acc[f][j] : acc[f][j];
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -717,21 +724,19 @@ cudaError_t launch_slice_project(const DevGauss& G, const ViewSet& VS, const Dev
 }
 
 template <int L, int K1>
-static void launch_sh(const DevGauss& G, int n_views, const float4* g2, float* gshs,
-                      cudaStream_t st) {
+static void launch_sh(const DevGauss& G, int n_views, const float4* g2, float* gshs, int acc, cudaStream_t st) {
     const dim3 grid((G.n + 255) / 256, 3);
-    sh_backward_kernel<L, K1><<<grid, 256, 0, st>>>(G.n, n_views, G.inv_period, g2, gshs);
+    sh_backward_kernel<L, K1><<<grid, 256, 0, st>>>(G.n, n_views, G.inv_period, g2, gshs, acc);
 }
 
 template <int L>
-static void launch_sh_k(const DevGauss& G, int n_views, const float4* g2, float* gshs,
-                        cudaStream_t st) {
+static void launch_sh_k(const DevGauss& G, int n_views, const float4* g2, float* gshs, int acc, cudaStream_t st) {
     switch (G.K) {
-        case 0: launch_sh<L, 1>(G, n_views, g2, gshs, st); break;
-        case 1: launch_sh<L, 2>(G, n_views, g2, gshs, st); break;
-        case 2: launch_sh<L, 3>(G, n_views, g2, gshs, st); break;
-        case 3: launch_sh<L, 4>(G, n_views, g2, gshs, st); break;
-        default: launch_sh<L, 5>(G, n_views, g2, gshs, st); break;
+        case 0: launch_sh<L, 1>(G, n_views, g2, gshs, acc, st); break;
+        case 1: launch_sh<L, 2>(G, n_views, g2, gshs, acc, st); break;
+        case 2: launch_sh<L, 3>(G, n_views, g2, gshs, acc, st); break;
+        case 3: launch_sh<L, 4>(G, n_views, g2, gshs, acc, st); break;
+        default: launch_sh<L, 5>(G, n_views, g2, gshs, acc, st); break;
     }
 }
 
@@ -757,11 +762,14 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
                             const fgs4d_gaussian_grads& grads, cudaStream_t st) {
     const size_t n = (size_t)G.n;
     cudaError_t e = cudaSuccess;
-    float* outs[5] = {grads.mu, grads.log_scale, grads.q_left, grads.q_right, grads.opacity_logit};
-    const size_t rows[5] = {4, 4, 4, 4, 1};
-    for (int i = 0; i < 5 && e == cudaSuccess; i++) e = cudaMemsetAsync(outs[i], 0, rows[i] * n * sizeof(float), st);
-    if (e == cudaSuccess && grads.mean2d_abs) e = cudaMemsetAsync(grads.mean2d_abs, 0, n * sizeof(float), st);
-    if (e == cudaSuccess && grads.mu_t_abs) e = cudaMemsetAsync(grads.mu_t_abs, 0, n * sizeof(float), st);
+    if (!O.accumulate) {  // accumulating: the outputs hold the sums to add to
+        float* outs[5] = {grads.mu, grads.log_scale, grads.q_left, grads.q_right, grads.opacity_logit};
+        const size_t rows[5] = {4, 4, 4, 4, 1};
+        for (int i = 0; i < 5 && e == cudaSuccess; i++)
+            e = cudaMemsetAsync(outs[i], 0, rows[i] * n * sizeof(float), st);
+        if (e == cudaSuccess && grads.mean2d_abs) e = cudaMemsetAsync(grads.mean2d_abs, 0, n * sizeof(float), st);
+        if (e == cudaSuccess && grads.mu_t_abs) e = cudaMemsetAsync(grads.mu_t_abs, 0, n * sizeof(float), st);
+    }
     if (e == cudaSuccess && gsum) e = cudaMemsetAsync(gsum, 0, kGsumRows * n * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const int sms = local_sm_count();
@@ -772,13 +780,13 @@ static cudaError_t launch_pb(const DevGauss& G, const ViewSet& VS, const DevOpts
     if (gsum) {
         project_backward_kernel<L, true, kMode>
             <<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, gsum);
-        covariance_chain_kernel<kMode><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, gsum, grads);
+        covariance_chain_kernel<kMode><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, gsum, grads, O.accumulate);
         count_launches(1);
     } else {
         project_backward_kernel<L, false, kMode>
             <<<blocks, kBwdThreads, 0, st>>>(G, VS, O, g2, list, list_count, grads, nullptr);
     }
-    launch_sh_k<L>(G, VS.n, g2, grads.shs, st);
+    launch_sh_k<L>(G, VS.n, g2, grads.shs, O.accumulate, st);
     count_launches(2);
     return cudaGetLastError();
 }

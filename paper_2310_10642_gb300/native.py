@@ -99,7 +99,8 @@ class Options(ctypes.Structure):
                 ("alpha_max", ctypes.c_float), ("T_min", ctypes.c_float), ("dilation", ctypes.c_float),
                 ("clamp_fov", ctypes.c_float), ("record_fp16", ctypes.c_int), ("schur_cond", ctypes.c_float),
                 ("conic_cond", ctypes.c_float), ("tile_size", ctypes.c_int), ("batch_depth", ctypes.c_int),
-                ("aux_channels", ctypes.c_int), ("flow_dt", ctypes.c_float), ("bin_size", ctypes.c_int)]
+                ("aux_channels", ctypes.c_int), ("flow_dt", ctypes.c_float), ("bin_size", ctypes.c_int),
+                ("accumulate_grads", ctypes.c_int)]
 
 
 class GaussianGrads(ctypes.Structure):
@@ -199,7 +200,7 @@ def lib(path: str | None = None) -> ctypes.CDLL:
                        "fgs4d_render_backward", "fgs4d_read_counters", "fgs4d_state_layout",
                        "fgs4d_render_backward_2d", "fgs4d_project_backward"):
                 getattr(L, fn).restype = ci
-            assert L.fgs4d_abi_version() == 4, "libfgs4d ABI version mismatch"
+            assert L.fgs4d_abi_version() == 5, "libfgs4d ABI version mismatch"
             _lib = L
     return _lib
 

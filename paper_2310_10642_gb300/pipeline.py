@@ -1,7 +1,7 @@
 """Forward + backward over host-resident batches with the copies overlapped.
 
-``HostPipeline`` runs ``Frame`` steps (slice/project, bin/sort, render,
-backward) whose inputs (parameters, dL/dimage) come from pinned host memory
+``HostPipeline`` runs ``Frame`` (or ``SplitFrame``) steps (slice/project,
+bin/sort, render, backward) whose inputs (parameters, dL/dimage) come from pinned host memory
 and whose outputs (image, gradients) go back to pinned host memory.  While
 step k computes on the current stream, the inputs of step k + 1 are copied
 in and the outputs of step k - 1 copied out on two copy streams, through two
@@ -52,10 +52,7 @@ class HostPipeline:
 
     def _step(self, sl):
         fr = self.frame
-        fr.slice_project(sl["p"])
-        fr.bin_sort()
-        fr.render()
-        fr.backward(sl["p"], sl["dL"], sl["g"])
+        fr.step(sl["p"], sl["dL"], sl["g"])
         sl["img"].copy_(fr.image, non_blocking=True)
 
     def _compute(self, sl):

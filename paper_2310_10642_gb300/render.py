@@ -68,7 +68,9 @@ class Frame:
     """
 
     def __init__(self, n: int, views: list, options: dict | None = None, pair_capacity: int | None = None,
-                 device="cuda"):
+                 device="cuda", outputs: tuple | None = None):
+        """outputs: optional (image, final_T, n_last) device tensors of the
+        packed sizes to render into (e.g. views of a larger packed buffer)."""
         if len(views) < 1 or len(views) > N.MAX_VIEWS:
             raise ValueError(f"1..{N.MAX_VIEWS} views per frame")
         self.n = int(n)
@@ -86,9 +88,15 @@ class Frame:
         if pair_capacity is None:
             tiles = sum(((int(v["width"]) + 15) // 16) * ((int(v["height"]) + 15) // 16) for v in self.views)
             pair_capacity = max(1 << 16, min(self.n * self.nv * 8, tiles * 4096))
-        self.image = torch.empty(3 * self.total_pixels, device=self.device, dtype=torch.float32)
-        self.final_T = torch.empty(self.total_pixels, device=self.device, dtype=torch.float32)
-        self.n_last = torch.empty(self.total_pixels, device=self.device, dtype=torch.int32)
+        if outputs is not None:
+            self.image, self.final_T, self.n_last = outputs
+            if (self.image.numel() != 3 * self.total_pixels or self.final_T.numel() != self.total_pixels
+                    or self.n_last.numel() != self.total_pixels or self.n_last.dtype != torch.int32):
+                raise ValueError("outputs do not match the views' packed sizes")
+        else:
+            self.image = torch.empty(3 * self.total_pixels, device=self.device, dtype=torch.float32)
+            self.final_T = torch.empty(self.total_pixels, device=self.device, dtype=torch.float32)
+            self.n_last = torch.empty(self.total_pixels, device=self.device, dtype=torch.int32)
         self._alloc(int(pair_capacity))
 
     def _alloc(self, cap: int):
@@ -252,6 +260,15 @@ class Frame:
                                  _stream(stream))
         return grads
 
+    def step(self, params: dict, dL_dimage: torch.Tensor, grads: dict, stream=None):
+        """One whole step on one stream: slice_project, bin_sort, render and
+        both adjoint steps (no check of the pair capacity; size it first with
+        forward())."""
+        self.slice_project(params, stream)
+        self.bin_sort(stream)
+        self.render(stream)
+        self.backward(params, dL_dimage, grads, stream)
+
     def grad2d(self) -> torch.Tensor:
         """[views, n, 9] view of the state: dL/d(u, v, a, b, c, alpha_eff, R, G, B) per splat, valid
         between backward_2d() and project_backward() (which reuses the section)."""
@@ -273,6 +290,138 @@ class Frame:
 
     def layout(self) -> N.StateLayoutInfo:
         return N.fgs4d_state_layout(self.n, self.c_views, self.nv, self.c_opts, self.state_bytes)
+
+
+def split_views(views: list, groups: int) -> list:
+    """Contiguous groups of views with balanced pixel counts: the first view
+    index of every group after the first."""
+    pix = [int(v["width"]) * int(v["height"]) for v in views]
+    groups = max(1, min(int(groups), len(views)))
+    total, cuts, acc = sum(pix), [], 0
+    for i, q in enumerate(pix):
+        if len(cuts) < groups - 1 and acc > 0 and acc + q / 2 > total * (len(cuts) + 1) / groups:
+            cuts.append(i)
+        acc += q
+    return cuts
+
+
+class SplitFrame:
+    """The views of one batch as contiguous sub-batches, each a Frame of its
+    own on a stream of its own: the groups run the whole step concurrently
+    (one group's latency-bound stages -- slice/project, binning, projection
+    adjoint -- overlap another's compositing kernels), rendering into one
+    packed image.  The groups' projection adjoints run one after the other
+    and add into one set of gradients (option accumulate_grads).  Views are
+    independent, so images, T and n_last are those of one Frame over all the
+    views (n_last counts positions in each group's own lists); gradients
+    differ only in the order of FP32 sums.  The streams fork from and join
+    the caller's stream, so a step can be captured in a CUDA graph."""
+
+    def __init__(self, n: int, views: list, options: dict | None = None, groups: int = 2,
+                 pair_capacity: int | None = None, device="cuda", cuts: list | None = None):
+        """cuts: the first view index of every group after the first (default:
+        split_views(views, groups), groups balanced by pixel count)."""
+        self.n = int(n)
+        self.views = list(views)
+        self.nv = len(self.views)
+        self.device = torch.device(device)
+        cuts = split_views(self.views, groups) if cuts is None else [int(c) for c in cuts]
+        if cuts != sorted(set(cuts)) or (cuts and (cuts[0] < 1 or cuts[-1] >= self.nv)):
+            raise ValueError("cuts must be increasing view indices in 1 .. len(views) - 1")
+        bounds = [0] + cuts + [self.nv]
+        self.parts = [(a, b) for a, b in zip(bounds[:-1], bounds[1:])]
+        self.pix_offsets, off = [], 0
+        for v in self.views:
+            self.pix_offsets.append(off)
+            off += int(v["width"]) * int(v["height"])
+        self.total_pixels = off
+        self.image = torch.empty(3 * off, device=self.device, dtype=torch.float32)
+        self.final_T = torch.empty(off, device=self.device, dtype=torch.float32)
+        self.n_last = torch.empty(off, device=self.device, dtype=torch.int32)
+        self.frames, self.ranges = [], []
+        for gi, (a, b) in enumerate(self.parts):
+            p0 = self.pix_offsets[a]
+            p1 = self.pix_offsets[b] if b < self.nv else off
+            opts = dict(options or {}, accumulate_grads=int(gi > 0))
+            outs = (self.image[3 * p0: 3 * p1], self.final_T[p0:p1], self.n_last[p0:p1])
+            cap = None if pair_capacity is None else max(1 << 16, int(pair_capacity * (p1 - p0) / max(off, 1)))
+            self.frames.append(Frame(n, self.views[a:b], opts, cap, device, outputs=outs))
+            self.ranges.append((p0, p1))
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in self.frames]
+        self._pb_done = [torch.cuda.Event() for _ in self.frames]
+
+    @property
+    def groups(self) -> int:
+        return len(self.frames)
+
+    def _dL(self, dL_dimage: torch.Tensor, gi: int) -> torch.Tensor:
+        p0, p1 = self.ranges[gi]
+        return dL_dimage[3 * p0: 3 * p1]
+
+    def forward(self, params: dict, stream=None, check: bool = True) -> torch.Tensor:
+        """Every group's slice_project -> bin_sort -> render, concurrently;
+        check=True sizes each group's pair capacity as Frame.forward does."""
+        if check:
+            for fr in self.frames:
+                fr.forward(params, stream, check=True)
+            return self.image
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        for fr, s in zip(self.frames, self.streams):
+            s.wait_stream(cur)
+            fr.slice_project(params, s)
+            fr.bin_sort(s)
+            fr.render(s)
+        for s in self.streams:
+            cur.wait_stream(s)
+        return self.image
+
+    def step(self, params: dict, dL_dimage: torch.Tensor, grads: dict, stream=None):
+        """One whole step: each group's forward and compositing adjoint on its
+        own stream, the projection adjoints chained group after group into
+        grads (the first overwrites, the others add)."""
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        dL = dL_dimage.contiguous()
+        for gi, (fr, s) in enumerate(zip(self.frames, self.streams)):
+            s.wait_stream(cur)
+            fr.slice_project(params, s)
+            fr.bin_sort(s)
+            fr.render(s)
+            fr.backward_2d(self._dL(dL, gi), s)
+            if gi > 0:
+                s.wait_event(self._pb_done[gi - 1])
+            fr.project_backward(params, grads, s)
+            self._pb_done[gi].record(s)
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def backward(self, params: dict, dL_dimage: torch.Tensor, grads: dict | None = None, stream=None) -> dict:
+        """The adjoint of the last forward: compositing adjoints concurrently,
+        projection adjoints chained into grads."""
+        if grads is None:
+            grads = {k: torch.empty(params[k].shape, device=self.device, dtype=torch.float32) for k in PARAM_KEYS}
+        cur = stream if stream is not None else torch.cuda.current_stream()
+        dL = dL_dimage.contiguous()
+        for gi, (fr, s) in enumerate(zip(self.frames, self.streams)):
+            s.wait_stream(cur)
+            fr.backward_2d(self._dL(dL, gi), s)
+            if gi > 0:
+                s.wait_event(self._pb_done[gi - 1])
+            fr.project_backward(params, grads, s)
+            self._pb_done[gi].record(s)
+        for s in self.streams:
+            cur.wait_stream(s)
+        return grads
+
+    def counters(self) -> list:
+        return [fr.counters() for fr in self.frames]
+
+    def split(self, packed: torch.Tensor, channels: int = 3) -> list:
+        out = []
+        for v, off in zip(self.views, self.pix_offsets):
+            w, h = int(v["width"]), int(v["height"])
+            out.append(packed[channels * off: channels * (off + w * h)].view(channels, h, w) if channels > 1
+                       else packed[off: off + w * h].view(h, w))
+        return out
 
 
 class Render4DGS(torch.autograd.Function):

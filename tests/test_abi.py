@@ -46,7 +46,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.fgs4d_abi_version() == 4
+    assert lib.fgs4d_abi_version() == 5
     for code in range(6):
         assert len(lib.fgs4d_status_string(code)) > 0
 
@@ -90,7 +90,8 @@ def test_invalid_arguments_rejected_on_host(lib):
     # bad options
     for field, val in (("alpha_max", 1.5), ("alpha_min", 0.0), ("near_z", 0.0), ("T_min", float("nan")),
                        ("tile_size", 8), ("batch_depth", 100), ("batch_depth", 512), ("record_fp16", 2),
-                       ("bin_size", 8), ("bin_size", 48), ("bin_size", 128), ("bin_size", -16)):
+                       ("bin_size", 8), ("bin_size", 48), ("bin_size", 128), ("bin_size", -16),
+                       ("accumulate_grads", 2), ("accumulate_grads", -1)):
         bad = N.fgs4d_default_options()
         setattr(bad, field, val)
         assert lib.fgs4d_state_size(10, v, 2, 10, ctypes.byref(bad), ctypes.byref(size)) == 1

@@ -300,6 +300,50 @@ def test_cuda_graph_batch_of_uneven_views(mixed):
         assert torch.equal(f1.image.view_as(imgs[i]), imgs[i]) and torch.equal(f1.final_T.view_as(Ts[i]), Ts[i])
 
 
+@pytest.mark.parametrize("groups,mixed", [(2, True), (3, False)])
+def test_split_frame_equals_one_batch(groups, mixed):
+    """SplitFrame: the views as contiguous groups on their own streams, the
+    projection adjoints chained into one set of gradients (the first group
+    overwrites, the others accumulate).  Images, T and n_last equal those of
+    one Frame over all views bit for bit; gradients equal its gradients up to
+    the order of FP32 sums; an eager step and a replay of the captured step
+    agree likewise."""
+    from paper_2310_10642_gb300 import render as R
+    c = I.config(2, n=20000, scale=0.1)
+    G, views = c["gaussians"], c["views"][:12]
+    opts = dict(c["options"], tile_size=32, bin_size=64, record_fp16=int(mixed))
+    p = R.params_to_device(G, shs_dtype=torch.bfloat16 if mixed else torch.float32)
+    n = G["logit"].shape[0]
+    fr = R.Frame(n, views, opts)
+    fr.forward(p)
+    dL = torch.randn(3 * fr.total_pixels, device="cuda", generator=torch.Generator(device="cuda").manual_seed(9))
+    ref = {k: v.clone() for k, v in fr.backward(p, dL).items()}
+    sf = R.SplitFrame(n, views, opts, groups=groups)
+    assert sf.groups == groups and sf.total_pixels == fr.total_pixels
+    sf.forward(p, check=True)
+    grads = {k: torch.full(p[k].shape, float("nan"), device="cuda") for k in R.PARAM_KEYS}
+    sf.step(p, dL, grads)
+    torch.cuda.synchronize()
+    assert torch.equal(sf.image, fr.image) and torch.equal(sf.final_T, fr.final_T)
+    assert torch.equal(sf.n_last, fr.n_last)
+
+    def close(got, want, what):  # FP32 sums in another order: 1e-4, a tenth of the oracle bar
+        for k in R.PARAM_KEYS:
+            assert_elementwise(got[k].double().cpu().numpy(), want[k].double().cpu().numpy(), 1e-4,
+                               f"{what} {k}", floor=1e-4 * grad_floor(want[k].double().cpu().numpy(), 1.0))
+    close(grads, ref, f"split x{groups}")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sf.step(p, dL, grads)
+    for k in grads:
+        grads[k].fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(sf.image, fr.image)
+    close(grads, ref, f"split x{groups} graph")
+    assert all(c_.status == 0 for c_ in sf.counters())
+
+
 @pytest.mark.parametrize("tile,mixed", [(16, False), (32, False), (32, True)])
 def test_render_stats_count_the_walk(tile, mixed):
     """fgs4d_render_stats: same image as fgs4d_render; its blended-pair count

@@ -88,3 +88,20 @@ def test_workload_view_sets():
     assert sizes == [(1352, 1014)] * 4 + [(800, 800)] * 4
     c2 = I.config(2, n=100)
     assert len(c2["views"]) == 100
+
+
+def test_split_views_balances_contiguous_groups():
+    """The view groups of SplitFrame: contiguous, non-empty, balanced by pixel
+    count, and never more groups than views."""
+    from paper_2310_10642_gb300 import render as R
+    same = [I.view((0, 0, 4), 100, 80, 0.5)] * 20
+    assert R.split_views(same, 2) == [10]
+    assert R.split_views(same, 4) == [5, 10, 15]
+    assert R.split_views(same[:1], 2) == [] and R.split_views(same[:3], 5) == [1, 2]
+    uneven = [I.view((0, 0, 4), 100, 100, 0.5), I.view((0, 0, 4), 10, 10, 0.5), I.view((0, 0, 4), 100, 100, 0.5)]
+    assert R.split_views(uneven, 2) == [2]
+    c = I.config(2, n=10, scale=0.1)
+    cuts = R.split_views(c["views"], 2)
+    pix = [v["width"] * v["height"] for v in c["views"]]
+    a = sum(pix[:cuts[0]])
+    assert abs(a - (sum(pix) - a)) <= max(pix)
