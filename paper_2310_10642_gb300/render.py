@@ -335,6 +335,7 @@ class SplitFrame:
             self.pix_offsets.append(off)
             off += int(v["width"]) * int(v["height"])
         self.total_pixels = off
+        self.c_views = N.make_views(self.views)
         self.image = torch.empty(3 * off, device=self.device, dtype=torch.float32)
         self.final_T = torch.empty(off, device=self.device, dtype=torch.float32)
         self.n_last = torch.empty(off, device=self.device, dtype=torch.int32)

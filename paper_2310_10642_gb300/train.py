@@ -26,9 +26,11 @@ DEFAULT_LRS = dict(mu=1.6e-4, log_s=5e-3, ql=1e-3, qr=1e-3, logit=5e-2, shs=2.5e
 class TrainStep:
     def __init__(self, params: dict, views: list, targets: torch.Tensor, options: dict | None = None,
                  mixed: bool = True, lrs: dict | None = None, lam: float = 0.2, betas=(0.9, 0.999), eps=1e-15,
-                 pair_capacity: int | None = None):
+                 pair_capacity: int | None = None, groups: int = 1):
         """params: FP32 device parameters (R.params_to_device); targets: packed
-        [3 * total pixels] float32 like the rendered image."""
+        [3 * total pixels] float32 like the rendered image.  groups > 1
+        renders the views as that many groups on their own streams
+        (R.SplitFrame): forward and adjoint of one group overlap another's."""
         self.master = params
         self.mixed = bool(mixed)
         self.lam = float(lam)
@@ -42,11 +44,15 @@ class TrainStep:
             self.render_params["shs"] = self.shs_bf16
         opts = dict(options or {}, record_fp16=int(self.mixed))
         n = int(params["logit"].shape[0])
-        self.frame = R.Frame(n, views, opts, pair_capacity=pair_capacity, device=dev)
+        if int(groups) > 1:
+            self.frame = R.SplitFrame(n, views, opts, groups=int(groups), pair_capacity=pair_capacity, device=dev)
+        else:
+            self.frame = R.Frame(n, views, opts, pair_capacity=pair_capacity, device=dev)
         self.frame.forward(self.render_params, check=True)
-        c = self.frame.last_counters
-        if c.n_pairs * 1.2 > self.frame.pair_capacity:  # headroom for the parameters to move
-            self.frame._alloc(int(c.n_pairs * 1.3) + 4096)
+        for fr in getattr(self.frame, "frames", [self.frame]):
+            c = fr.last_counters
+            if c.n_pairs * 1.2 > fr.pair_capacity:  # headroom for the parameters to move
+                fr._alloc(int(c.n_pairs * 1.3) + 4096)
         self.targets = targets.contiguous()
         if self.targets.numel() != 3 * self.frame.total_pixels:
             raise ValueError("targets must have the packed image layout")
@@ -75,9 +81,7 @@ class TrainStep:
         """Enqueues one full training step on the current stream."""
         fr = self.frame
         s = R._stream(stream)
-        fr.slice_project(self.render_params, stream)
-        fr.bin_sort(stream)
-        fr.render(stream)
+        fr.forward(self.render_params, stream, check=False)
         N.fgs4d_loss_l1_dssim(fr.c_views, fr.nv, fr.image.data_ptr(), self.targets.data_ptr(), self.lam,
                               self.loss.data_ptr(), self.dL.data_ptr(), self.scratch.data_ptr(), self.scratch_bytes,
                               s)

@@ -128,6 +128,20 @@ def test_training_step_as_one_cuda_graph(mixed):
         losses.append(float(ts.loss.item()))
     assert int(ts.step_count.item()) == 6
     assert ts.frame.counters().status == 0
+    # the same steps with the views in two groups on two streams: same images, so the same
+    # losses up to the order of FP32 sums in the gradients
+    p, tg = fresh()
+    ts2 = TrainStep(p, views, tg, dict(tile_size=32), mixed=mixed, eps=1e-8, groups=2)
+    assert ts2.frame.groups == 2
+    ts2.capture()
+    losses2 = []
+    for k in range(6):
+        ts2.replay()
+        torch.cuda.synchronize()
+        losses2.append(float(ts2.loss.item()))
+    assert losses2[0] == losses[0]
+    assert np.allclose(losses2, losses, rtol=1e-5, atol=0.0), (losses2, losses)
+    assert all(c_.status == 0 for c_ in ts2.frame.counters())
     assert losses[0] == loss_eager
     assert losses[-1] < losses[0]
     if mixed:
