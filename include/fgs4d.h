@@ -152,10 +152,11 @@ typedef struct {
                          results do not depend on it.  "Tile" in the counters, the state
                          layout and fgs4d_bin_sort means a binning tile. */
     int accumulate_grads; /* 0: the backward calls overwrite grads; 1: they add to grads'
-                         current contents (nothing is zeroed), so that the adjoints of
-                         several view batches of one parameter set sum into one set of
-                         gradients, one call after another on the same stream (calls that
-                         overlap on the GPU race on the outputs) */
+                         current contents with atomic adds (nothing is zeroed), so that
+                         the adjoints of several view batches of one parameter set, each
+                         with its own state, sum into one set of gradients, also when
+                         they run concurrently on different streams (the order of the
+                         FP32 sums then varies from run to run) */
 } fgs4d_options;
 
 /* Gradients w.r.t. the raw parameters, same layouts as fgs4d_gaussians but

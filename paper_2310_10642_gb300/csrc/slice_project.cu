@@ -617,8 +617,14 @@ __global__ void __launch_bounds__(256) covariance_chain_kernel(const DevGauss G,
     if (!cl.ok) return;
     float gls[4], gql[4], gqr[4], glogit;
     covariance_chain<kMode>(G, cl, GS, galpha, gls, gql, gqr, glogit);
-    // one thread per Gaussian: plain stores, or read-add-write when accumulating
-    auto put = [accumulate](float* p, float v) { *p = accumulate ? *p + v : v; };
+    // one thread per Gaussian: plain stores, or atomic adds when accumulating (calls on
+    // other states may add into the same outputs concurrently)
+    auto put = [accumulate](float* p, float v) {
+        if (accumulate)
+            atomicAdd(p, v);
+        else
+            *p = v;
+    };
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         put(&out.log_scale[i * n + g], gls[i]);
@@ -671,7 +677,10 @@ __global__ void __launch_bounds__(256, 4) sh_backward_kernel(int n, int n_views,
 #pragma unroll
         for (int j = 0; j < NB; j++) {
             float* dst = gshs + (size_t)((f * NB + j) * 3 + ch) * n + g;
-            *dst = accumulate ? *dst + acc[f][j] : acc[f][j];
+            if (!accumulate)
+                *dst = acc[f][j];
+            else if (acc[f][j] != 0.0f)
+                atomicAdd(dst, acc[f][j]);
         }
 }
 

@@ -310,12 +310,14 @@ class SplitFrame:
     own on a stream of its own: the groups run the whole step concurrently
     (one group's latency-bound stages -- slice/project, binning, projection
     adjoint -- overlap another's compositing kernels), rendering into one
-    packed image.  The groups' projection adjoints run one after the other
-    and add into one set of gradients (option accumulate_grads).  Views are
+    packed image.  The step zeroes the gradients once and every group's
+    adjoint adds into them (option accumulate_grads).  Views are
     independent, so images, T and n_last are those of one Frame over all the
     views (n_last counts positions in each group's own lists); gradients
     differ only in the order of FP32 sums.  The streams fork from and join
     the caller's stream, so a step can be captured in a CUDA graph."""
+    # (the groups' adjoints add into one set of gradients with accumulate_grads; their
+    # per-Gaussian outputs take atomic adds, so the groups run without ordering)
 
     def __init__(self, n: int, views: list, options: dict | None = None, groups: int = 2,
                  pair_capacity: int | None = None, device="cuda", cuts: list | None = None):
@@ -343,13 +345,12 @@ class SplitFrame:
         for gi, (a, b) in enumerate(self.parts):
             p0 = self.pix_offsets[a]
             p1 = self.pix_offsets[b] if b < self.nv else off
-            opts = dict(options or {}, accumulate_grads=int(gi > 0))
+            opts = dict(options or {}, accumulate_grads=1)
             outs = (self.image[3 * p0: 3 * p1], self.final_T[p0:p1], self.n_last[p0:p1])
             cap = None if pair_capacity is None else max(1 << 16, int(pair_capacity * (p1 - p0) / max(off, 1)))
             self.frames.append(Frame(n, self.views[a:b], opts, cap, device, outputs=outs))
             self.ranges.append((p0, p1))
         self.streams = [torch.cuda.Stream(device=self.device) for _ in self.frames]
-        self._pb_done = [torch.cuda.Event() for _ in self.frames]
 
     @property
     def groups(self) -> int:
@@ -377,38 +378,38 @@ class SplitFrame:
         return self.image
 
     def step(self, params: dict, dL_dimage: torch.Tensor, grads: dict, stream=None):
-        """One whole step: each group's forward and compositing adjoint on its
-        own stream, the projection adjoints chained group after group into
-        grads (the first overwrites, the others add)."""
+        """One whole step: grads are zeroed, then every group runs its forward
+        and both adjoint steps on its own stream, adding into grads
+        (accumulate_grads: atomic adds, so the groups need no ordering)."""
         cur = stream if stream is not None else torch.cuda.current_stream()
         dL = dL_dimage.contiguous()
+        with torch.cuda.stream(cur):
+            for k in PARAM_KEYS:
+                grads[k].zero_()
         for gi, (fr, s) in enumerate(zip(self.frames, self.streams)):
             s.wait_stream(cur)
             fr.slice_project(params, s)
             fr.bin_sort(s)
             fr.render(s)
             fr.backward_2d(self._dL(dL, gi), s)
-            if gi > 0:
-                s.wait_event(self._pb_done[gi - 1])
             fr.project_backward(params, grads, s)
-            self._pb_done[gi].record(s)
         for s in self.streams:
             cur.wait_stream(s)
 
     def backward(self, params: dict, dL_dimage: torch.Tensor, grads: dict | None = None, stream=None) -> dict:
-        """The adjoint of the last forward: compositing adjoints concurrently,
-        projection adjoints chained into grads."""
+        """The adjoint of the last forward: grads are zeroed, then every
+        group's adjoint adds into them on its own stream."""
         if grads is None:
             grads = {k: torch.empty(params[k].shape, device=self.device, dtype=torch.float32) for k in PARAM_KEYS}
         cur = stream if stream is not None else torch.cuda.current_stream()
         dL = dL_dimage.contiguous()
+        with torch.cuda.stream(cur):
+            for k in PARAM_KEYS:
+                grads[k].zero_()
         for gi, (fr, s) in enumerate(zip(self.frames, self.streams)):
             s.wait_stream(cur)
             fr.backward_2d(self._dL(dL, gi), s)
-            if gi > 0:
-                s.wait_event(self._pb_done[gi - 1])
             fr.project_backward(params, grads, s)
-            self._pb_done[gi].record(s)
         for s in self.streams:
             cur.wait_stream(s)
         return grads
