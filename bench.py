@@ -749,13 +749,45 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ks = max(3, min(args.steps, 10))
+        clocks_e2e = ClockSampler(torch.cuda.current_device())
+        clocks_e2e.start()
+        time.sleep(0.3)
         e0.record(stream)
         pipe.run([(host_p, host_dL)] * ks, [(host_img, host_g)] * ks)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk_e2e = clocks_e2e.stop()
         ms_e2e = e0.elapsed_time(e1) / ks
+
+        # the copies alone on this machine (same buffers, the pipeline's copy streams): in, out, both at once
+        def copies(kind):
+            s_in, s_out = pipe.s_in, pipe.s_out
+            sl = pipe.slots[0]
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            s_in.wait_stream(stream)
+            s_out.wait_stream(stream)
+            for _ in range(3):
+                if kind in ("in", "both"):
+                    with torch.cuda.stream(s_in):
+                        for k_ in R.PARAM_KEYS:
+                            sl["p"][k_].copy_(host_p[k_], non_blocking=True)
+                        sl["dL"].copy_(host_dL, non_blocking=True)
+                if kind in ("out", "both"):
+                    with torch.cuda.stream(s_out):
+                        host_img.copy_(sl["img"], non_blocking=True)
+                        for k_ in R.PARAM_KEYS:
+                            host_g[k_].copy_(sl["g"][k_], non_blocking=True)
+            stream.wait_stream(s_in)
+            stream.wait_stream(s_out)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            return round(c0.elapsed_time(c1) / 3, 3)
+
+        copy_ms = {k_: copies(k_) for k_ in ("in", "out", "both")}
         e2e = dict(value=npix * world / (ms_e2e * 1e-3) / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h), ms_per_step=ms_e2e,
+                   d2h_bytes_per_step=int(d2h), ms_per_step=ms_e2e, copies_alone_ms=copy_ms, clocks=clk_e2e,
                    pipeline="inputs of step k+1 in and outputs of step k-1 out on copy streams while step k "
                             "computes (each buffer set's step replayed as a CUDA graph)")
 

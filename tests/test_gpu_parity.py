@@ -1095,12 +1095,13 @@ def test_config1_crops_and_gradients():
     assert_grad_parity(gg, go)
 
 
-@pytest.mark.parametrize("graphs", [False, True])
-def test_host_pipeline_equals_plain_steps(graphs):
+@pytest.mark.parametrize("graphs,split", [(False, False), (True, False), (True, True)])
+def test_host_pipeline_equals_plain_steps(graphs, split):
     """HostPipeline (copies of neighbouring steps overlapped with compute)
     returns, for each step's host inputs, what a plain forward + backward of
     those inputs returns, eagerly or replaying each slot's captured graph
-    (five steps: both slots replay)."""
+    (five steps: both slots replay); also with the step as two view groups
+    on two streams (SplitFrame), as the benchmark runs it."""
     from paper_2310_10642_gb300 import render as R
     from paper_2310_10642_gb300.pipeline import HostPipeline
     G, views = ragged_scene(n=1500, seed=61)
@@ -1120,7 +1121,12 @@ def test_host_pipeline_equals_plain_steps(graphs):
         fr.forward(dp, check=False)
         g = fr.backward(dp, hd.cuda())
         want.append((fr.image.cpu(), {key: v.cpu() for key, v in g.items()}))
-    pipe = HostPipeline(fr, p, graphs=graphs)
+    run_frame = fr
+    if split:
+        run_frame = R.SplitFrame(G["logit"].shape[0], views, dict(tile_size=32), groups=2)
+        run_frame.forward(p, check=True)
+        assert run_frame.groups == 2
+    pipe = HostPipeline(run_frame, p, graphs=graphs)
     pipe.run(inputs, outputs)
     torch.cuda.synchronize()
     assert all((sl["graph"] is not None) == graphs for sl in pipe.slots)
