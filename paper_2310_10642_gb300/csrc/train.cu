@@ -20,7 +20,7 @@
 // halo, then s and its three partials, stored per pixel, and the tile's loss
 // sum); ssim_grad_kernel (window sums of the three partials, combined with x,
 // y and the L1 sign); loss_reduce_kernel (the per-tile sums, in FP64, in a
-// fixed order).
+// fixed order; a tile's sum is FP32 within each warp, FP64 across warps).
 #include <math.h>
 
 #include "fgs4d_internal.cuh"
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) ssim_moments_kernel(const __grid_constant
     __syncthreads();
     const int c = threadIdx.x & (kT - 1), r = threadIdx.x / kT;  // one output pixel per thread
     const int gx = x0 + c, gy = y0 + r;
-    double contrib = 0.0;
+    float contrib = 0.0f;
     if (gx < V.width && gy < V.height) {
         float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
@@ -140,12 +140,13 @@ __global__ void __launch_bounds__(256) ssim_moments_kernel(const __grid_constant
         P[npix + p] = s_xx;
         P[2 * npix + p] = s_xy;
         const float xv = sx[r + kR][c + kR], yv = sy[r + kR][c + kR];
-        contrib = (double)(1.0f - lambda) * fabs((double)xv - (double)yv) + (double)lambda * (1.0 - (double)s);
+        contrib = fmaf(1.0f - lambda, fabsf(xv - yv), lambda * (1.0f - s));
     }
-    // fixed-order block sum in FP64
+    // fixed-order sums: FP32 over a warp's 32 pixels (FP64 runs at a small fraction of the
+    // FP32 rate), then FP64 over the block's warps and, in loss_reduce_kernel, the tiles
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = contrib;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)contrib;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -256,14 +257,43 @@ __global__ void __launch_bounds__(256) adam_update_kernel(const __grid_constant_
     const AdamGroup& G = AG.grp[blockIdx.y];
     const float lr = lrs[G.lr_index];
     const float ib1 = 1.0f / bias[0], ib2 = 1.0f / bias[1];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G.count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = G.g[i];
-        const float m = fmaf(b1, G.m[i], (1.0f - b1) * g);
-        const float v = fmaf(b2, G.v[i], (1.0f - b2) * g * g);
+    auto update = [&](float g, float& m, float& v, float& p) {
+        m = fmaf(b1, m, (1.0f - b1) * g);
+        v = fmaf(b2, v, (1.0f - b2) * g * g);
+        p = p - lr * (m * ib1) / (sqrtf(v * ib2) + eps);
+    };
+    // four elements per thread in 16-byte accesses when every array allows it (HBM-bound: four
+    // float streams in, three out, plus the BF16 copy), then the remainder one by one
+    const bool vec = ((reinterpret_cast<uintptr_t>(G.p) | reinterpret_cast<uintptr_t>(G.m) |
+                       reinterpret_cast<uintptr_t>(G.v) | reinterpret_cast<uintptr_t>(G.g)) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(G.p_bf16) & 7u) == 0;
+    const int64_t n4 = vec ? G.count / 4 : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const float4 g = reinterpret_cast<const float4*>(G.g)[q];
+        float4 m = reinterpret_cast<const float4*>(G.m)[q];
+        float4 v = reinterpret_cast<const float4*>(G.v)[q];
+        float4 p = reinterpret_cast<const float4*>(G.p)[q];
+        update(g.x, m.x, v.x, p.x);
+        update(g.y, m.y, v.y, p.y);
+        update(g.z, m.z, v.z, p.z);
+        update(g.w, m.w, v.w, p.w);
+        reinterpret_cast<float4*>(G.m)[q] = m;
+        reinterpret_cast<float4*>(G.v)[q] = v;
+        reinterpret_cast<float4*>(G.p)[q] = p;
+        if (G.p_bf16) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(p.x, p.y), hi = __floats2bfloat162_rn(p.z, p.w);
+            uint2 packed;
+            packed.x = *reinterpret_cast<uint32_t*>(&lo);
+            packed.y = *reinterpret_cast<uint32_t*>(&hi);
+            reinterpret_cast<uint2*>(G.p_bf16)[q] = packed;
+        }
+    }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G.count; i += stride) {
+        float m = G.m[i], v = G.v[i], p = G.p[i];
+        update(G.g[i], m, v, p);
         G.m[i] = m;
         G.v[i] = v;
-        const float p = G.p[i] - lr * (m * ib1) / (sqrtf(v * ib2) + eps);
         G.p[i] = p;
         if (G.p_bf16) G.p_bf16[i] = __float2bfloat16_rn(p);
     }
@@ -364,7 +394,8 @@ fgs4d_status fgs4d_adam_step(const fgs4d_adam_group* groups, int n_groups, const
     adam_tick_kernel<<<1, 1, 0, st>>>(step, beta1, beta2, bias_scratch);
     count_launches(1);
     if (most > 0) {
-        int64_t blocks = (most + 255) / 256;
+        int64_t blocks = (most / 4 + 255) / 256;
+        if (blocks < 1) blocks = 1;
         if (blocks > 152 * 16) blocks = 152 * 16;
         adam_update_kernel<<<dim3((unsigned)blocks, (unsigned)n_groups), 256, 0, st>>>(AG, lrs, beta1, beta2, eps,
                                                                                       bias_scratch);

@@ -64,24 +64,34 @@ def test_loss_and_image_gradient_match_oracle(lam):
 
 
 def test_adam_matches_oracle_over_three_steps():
+    """Groups of 1000 and 777 elements take the 16-byte path (777: and its
+    one-element tail, with the BF16 copy), 33 elements mostly the tail, and a
+    group starting one element into its arrays (not 16-byte aligned) the
+    element-by-element path."""
     from paper_2310_10642_gb300 import native as N
     r = np.random.default_rng(9)
-    sizes = [1000, 777, 33]
-    lrs_h = [1e-2, 3e-3, 1e-1]
-    p = [torch.tensor(r.normal(size=s), dtype=torch.float32, device="cuda") for s in sizes]
-    m = [torch.zeros_like(x) for x in p]
-    v = [torch.zeros_like(x) for x in p]
-    gs = [torch.zeros_like(x) for x in p]
+    sizes = [1000, 777, 33, 101]
+    lrs_h = [1e-2, 3e-3, 1e-1, 5e-3]
+    ng = len(sizes)
+    p = [torch.tensor(r.normal(size=s + 1), dtype=torch.float32, device="cuda")[1:] if i == 3 else
+         torch.tensor(r.normal(size=s), dtype=torch.float32, device="cuda") for i, s in enumerate(sizes)]
+    m = [torch.zeros(s + 1, device="cuda")[1:] if i == 3 else torch.zeros_like(x)
+         for i, (x, s) in enumerate(zip(p, sizes))]
+    v = [torch.zeros(s + 1, device="cuda")[1:] if i == 3 else torch.zeros_like(x)
+         for i, (x, s) in enumerate(zip(p, sizes))]
+    gs = [torch.zeros(s + 1, device="cuda")[1:] if i == 3 else torch.zeros_like(x)
+          for i, (x, s) in enumerate(zip(p, sizes))]
+    assert p[3].data_ptr() % 16 != 0
     bf = torch.empty(sizes[1], dtype=torch.bfloat16, device="cuda")
     lrs = torch.tensor(lrs_h, device="cuda")
     step = torch.zeros(1, dtype=torch.int64, device="cuda")
     bias = torch.zeros(2, device="cuda")
     groups = [N.AdamGroup(p[i].data_ptr(), m[i].data_ptr(), v[i].data_ptr(), gs[i].data_ptr(),
-                          bf.data_ptr() if i == 1 else None, sizes[i], i) for i in range(3)]
+                          bf.data_ptr() if i == 1 else None, sizes[i], i) for i in range(ng)]
     ref = [(x.double().cpu().numpy(), np.zeros(s), np.zeros(s)) for x, s in zip(p, sizes)]
     for t in range(1, 4):
         gh = [r.normal(size=s).astype(np.float32) for s in sizes]
-        for i in range(3):
+        for i in range(ng):
             gs[i].copy_(torch.as_tensor(gh[i]))
         N.fgs4d_adam_step(groups, lrs.data_ptr(), 0.9, 0.999, 1e-8, step.data_ptr(), bias.data_ptr(),
                           torch.cuda.current_stream().cuda_stream)
@@ -89,7 +99,7 @@ def test_adam_matches_oracle_over_three_steps():
                for i, (rp, rm, rv) in enumerate(ref)]
     torch.cuda.synchronize()
     assert int(step.item()) == 3
-    for i in range(3):
+    for i in range(ng):
         assert np.abs(p[i].double().cpu().numpy() - ref[i][0]).max() < 1e-5
         assert np.abs(m[i].double().cpu().numpy() - ref[i][1]).max() < 1e-6
         assert np.abs(v[i].double().cpu().numpy() - ref[i][2]).max() < 1e-6
