@@ -15,7 +15,7 @@
 // where S_mu = ds/dmu_x, S_xx = ds/de_xx, S_xy = ds/de_xy at every pixel q
 // (moments held fixed), so the gradient is three more window sums.
 //
-// Kernels: ssim_moments_kernel (one CTA per 16x16 output tile and channel:
+// Kernels: ssim_moments_kernel (one CTA per 32x32 output tile and channel:
 // window sums of x, y, x^2, y^2, xy from a shared-memory tile with a 5-pixel
 // halo, then s and its three partials, stored per pixel, and the tile's loss
 // sum); ssim_grad_kernel (window sums of the three partials, combined with x,
@@ -29,7 +29,8 @@ namespace fgs4d {
 
 namespace {
 
-constexpr int kT = 16;              // output tile side
+constexpr int kT = 32;              // output tile side (256 threads, four output pixels each)
+constexpr int kPPT = kT * kT / 256; // output pixels per thread
 constexpr int kR = 5;               // window radius (11 taps)
 constexpr int kE = kT + 2 * kR;     // tile side with halo
 constexpr float kC1 = 0.01f * 0.01f;
@@ -71,7 +72,7 @@ __device__ __forceinline__ void load_halo(float (*sh)[kE + 1], const float* __re
 
 }  // namespace
 
-// One CTA (256 threads) per 16x16 tile of one channel of one view.
+// One CTA (256 threads) per 32x32 tile of one channel of one view.
 __global__ void __launch_bounds__(256) ssim_moments_kernel(const __grid_constant__ LossViews LV,
                                                            const float* __restrict__ image,
                                                            const float* __restrict__ target, float lambda,
@@ -112,37 +113,41 @@ __global__ void __launch_bounds__(256) ssim_moments_kernel(const __grid_constant
         hxy[r][c] = ab;
     }
     __syncthreads();
-    const int c = threadIdx.x & (kT - 1), r = threadIdx.x / kT;  // one output pixel per thread
-    const int gx = x0 + c, gy = y0 + r;
     float contrib = 0.0f;
-    if (gx < V.width && gy < V.height) {
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
-        for (int k = 0; k <= 2 * kR; k++) {
-            const float wk = LV.win[k];
-            mx = fmaf(wk, hx[r + k][c], mx);
-            my = fmaf(wk, hy[r + k][c], my);
-            exx = fmaf(wk, hxx[r + k][c], exx);
-            eyy = fmaf(wk, hyy[r + k][c], eyy);
-            exy = fmaf(wk, hxy[r + k][c], exy);
+    for (int j = 0; j < kPPT; j++) {  // output pixels threadIdx.x + 256 j
+        const int o = threadIdx.x + 256 * j;
+        const int c = o & (kT - 1), r = o / kT;
+        const int gx = x0 + c, gy = y0 + r;
+        if (gx < V.width && gy < V.height) {
+            float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * kR; k++) {
+                const float wk = LV.win[k];
+                mx = fmaf(wk, hx[r + k][c], mx);
+                my = fmaf(wk, hy[r + k][c], my);
+                exx = fmaf(wk, hxx[r + k][c], exx);
+                eyy = fmaf(wk, hyy[r + k][c], eyy);
+                exy = fmaf(wk, hxy[r + k][c], exy);
+            }
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * (exy - mx * my) + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = (exx - mx * mx) + (eyy - my * my) + kC2;
+            const float D = B1 * B2;
+            const float s = A1 * A2 / D;
+            // partials of s at fixed (e_xx, e_xy) and the other image's moments
+            const float s_mu = (2.f * my * (A2 - A1) - 2.f * mx * s * (B2 - B1)) / D;
+            const float s_xx = -s / B2;
+            const float s_xy = 2.f * A1 / D;
+            const size_t p = (size_t)gy * V.width + gx;
+            float* P = partials + 3 * plane;  // three planes per channel plane
+            P[p] = s_mu;
+            P[npix + p] = s_xx;
+            P[2 * npix + p] = s_xy;
+            const float xv = sx[r + kR][c + kR], yv = sy[r + kR][c + kR];
+            contrib += fmaf(1.0f - lambda, fabsf(xv - yv), lambda * (1.0f - s));
         }
-        const float A1 = 2.f * mx * my + kC1, A2 = 2.f * (exy - mx * my) + kC2;
-        const float B1 = mx * mx + my * my + kC1, B2 = (exx - mx * mx) + (eyy - my * my) + kC2;
-        const float D = B1 * B2;
-        const float s = A1 * A2 / D;
-        // partials of s at fixed (e_xx, e_xy) and the other image's moments
-        const float s_mu = (2.f * my * (A2 - A1) - 2.f * mx * s * (B2 - B1)) / D;
-        const float s_xx = -s / B2;
-        const float s_xy = 2.f * A1 / D;
-        const size_t p = (size_t)gy * V.width + gx;
-        float* P = partials + 3 * plane;  // three planes per channel plane
-        P[p] = s_mu;
-        P[npix + p] = s_xx;
-        P[2 * npix + p] = s_xy;
-        const float xv = sx[r + kR][c + kR], yv = sy[r + kR][c + kR];
-        contrib = fmaf(1.0f - lambda, fabsf(xv - yv), lambda * (1.0f - s));
     }
-    // fixed-order sums: FP32 over a warp's 32 pixels (FP64 runs at a small fraction of the
+    // fixed-order sums: FP32 over a warp's 128 pixels (FP64 runs at a small fraction of the
     // FP32 rate), then FP64 over the block's warps and, in loss_reduce_kernel, the tiles
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
@@ -190,22 +195,26 @@ __global__ void __launch_bounds__(256) ssim_grad_kernel(const __grid_constant__ 
         hm[2][r][c] = a2;
     }
     __syncthreads();
-    const int c = threadIdx.x & (kT - 1), r = threadIdx.x / kT;
-    const int gx = x0 + c, gy = y0 + r;
-    if (gx >= V.width || gy >= V.height) return;
-    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
 #pragma unroll
-    for (int k = 0; k <= 2 * kR; k++) {
-        const float wk = LV.win[k];
-        w0 = fmaf(wk, hm[0][r + k][c], w0);
-        w1 = fmaf(wk, hm[1][r + k][c], w1);
-        w2 = fmaf(wk, hm[2][r + k][c], w2);
+    for (int j = 0; j < kPPT; j++) {  // output pixels threadIdx.x + 256 j
+        const int o = threadIdx.x + 256 * j;
+        const int c = o & (kT - 1), r = o / kT;
+        const int gx = x0 + c, gy = y0 + r;
+        if (gx >= V.width || gy >= V.height) continue;
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 2 * kR; k++) {
+            const float wk = LV.win[k];
+            w0 = fmaf(wk, hm[0][r + k][c], w0);
+            w1 = fmaf(wk, hm[1][r + k][c], w1);
+            w2 = fmaf(wk, hm[2][r + k][c], w2);
+        }
+        const size_t p = (size_t)gy * V.width + gx;
+        const float xv = image[plane + p], yv = target[plane + p];
+        const float dssim = w0 + 2.f * xv * w1 + yv * w2;
+        const float sgn = (xv > yv) ? 1.f : ((xv < yv) ? -1.f : 0.f);
+        dL_dimage[plane + p] = inv_count * ((1.0f - lambda) * sgn - lambda * dssim);
     }
-    const size_t p = (size_t)gy * V.width + gx;
-    const float xv = image[plane + p], yv = target[plane + p];
-    const float dssim = w0 + 2.f * xv * w1 + yv * w2;
-    const float sgn = (xv > yv) ? 1.f : ((xv < yv) ? -1.f : 0.f);
-    dL_dimage[plane + p] = inv_count * ((1.0f - lambda) * sgn - lambda * dssim);
 }
 
 // Sums the per-tile losses in a fixed order (one CTA) and writes the mean.
