@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-aux", action="store_true", help="skip the depth/flow-map key of the default run")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the No-4DRot / static-3DGS stage times of the default run")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the uneven-batch key (300k Gaussians, 100 views, batched vs one by one)")
     ap.add_argument("--workload", default="render", choices=["render", "train"],
                     help="render: forward+backward of the 1M-Gaussian batch (the headline); train: the full "
                          "training step (loss, adjoint, Adam) on 3M Gaussians x 8 views")
@@ -837,6 +839,60 @@ def main():
                     "static_3dgs: no time axis, SH degree 3 colour without Fourier orders",
         }
 
+    # ---- batching on the workload shaped for it (config 2: 300k Gaussians, 80 views at 1352x1014 from
+    # 20 arc cameras x 4 times plus 20 views at 676x507): the whole batch as one graph step (two view
+    # groups) against the same views one call each (eager), both mixed precision, forward + backward
+    batching = None
+    if rank == 0 and not args.no_batching:
+        from paper_2310_10642_gb300 import inputs as I2
+        c2 = I2.config(2, n=(args.n // 3 if args.n else None), scale=args.scale)
+        G2, views2 = c2["gaussians"], c2["views"]
+        n2 = G2["logit"].shape[0]
+        p2 = R.params_to_device(G2, shs_dtype=torch.bfloat16 if mixed else torch.float32)
+        o2 = dict(c2["options"], record_fp16=int(mixed), **{k: opts[k] for k in ("tile_size", "bin_size",
+                                                                                 "batch_depth")})
+        g2 = {k: torch.empty(p2[k].shape, device="cuda", dtype=torch.float32) for k in R.PARAM_KEYS}
+        sf2 = R.SplitFrame(n2, views2, o2, groups=max(1, args.groups))
+        sf2.forward(p2, check=True)
+        for fr_ in sf2.frames:
+            fr_._alloc(int(fr_.last_counters.n_pairs * 1.15) + 4096)
+        sf2.forward(p2, check=True)
+        dL2 = torch.randn(3 * sf2.total_pixels, device="cuda", generator=gen) * (1.0 / sf2.total_pixels)
+        for _ in range(2):
+            sf2.step(p2, dL2, g2)
+        torch.cuda.synchronize()
+        gb = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gb):
+            sf2.step(p2, dL2, g2)
+        ms_b = time_graph(gb, 3)
+        del gb
+        ones = [R.Frame(n2, [v], o2) for v in views2]
+        for f1 in ones:
+            f1.forward(p2, check=True)
+        offs = sf2.pix_offsets + [sf2.total_pixels]
+
+        def one_by_one():
+            for i, f1 in enumerate(ones):
+                f1.step(p2, dL2[3 * offs[i]: 3 * offs[i + 1]], g2)
+
+        one_by_one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_by_one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_1 = e0.elapsed_time(e1)
+        npix2 = sf2.total_pixels
+        batching = dict(views=len(views2), sizes=sorted({f"{v['width']}x{v['height']}" for v in views2}),
+                        gaussians=n2, pixels=npix2, batched_ms=round(ms_b, 3),
+                        batched_mpix_s=round(npix2 / (ms_b * 1e-3) / 1e6, 3), one_by_one_ms=round(ms_1, 3),
+                        one_by_one_mpix_s=round(npix2 / (ms_1 * 1e-3) / 1e6, 3), speedup=round(ms_1 / ms_b, 3),
+                        what="forward + backward of all views: one CUDA graph step (views in two groups) vs one "
+                             "eager call sequence per view (its gradients overwritten per view)")
+        del sf2, ones, p2, g2
+        torch.cuda.empty_cache()
+
     # ---- depth and optical-flow maps (f2) through the same lists: eager stage times
     aux = None
     if rank == 0 and not args.no_aux:
@@ -899,7 +955,7 @@ def main():
                    single_view=single, batched_fp32=batched_fp32,
                    batched_vs_single_fp32=round(value / world / single["mpix_s"], 3) if single else None,
                    roofline=roofline, stage_roofline=stage_roof, work=work, cpu_baseline=cpu, e2e=e2e, clocks=clk,
-                   rotation_variants=variants, depth_flow_maps=aux, train_step=train,
+                   rotation_variants=variants, uneven_batch=batching, depth_flow_maps=aux, train_step=train,
                    gpu_launches=int(launches))
         print(json.dumps(out))
     if dist:
