@@ -651,6 +651,22 @@ def main():
     ms_step = total_ms / args.steps
     fwd_ms = stage_ms["slice_project"] + stage_ms["bin_sort"] + stage_ms["render"]  # per step, eager
     fwd_mpix = npix / (fwd_ms * 1e-3) / 1e6
+    # the forward alone (slice/project, binning, compositing) as a CUDA graph step, like the headline
+    fwd_graph = None
+    if graph is not None:
+        def fwd_step():
+            run_frame.forward(p, check=False)
+        for _ in range(2):
+            fwd_step()
+        torch.cuda.synchronize()
+        gf = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gf):
+            fwd_step()
+        ms_f = time_graph(gf, max(3, args.steps))
+        del gf
+        fwd_graph = dict(mpix_s=round(npix / (ms_f * 1e-3) / 1e6, 3), ms_per_step=round(ms_f, 4),
+                         what="forward only (slice/project, binning, compositing), one CUDA graph per step, "
+                              "the headline's view groups")
 
     # ---- roofline of the dominant kernel (algorithmic bytes per launch / time)
     peaks, peak_kind = measured_peaks()
@@ -951,7 +967,8 @@ def main():
                        l2="inputs larger than L2 (356 MB mixed / 644 MB FP32 parameters)",
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                                pixels_per_step=npix, visible_splats=nvis, pairs=npairs),
-                   fwd_mpix_s=round(fwd_mpix, 3), stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
+                   fwd_mpix_s=round(fwd_mpix, 3), fwd_graph=fwd_graph,
+                   stage_ms={k: round(v, 4) for k, v in stage_ms.items()},
                    single_view=single, batched_fp32=batched_fp32,
                    batched_vs_single_fp32=round(value / world / single["mpix_s"], 3) if single else None,
                    roofline=roofline, stage_roofline=stage_roof, work=work, cpu_baseline=cpu, e2e=e2e, clocks=clk,
