@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"],
                     help="mixed: BF16 4DSH coefficients + 16-bit conic records; fp32: plain FP32 storage")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly, not as a CUDA graph")
-    ap.add_argument("--groups", type=int, default=2,
-                    help="view groups of the timed step, each on a stream of its own (1: one batch on one stream)")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="view groups of the timed step, each on a stream of its own (1: one batch on one stream; "
+                         "0: the autotuner times 1 and 2)")
     ap.add_argument("--tile", default="auto", choices=["auto", "16", "32"],
                     help="compositing tile side; auto: the autotuner times both on this workload")
     ap.add_argument("--bin-size", default="auto", choices=["auto", "16", "32", "64"],
@@ -527,6 +528,9 @@ def main():
         opts, tune_table = A.tune(p, views, opts, cands=cands, cache=None)
     else:
         opts = dict(opts, **cands[0])
+    groups_table = None
+    if args.groups <= 0:  # one batch or two view groups, timed on this workload with the chosen shape
+        args.groups, groups_table = A.tune_groups(p, views, opts)
     opts_fp32 = dict(opts, record_fp16=0)
     stream = torch.cuda.current_stream()
     gen = torch.Generator(device="cuda").manual_seed(1234)
@@ -961,6 +965,7 @@ def main():
                    config=dict(WORKLOAD, n=n, views=V, tile=opts["tile_size"], bin=opts["bin_size"],
                                batch_depth=opts["batch_depth"],
                                view_groups=[list(g) for g in run_frame.parts] if args.groups > 1 else [[0, V]],
+                               view_groups_tuned=groups_table,
                                autotune=tune_table, precision=(
                        "BF16 4DSH coefficients, 16-bit Cholesky conics; FP32 arithmetic" if mixed else "FP32"),
                        cuda_graph=graph is not None,

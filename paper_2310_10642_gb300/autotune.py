@@ -1,4 +1,5 @@
-"""Picks the tile sizes and the per-tile batch depth of a frame by timing.
+"""Picks the tile sizes, the per-tile batch depth and the number of view
+groups of a frame by timing.
 
 Three launch-shape knobs change speed but not results: ``tile_size`` (16 or
 32, the side of the square compositing tiles, one thread block each),
@@ -9,6 +10,10 @@ combination is fastest depends on the splat-size distribution and the image
 sizes, so ``tune`` renders the caller's own frame (forward + backward) with
 every candidate, times it with CUDA events, and returns the fastest.  Results are cached in a JSON file keyed
 by the device and the shape of the workload, so a training loop tunes once.
+
+``tune_groups`` then times the whole step as one batch against the views as
+two (or more) groups on their own streams (``render.SplitFrame``): that
+overlap pays when every group still has enough views to keep the GPU busy.
 
 Cache file: ``$FGS4D_AUTOTUNE_CACHE`` if set, else
 ``~/.cache/fgs4d/autotune.json``; ``cache=None`` disables it.
@@ -140,3 +145,38 @@ def tune(params: dict, views: list, options: dict | None = None, cands: list | N
 
     choice, table = tune_with(timer, cands, key, cache)
     return dict(opts, **choice), table
+
+
+def tune_groups(params: dict, views: list, options: dict, groups=(1, 2), reps: int = 3, warmup: int = 2) -> tuple:
+    """Fastest number of view groups for the forward + backward step of
+    ``params`` into ``views`` with ``options`` (a launch shape from ``tune``):
+    1 is one Frame on one stream, g > 1 a SplitFrame of g groups.  Returns
+    (groups, table of [groups, ms])."""
+    import torch
+
+    from . import render as R
+
+    n = int(params["logit"].shape[0])
+    stream = torch.cuda.current_stream()
+    table = []
+    for g in groups:
+        fr = R.SplitFrame(n, views, options, groups=g) if g > 1 else R.Frame(n, views, options)
+        fr.forward(params, check=True)
+        gen = torch.Generator(device=fr.device).manual_seed(0)
+        dL = torch.randn(3 * fr.total_pixels, device=fr.device, generator=gen)
+        grads = {k: torch.empty(params[k].shape, device=fr.device, dtype=torch.float32) for k in R.PARAM_KEYS}
+        for _ in range(warmup):
+            fr.step(params, dL, grads)
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fr.step(params, dL, grads)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        table.append((dict(groups=int(g)), statistics.median(times)))
+        del fr, dL, grads
+        torch.cuda.empty_cache()
+    best = select(table)
+    return best["groups"], [dict(c, ms=round(ms, 4)) for c, ms in table]

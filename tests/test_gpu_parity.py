@@ -427,6 +427,16 @@ def test_bin_size_does_not_change_results(tile):
             assert rel < 1e-5, (b, k, rel)
 
 
+def test_autotune_groups_returns_a_timed_count():
+    from paper_2310_10642_gb300 import autotune as A
+    from paper_2310_10642_gb300 import render as R
+    G, views = ragged_scene(n=2000, seed=24)
+    p = R.params_to_device(G)
+    g, table = A.tune_groups(p, views, dict(tile_size=32), groups=(1, 2), reps=2, warmup=1)
+    assert g in (1, 2) and [t["groups"] for t in table] == [1, 2] and all(t["ms"] > 0 for t in table)
+    assert min(t["ms"] for t in table) == [t["ms"] for t in table if t["groups"] == g][0]
+
+
 def test_autotune_returns_a_timed_candidate():
     from paper_2310_10642_gb300 import autotune as A
     from paper_2310_10642_gb300 import render as R
@@ -955,8 +965,8 @@ def _block_diagonal_pairs(q3):
     return np.stack([a for a, _ in pairs], 1), np.stack([b for _, b in pairs], 1)
 
 
-@pytest.mark.parametrize("n_freq", [0, 1])
-def test_static_3dgs_special_case_against_oracle(n_freq):
+@pytest.mark.parametrize("n_freq,mixed", [(0, False), (1, False), (0, True)])
+def test_static_3dgs_special_case_against_oracle(n_freq, mixed):
     """FGS4D_ROT_STATIC (3DGS as the special case of 4DGS, Sec. 3.1): the
     GPU reads neither q_right nor mu_t nor s_t (all NaN here).  The oracle
     renders the same Gaussians as 4D ones with the block-diagonal rotation
@@ -964,9 +974,15 @@ def test_static_3dgs_special_case_against_oracle(n_freq):
     Images and the gradients of mu_xyz, log s_xyz, the opacity and the
     coefficients match element by element; the gradients of q_right, mu_t and
     log s_t are zero; dL/dq_left matches FP64 central differences of the
-    oracle through the pair."""
+    oracle through the pair.  Mixed precision (BF16 coefficients, 16-bit
+    conics) against the oracle at the rounded coefficients, at the mixed
+    tolerances.  The depth and flow maps: static splats do not move, so both
+    flow planes are 0, and the depth plane is the oracle's compositing of the
+    camera depths."""
     from paper_2310_10642_gb300 import native as N
     G, views = ragged_scene(n=800, seed=47, L=3, K=n_freq)
+    if mixed:
+        G = dict(G, shs=torch.as_tensor(G["shs"]).to(torch.bfloat16).float().numpy())
     n = G["logit"].shape[0]
     q3 = G["ql"].astype(np.float64)
     ql_o, qr_o = _block_diagonal_pairs(q3)
@@ -975,8 +991,10 @@ def test_static_3dgs_special_case_against_oracle(n_freq):
     Gs["mu"][3] = np.nan
     Gs["log_s"] = G["log_s"].copy()
     Gs["log_s"][3] = np.nan
-    fr, p, imgs, Ts = gpu_forward(Gs, views, dict(tile_size=32))
+    opts = dict(tile_size=32, record_fp16=int(mixed), aux_channels=1)
+    fr, p, imgs, Ts = gpu_forward(Gs, views, opts, shs_dtype=torch.bfloat16 if mixed else None)
     assert fr.last_counters.status == 0
+    img_tol, grad_tol = (1e-3, MIXED_GRAD_TOL) if mixed else (IMG_TOL, GRAD_TOL)
 
     def oracle_for(v, ql=ql_o, qr=qr_o):
         mu = G["mu"].astype(np.float64).copy()
@@ -985,7 +1003,15 @@ def test_static_3dgs_special_case_against_oracle(n_freq):
 
     refs = [O.render(oracle_for(v), v) for v in views]
     for img, T, ref in zip(imgs, Ts, refs):
-        assert_image_parity(img, T, ref)
+        assert_image_parity(img, T, ref, tol=img_tol)
+    aux = [a.double().cpu().numpy() for a in fr.split(fr.render_aux().clone())]
+    for v, a, ref in zip(views, aux, refs):
+        assert np.all(a[1:] == 0.0)  # no motion
+        want = O.render_values(oracle_for(v), v, O.aux_values(oracle_for(v), v, 0.0))
+        ok = ref["flags"] == 0
+        depth_range = max(float(np.abs(want[0]).max()), 1e-9)
+        err = float(np.abs(a[0] - want[0])[ok].max()) / depth_range
+        assert err <= (3e-3 if mixed else 2e-4), err
     dL = masked_dL(views, refs, 15)
     gg = grads_gpu(fr, p, dL)
     go = None
@@ -994,10 +1020,12 @@ def test_static_3dgs_special_case_against_oracle(n_freq):
         o.pop("grad2d")
         go = o if go is None else {k: go[k] + o[k] for k in go}
     for k in ("mu", "log_s"):
-        assert_elementwise(gg[k][:3], go[k][:3], GRAD_TOL, f"static {k}[xyz]")
+        assert_elementwise(gg[k][:3], go[k][:3], grad_tol, f"static {k}[xyz]")
         assert np.all(gg[k][3] == 0.0), k  # no time axis
-    assert_grad_parity(gg, go, keys=("logit", "shs"), what="static ")
+    assert_grad_parity(gg, go, grad_tol, keys=("logit", "shs"), what="static ")
     assert np.all(gg["qr"] == 0.0)
+    if mixed:
+        return  # dL/dq_left by differences: covered at FP32
 
     def loss(q):
         a, b = _block_diagonal_pairs(q)
