@@ -8,6 +8,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "fgs4d_internal.cuh"
@@ -153,22 +154,44 @@ fgs4d_status make_layout(int64_t n, const ViewSet& VS, int record_fp16, int aux,
     L->grad2d = take(s * 48);
     L->aux = aux ? take(s * 16) : 0;
     L->gsum = take((size_t)n * 11 * sizeof(float));
+    // Pair binning path: the counting sort keeps one uint32 counter per
+    // (binning tile, chunk of a view's depth-ordered visible splats) and one
+    // pair array; the radix path keys and values, double-buffered.
+    uint32_t tmax = 0;
+    for (int i = 0; i < VS.n; i++) tmax = std::max(tmax, (uint32_t)(VS.v[i].tiles_x * VS.v[i].tiles_y));
+    L->view_tiles_max = tmax;
+    L->count_sort = n > 0 && tmax <= kCountTilesMax;
+    if (L->count_sort) {
+        // chunks of 256 splats unless the counters would pass 2^26 entries
+        uint32_t C = 256;
+        while ((uint64_t)VS.total_tiles * (uint64_t)((n + C - 1) / C) > (1ull << 26) && C < (1u << 20)) C <<= 1;
+        L->chunk = C;
+        L->chunks_per_view = (uint32_t)((n + C - 1) / C);
+        if ((uint64_t)VS.total_tiles * L->chunks_per_view >= (1ull << 31)) L->count_sort = 0;  // 32-bit scan
+        else L->chunk_hist = take((size_t)VS.total_tiles * L->chunks_per_view * 4);
+    }
     L->fixed_bytes = off;
+    const int arrays = L->count_sort ? 1 : 4;  // uint32 arrays of `capacity`
     if (capacity < 0) {
         if (state_bytes < L->fixed_bytes) return FGS4D_ERR_CAPACITY;
-        // four uint32 arrays of `capacity`, each padded to the alignment
-        int64_t cap = (int64_t)((state_bytes - L->fixed_bytes) / 16);
-        while (cap > 0 && L->fixed_bytes + 4 * align_up((size_t)cap * 4) > state_bytes) cap--;
+        // each array padded to the alignment
+        int64_t cap = (int64_t)((state_bytes - L->fixed_bytes) / (4 * arrays));
+        while (cap > 0 && L->fixed_bytes + arrays * align_up((size_t)cap * 4) > state_bytes) cap--;
         capacity = cap;
     }
     if (capacity > 0xffffffffll) capacity = 0xffffffffll;
     L->capacity = capacity;
     const size_t pb = align_up((size_t)capacity * 4);
-    L->pair_keys[0] = off;
-    L->pair_keys[1] = off + pb;
-    L->pair_vals[0] = off + 2 * pb;
-    L->pair_vals[1] = off + 3 * pb;
-    L->total = off + 4 * pb;
+    if (L->count_sort) {
+        L->pair_keys[0] = L->pair_keys[1] = L->pair_vals[0] = L->pair_vals[1] = off;
+        L->total = off + pb;
+    } else {
+        L->pair_keys[0] = off;
+        L->pair_keys[1] = off + pb;
+        L->pair_vals[0] = off + 2 * pb;
+        L->pair_vals[1] = off + 3 * pb;
+        L->total = off + 4 * pb;
+    }
     return FGS4D_OK;
 }
 
@@ -327,7 +350,7 @@ fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view* views, int n_views, con
 }
 
 static int pair_buffer(const Prepared& P) {
-    if (P.L.capacity == 0) return 0;
+    if (P.L.capacity == 0 || P.L.count_sort) return 0;
     return radix_passes(pair_sort_bits(P.VS.total_tiles + 1)) & 1;
 }
 

@@ -510,6 +510,282 @@ __global__ void __launch_bounds__(256) tile_ranges_kernel(const uint32_t* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Counting-sort binning (views of at most kCountTilesMax binning tiles).
+// The visible splats are ordered by (view, depth, index); each view's run is
+// cut into chunks of `chunk` splats, one warp per chunk.  The histogram
+// kernel counts, per chunk, the pairs of each binning tile of its view; an
+// exclusive scan of the counts laid out tile-major (per view, (tile, chunk)
+// at tile * chunks + chunk after the earlier views' entries) gives every
+// (tile, chunk) the first slot of its run in the tile-major pair array.
+// Small chunks keep the part of the pair array that the warps in flight are
+// writing small enough to stay in L2 until its sectors are complete (with
+// 1024-splat chunks the scatter's stores missed L2 and re-read their sectors
+// from DRAM several times over).  The scatter kernel re-walks each
+// chunk in order and writes every splat id to its slot.  Chunks of a tile
+// follow each other in depth order and a warp keeps its chunk's order, so
+// each tile's list comes out in (depth, index) order, as with the radix path.
+// ---------------------------------------------------------------------------
+
+// Splat ids in (depth, index) order -> their view, the key of the stable
+// pass that groups the list by view.
+__global__ void __launch_bounds__(256) view_keys_kernel(const uint32_t* __restrict__ sorted, const uint32_t* counters,
+                                                        uint32_t n_max, uint32_t n_gauss,
+                                                        uint32_t* __restrict__ keys) {
+    const uint32_t n = min(counters[0], n_max);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        keys[i] = sorted[i] / n_gauss;
+}
+
+// Where chunk c of view v lies.  view_count[] holds the visible splats per
+// view, whose runs follow each other in view order in the sorted list; the
+// chunk is positions [b, e) of it (empty past the view's end).  The view's
+// (tile, chunk) counts take entries [off, off + tiles * chunks) of H, entry
+// (t, c) at off + t * chunks + c, with chunks = ceil(visible / chunk): views
+// in order, so that H is tile-major over all views.  Called by a whole warp.
+struct ChunkPlace {
+    uint32_t b, e, off, chunks;
+};
+__device__ __forceinline__ ChunkPlace chunk_place(const ViewSet& VS, const uint32_t* view_count, uint32_t v,
+                                                  uint32_t c, uint32_t chunk) {
+    const int lane = threadIdx.x & 31;
+    uint32_t before = 0, off = 0;
+    for (int i = lane; i < (int)v; i += 32) {
+        const uint32_t n = view_count[i];
+        before += n;
+        off += (uint32_t)(VS.v[i].tiles_x * VS.v[i].tiles_y) * ((n + chunk - 1) / chunk);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(kFull, before, o);
+        off += __shfl_xor_sync(kFull, off, o);
+    }
+    const uint32_t cnt = view_count[v];
+    ChunkPlace P;
+    const uint32_t lo = min(c * chunk, cnt), hi = min(lo + chunk, cnt);
+    P.b = before + lo;
+    P.e = before + hi;
+    P.off = off;
+    P.chunks = (cnt + chunk - 1) / chunk;
+    return P;
+}
+
+// Calls f(local tile index ty * tiles_x + tx, k) for the k-th binning tile
+// (k = 0, 1, ...) of view V that the splat's support ellipse reaches, in row
+// order, at most `limit` times; returns the number of calls.  The same box and ellipse rows as the
+// pair count of the radix path.
+template <class F>
+__device__ __forceinline__ uint32_t for_each_tile(const SplatView& r, const DevView& V, int bin, float ln_alpha_min,
+                                                  uint32_t limit, F&& f) {
+    int rect[4];
+    uint32_t n = 0;
+    if (box_tiles(r.u, r.v, r.hx, r.hy, V, bin, rect) > 0) {
+        const EllipseRows e = ellipse_rows(r, ln_alpha_min);
+        for (int ty = rect[1]; ty <= rect[3] && n < limit; ty++) {
+            int tx0;
+            const int nr = ellipse_row_tiles(e, V, bin, rect, ty, &tx0);
+            const uint32_t row = (uint32_t)ty * (uint32_t)V.tiles_x + (uint32_t)tx0;
+            for (int i = 0; i < nr && n < limit; i++, n++) f(row + (uint32_t)i, n);
+        }
+    }
+    return n;
+}
+
+__device__ __forceinline__ SplatView load_record(const void* rec, int rec_fp16, uint32_t sid, float ln_alpha_min) {
+    return rec_fp16 ? decode_record(reinterpret_cast<const SplatRecordH*>(rec)[sid], ln_alpha_min)
+                    : decode_record(reinterpret_cast<const SplatRecord*>(rec)[sid], ln_alpha_min);
+}
+
+// Per (view, chunk) warp: pairs per binning tile of the view, into H at
+// the chunk's entries (chunk_place); also each visible splat's exact tile
+// count, as the radix path's count kernel leaves it.  Warp 0 also stores
+// the number of entries of H in use to *n_entries.
+__global__ void __launch_bounds__(kCountWarps * 32) count_hist_kernel(
+    const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted,
+    const uint32_t* __restrict__ view_count, const void* __restrict__ rec, int rec_fp16, float ln_alpha_min, int bin,
+    uint32_t chunk, uint32_t chunks_per_view, uint32_t tiles_max, uint32_t* __restrict__ tiles,
+    uint32_t* __restrict__ H, uint32_t* __restrict__ n_entries) {
+    extern __shared__ uint32_t s_count[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t gw = blockIdx.x * kCountWarps + (uint32_t)w;
+    if (gw >= (uint32_t)VS.n * chunks_per_view) return;  // warp-uniform; the kernel has no block barrier
+    const uint32_t v = gw / chunks_per_view, c = gw - v * chunks_per_view;
+    if (gw == 0) {
+        const ChunkPlace L = chunk_place(VS, view_count, (uint32_t)VS.n - 1, 0, chunk);
+        if (lane == 0) n_entries[0] = L.off + (uint32_t)(VS.v[VS.n - 1].tiles_x * VS.v[VS.n - 1].tiles_y) * L.chunks;
+    }
+    const ChunkPlace P = chunk_place(VS, view_count, v, c, chunk);
+    if (c >= P.chunks) return;  // warp-uniform: past the view's last chunk
+    const DevView& V = VS.v[v];
+    const uint32_t nt = (uint32_t)(V.tiles_x * V.tiles_y);
+    uint32_t* cnt = s_count + (size_t)w * tiles_max;
+    for (uint32_t t = lane; t < nt; t += 32) cnt[t] = 0u;
+    __syncwarp();
+    for (uint32_t p = P.b + lane; p < P.e; p += 32) {
+        const uint32_t sid = sorted[p];
+        const SplatView r = load_record(rec, rec_fp16, sid, ln_alpha_min);
+        tiles[sid] =
+            for_each_tile(r, V, bin, ln_alpha_min, 0xffffffffu, [&](uint32_t t, uint32_t) { atomicAdd(&cnt[t], 1u); });
+    }
+    __syncwarp();
+    for (uint32_t t = lane; t < nt; t += 32) H[P.off + t * P.chunks + c] = cnt[t];
+}
+
+// Per (view, chunk) warp, after the exclusive scan of H: writes the chunk's
+// splat ids to their slots of the tile-major pair array.  Per round of 32
+// splats, each lane walks its splat's tiles into the warp's buffer and sets
+// its bit in each tile's lane mask (shared atomic OR); a splat's slot in
+// tile t is then the tile's next free slot plus the number of lower lanes
+// (earlier splats) in the mask, and the lowest lane advances the tile by the
+// mask's population and clears it.  So every tile's slots are taken in list
+// order.  A round with more pairs than the buffer holds goes through it in
+// runs of consecutive lanes; a splat with more pairs than the buffer holds
+// walks them alone.
+__global__ void __launch_bounds__(kCountWarps * 32) count_scatter_kernel(
+    const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted,
+    const uint32_t* __restrict__ view_count, const void* __restrict__ rec, int rec_fp16, float ln_alpha_min, int bin,
+    uint32_t chunk, uint32_t chunks_per_view, uint32_t tiles_max, const uint32_t* __restrict__ tiles,
+    const uint32_t* __restrict__ H, uint32_t capacity, uint32_t* counters, uint32_t* __restrict__ pair_vals) {
+    extern __shared__ uint32_t s_count[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t gw = blockIdx.x * kCountWarps + (uint32_t)w;
+    if (gw >= (uint32_t)VS.n * chunks_per_view) return;  // warp-uniform
+    const uint32_t v = gw / chunks_per_view, c = gw - v * chunks_per_view;
+    const ChunkPlace P = chunk_place(VS, view_count, v, c, chunk);
+    if (c >= P.chunks) return;  // warp-uniform: past the view's last chunk
+    const uint32_t b = P.b, e = P.e;
+    const DevView& V = VS.v[v];
+    const uint32_t nt = (uint32_t)(V.tiles_x * V.tiles_y);
+    uint32_t* next = s_count + (size_t)w * (2 * tiles_max + kCountBuf);  // next free slot of each tile
+    uint32_t* mask = next + tiles_max;                                   // lanes of the run reaching each tile
+    uint32_t* buf = mask + tiles_max;
+    for (uint32_t t = lane; t < nt; t += 32) {
+        next[t] = H[P.off + t * P.chunks + c];
+        mask[t] = 0u;
+    }
+    __syncwarp();
+    const uint32_t lt = lanemask_lt(), bit = 1u << lane;
+    for (uint32_t p0 = b; p0 < e; p0 += 32) {  // warp-uniform
+        const uint32_t p = p0 + lane;
+        uint32_t sid = 0, n_t = 0;
+        if (p < e) {
+            sid = sorted[p];
+            n_t = tiles[sid];
+        }
+        uint32_t incl = n_t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        for (int l0 = 0; l0 < 32;) {  // warp-uniform
+            const uint32_t base = __shfl_sync(kFull, incl - n_t, l0);
+            const uint32_t fit = __ballot_sync(kFull, lane >= l0 && incl - base <= kCountBuf);
+            if (fit == 0u) {  // lane l0 alone holds more pairs than the buffer: it walks them by itself
+                if (lane == l0) {
+                    const SplatView r = load_record(rec, rec_fp16, sid, ln_alpha_min);
+                    for_each_tile(r, V, bin, ln_alpha_min, n_t, [&](uint32_t t, uint32_t) {
+                        const uint32_t at_slot = next[t]++;
+                        if (at_slot < capacity) pair_vals[at_slot] = sid;
+                        else atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
+                    });
+                }
+                __syncwarp();
+                l0++;
+                continue;
+            }
+            const int l1 = 32 - __clz(fit);  // lanes l0 .. l1 - 1 (fit is contiguous from l0)
+            const uint32_t mine = (lane >= l0 && lane < l1) ? n_t : 0u;
+            const uint32_t at0 = incl - n_t - base;
+            if (mine > 0) {
+                const SplatView r = load_record(rec, rec_fp16, sid, ln_alpha_min);
+                const uint32_t got = for_each_tile(r, V, bin, ln_alpha_min, mine, [&](uint32_t t, uint32_t k) {
+                    buf[at0 + k] = t;
+                    atomicOr(&mask[t], bit);
+                });
+                for (uint32_t k = got; k < mine; k++) buf[at0 + k] = 0xffffffffu;  // never: the walk repeats the count
+            }
+            __syncwarp();
+#pragma unroll 2
+            for (uint32_t k = 0; k < mine; k++) {
+                const uint32_t t = buf[at0 + k];
+                if (t < nt) {
+                    const uint32_t at_slot = next[t] + __popc(mask[t] & lt);
+                    if (at_slot < capacity) pair_vals[at_slot] = sid;
+                    else atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
+                }
+            }
+            __syncwarp();
+            // the lowest lane of each mask advances its tile and clears the mask (another lane
+            // reads either the mask, in which it is not lowest, or zero)
+#pragma unroll 2
+            for (uint32_t k = 0; k < mine; k++) {
+                const uint32_t t = buf[at0 + k];
+                if (t < nt) {
+                    const uint32_t m = mask[t];
+                    if ((m & lt) == 0u && m != 0u) {
+                        next[t] += __popc(m);
+                        mask[t] = 0u;
+                    }
+                }
+            }
+            __syncwarp();
+            l0 = l1;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_view_of_tile(const ViewSet& VS, uint32_t tile) {
+    int lo = 0, hi = VS.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (VS.v[mid].tile_base <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tile t's list: from its first entry of the scanned counts to the next
+// tile's first entry (the pair total after the last tile), clamped to the
+// capacity; flags a pair total beyond it.
+__global__ void __launch_bounds__(256) count_ranges_kernel(const __grid_constant__ ViewSet VS,
+                                                           const uint32_t* __restrict__ H,
+                                                           const uint32_t* __restrict__ view_count, uint32_t chunk,
+                                                           uint32_t* counters, uint32_t capacity,
+                                                           uint2* __restrict__ ranges) {
+    __shared__ uint32_t s_off[FGS4D_MAX_VIEWS], s_ch[FGS4D_MAX_VIEWS];
+    if (threadIdx.x == 0) {
+        uint32_t off = 0;
+        for (int i = 0; i < VS.n; i++) {
+            const uint32_t ch = (view_count[i] + chunk - 1) / chunk;
+            s_off[i] = off;
+            s_ch[i] = ch;
+            off += (uint32_t)(VS.v[i].tiles_x * VS.v[i].tiles_y) * ch;
+        }
+    }
+    __syncthreads();
+    const uint32_t n_pairs = counters[1], n_entries = counters[8];
+    const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0 && n_pairs > capacity) atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
+    for (uint32_t t = i0; t < VS.total_tiles; t += gridDim.x * blockDim.x) {
+        const int v = find_view_of_tile(VS, t);
+        const uint32_t tl = t - VS.v[v].tile_base;
+        const uint32_t i_s = s_off[v] + tl * s_ch[v], i_e = i_s + s_ch[v];
+        const uint32_t s = i_s < n_entries ? H[i_s] : n_pairs;
+        const uint32_t e = i_e < n_entries ? H[i_e] : n_pairs;
+        ranges[t] = make_uint2(min(s, capacity), min(e, capacity));
+    }
+}
+
+struct LoadPlain {
+    const uint32_t* a;
+    __device__ uint32_t operator()(uint32_t i) const { return a[i]; }
+};
+struct StorePrefix {
+    uint32_t* a;
+    __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { a[i] = prefix; }
+};
+
 static int grid_cap(uint32_t want, int cap) { return (int)(want < (uint32_t)cap ? (want > 0 ? want : 1) : (uint32_t)cap); }
 
 // Visible splats in Gaussian-major order (g, then view): i' = g V + v.
@@ -539,6 +815,77 @@ int pair_sort_bits(uint32_t total_tiles) {
     int bits = 1;
     while (bits < 32 && (1ull << bits) < (unsigned long long)total_tiles) bits++;
     return bits;
+}
+
+// Steps 3-6 of the counting path, after the depth sort left the visible
+// splat ids in (depth, index) order in sv[buf]: a stable pass by view, the
+// (tile, chunk) counts, their scan (-> counters[1]), the scatter and the
+// ranges.
+static cudaError_t count_bin(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int sm_count,
+                             cudaStream_t st, uint32_t* sk[2], uint32_t* sv[2], int buf, int Gs, int* out_buf) {
+    const uint32_t S = (uint32_t)lay.n_splats;
+    const uint32_t n_gauss = S / (uint32_t)VS.n;
+    uint32_t* counters = reinterpret_cast<uint32_t*>(state + lay.counters);
+    uint32_t* tiles = reinterpret_cast<uint32_t*>(state + lay.tiles_touched);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(state + lay.hist);
+    uint32_t* digit_total = hist + kMaxDigits * kSortBlocksMax;
+    uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(state + lay.scan_tmp);
+    uint32_t* H = reinterpret_cast<uint32_t*>(state + lay.chunk_hist);
+    uint32_t* pv = reinterpret_cast<uint32_t*>(state + lay.pair_vals[0]);
+    uint2* ranges = reinterpret_cast<uint2*>(state + lay.ranges);
+    const void* rec = state + lay.records;
+    const int stride_grid = 16 * sm_count;
+    cudaError_t e;
+    *out_buf = 0;
+    // stable pass by view: the list becomes (view, depth, index) ordered and
+    // the pass's digit totals are the visible splats per view
+    const uint32_t* sorted = sv[buf];
+    const uint32_t* view_count = &counters[0];  // one view: all visible splats
+    if (VS.n > 1) {
+        view_keys_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(sv[buf], counters, S, n_gauss,
+                                                                                  sk[buf]);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        uint32_t* k2[2] = {sk[buf], sk[buf ^ 1]};
+        uint32_t* v2[2] = {sv[buf], sv[buf ^ 1]};
+        int vb = 0;
+        e = radix_sort(k2, v2, &counters[0], S, pair_sort_bits((uint32_t)VS.n), hist, digit_total, Gs, st, &vb);
+        if (e != cudaSuccess) return e;
+        sorted = v2[vb];
+        view_count = digit_total;
+    }
+    const uint32_t CH = lay.chunks_per_view, tmax = lay.view_tiles_max;
+    const uint32_t warps = (uint32_t)VS.n * CH;
+    const int blocks = (int)((warps + kCountWarps - 1) / kCountWarps);
+    const size_t smem_hist = (size_t)kCountWarps * tmax * 4;
+    const size_t smem_scatter = (size_t)kCountWarps * (2 * tmax + kCountBuf) * 4;
+    if ((e = cudaFuncSetAttribute((const void*)count_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_hist)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute((const void*)count_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_scatter)) != cudaSuccess)
+        return e;
+    count_hist_kernel<<<blocks, kCountWarps * 32, smem_hist, st>>>(VS, n_gauss, sorted, view_count, rec,
+                                                                   O.record_fp16, O.ln_alpha_min, O.bin, lay.chunk,
+                                                                   CH, tmax, tiles, H, &counters[8]);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the entries in use (counters[8]) are at most total_tiles * chunks_per_view
+    const uint32_t nH = VS.total_tiles * CH;
+    const uint32_t want = (nH + kTileItems - 1) / kTileItems;
+    const int Gh = (int)max(1u, min(want, (uint32_t)min(kScanBlocksMax, 4 * sm_count)));
+    e = device_scan(LoadPlain{H}, StorePrefix{H}, &counters[8], nH, scan_tmp, &counters[1], Gh, st);
+    if (e != cudaSuccess) return e;
+    const uint32_t cap = (uint32_t)lay.capacity;
+    count_scatter_kernel<<<blocks, kCountWarps * 32, smem_scatter, st>>>(
+        VS, n_gauss, sorted, view_count, rec, O.record_fp16, O.ln_alpha_min, O.bin, lay.chunk, CH, tmax, tiles, H,
+        cap, counters, pv);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_ranges_kernel<<<grid_cap((VS.total_tiles + 255) / 256, stride_grid), 256, 0, st>>>(
+        VS, H, view_count, lay.chunk, counters, cap, ranges);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayout& lay, char* state, int sm_count,
@@ -580,8 +927,9 @@ cudaError_t launch_bin_sort(const ViewSet& VS, const DevOpts& O, const StateLayo
     e = radix_sort(sk, sv, &counters[0], S, 32, hist, digit_total, Gs, st, &buf);
     if (e != cudaSuccess) return e;
     const uint32_t* sorted = sv[buf];
-    // 3. exact tile counts (support ellipse), then pair offsets in depth order -> counters[1]
     const int stride_grid = 16 * sm_count;
+    if (lay.count_sort) return count_bin(VS, O, lay, state, sm_count, st, sk, sv, buf, Gs, out_buf);
+    // 3. exact tile counts (support ellipse), then pair offsets in depth order -> counters[1]
     ellipse_count_kernel<<<grid_cap((S + 255) / 256, stride_grid), 256, 0, st>>>(
         VS, (uint32_t)(S / (uint32_t)VS.n), sorted, rec, O.record_fp16, O.ln_alpha_min, S, counters, O.bin, tiles);
     count_launches(1);

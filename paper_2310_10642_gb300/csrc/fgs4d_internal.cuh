@@ -94,18 +94,29 @@ struct StateLayout {
     size_t grad2d;         // float4[3 * V*n] per-splat 2D gradient
     size_t aux;            // float4[V*n] depth, flow u, flow v (0 when aux channels are off)
     size_t gsum;           // float[11][n] per-Gaussian sums of the projection adjoint
-    size_t pair_keys[2];   // uint32[capacity] double buffer
-    size_t pair_vals[2];   // uint32[capacity]
+    size_t chunk_hist;     // uint32[total_tiles * chunks_per_view]: (tile, chunk) counts (counting path only)
+    size_t pair_keys[2];   // uint32[capacity] double buffer (radix path only)
+    size_t pair_vals[2];   // uint32[capacity] (the counting path uses pair_vals[0] alone)
     size_t fixed_bytes;    // everything above except the pair buffers
     size_t total;
     int64_t capacity;
     int64_t n_splats;      // V * n
     uint32_t record_bytes;
+    // Pair binning by a stable counting sort over (tile, chunk) counts when
+    // every view has at most kCountTilesMax binning tiles; otherwise by a
+    // radix sort of the pairs on their tile id.
+    int count_sort;
+    uint32_t chunk;            // visible splats per chunk (a power of two)
+    uint32_t chunks_per_view;  // ceil(n / chunk): a view has at most n visible splats (chunks in use: device)
+    uint32_t view_tiles_max;   // binning tiles of the largest view
 };
 
 constexpr int kScanBlocksMax = 1024;
 constexpr int kSortBlocksMax = 1024;
 constexpr int kMaxDigits = 512;  // radix digits of at most 9 bits
+constexpr uint32_t kCountTilesMax = 4096;  // binning tiles per view for the counting path
+constexpr int kCountWarps = 4;              // warps per block of the counting kernels, one chunk each
+constexpr uint32_t kCountBuf = 1024;        // pairs a warp of the scatter stages per round of 32 splats
 
 // Splat record (FP32): 48 bytes, three 16-byte vectors.
 //   r0 = (u, v, conic_a, conic_b)   r1 = (conic_c, alpha_eff, R, G)
@@ -592,8 +603,10 @@ __device__ __forceinline__ bool ellipse_row_span(const EllipseRows& e, const Dev
     if (!(lo <= hi)) return false;
     const float yl = fminf(fmaxf(e.dyl, lo), hi), yr = fminf(fmaxf(-e.dyl, lo), hi);
     const float ql = yl * e.irys, qr = yr * e.irys;
-    const float xl = -e.ba * yl - sqrt_approx(fmaxf(e.ks * (1.0f - ql * ql), 0.0f) * e.ia);
-    const float xr = -e.ba * yr + sqrt_approx(fmaxf(e.ks * (1.0f - qr * qr), 0.0f) * e.ia);
+    // explicit fused operations: every kernel that walks these spans (the
+    // pair count, the pair scatter, the raster masks) rounds them alike
+    const float xl = __fmaf_rn(-e.ba, yl, -sqrt_approx(fmaxf(e.ks * __fmaf_rn(-ql, ql, 1.0f), 0.0f) * e.ia));
+    const float xr = __fmaf_rn(-e.ba, yr, sqrt_approx(fmaxf(e.ks * __fmaf_rn(-qr, qr, 1.0f), 0.0f) * e.ia));
     *px0 = fmaxf(ceilf(e.u + xl - 0.5f), 0.0f);
     *px1 = fminf(floorf(e.u + xr + 0.5f), (float)(V.width - 1));
     return *px0 <= *px1;

@@ -68,7 +68,10 @@ def test_state_size_grows_with_capacity(lib):
     v = _views()
     a = N.fgs4d_state_size(1000, v, 2, 0, o)
     b = N.fgs4d_state_size(1000, v, 2, 100000, o)
-    assert b - a >= 16 * 100000
+    assert 4 * 100000 <= b - a < 4 * 100000 + 1024  # counting path: one array of splat ids
+    # a view of more than 4096 binning tiles takes the radix path (keys and values, double-buffered)
+    big = N.make_views([I.view((0, 0, 4), 1600, 1400, 0.5)])  # 100 x 88 tiles of 16 pixels
+    assert N.fgs4d_state_size(1000, big, 1, 100000, o) - N.fgs4d_state_size(1000, big, 1, 0, o) >= 16 * 100000
     info = N.fgs4d_state_layout(1000, v, 2, o, b)
     assert 100000 <= info.pair_capacity < 100000 + 64 and info.n_splats == 2000
     assert info.total_tiles == 2 * 7 * 4

@@ -172,32 +172,21 @@ def test_slice_project_records_match_oracle():
 
 
 def large_splat_scene():
-    """Splats from a few pixels to most of a 320x240 view: a warp's 32
-    consecutive splats then own more pairs than its emission buffer holds."""
+    """Splats from a few pixels to most of a 320x240 view: at 16-pixel bins
+    some 32 consecutive splats own more pairs than the scatter's staging
+    buffer holds."""
     G = I.gaussians(400, 31, 3, 2, log_s_xyz=(-2.0, 1.0))
     views = [I.view((0.2, 0.1, 4.0), 320, 240, 0.4), I.view((-1.5, 0.5, 3.5), 200, 150, 0.6)]
     return G, views
 
 
-@TILE_BINS
-@pytest.mark.parametrize("scene", ["ragged", "large"])
-def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
-    """Every splat is listed in the binning tiles its support ellipse reaches
-    (R7 with slack): within its support box, once per tile, as many tiles as
-    slice/project counted, and in every tile holding a pixel where the
-    record's own alpha (in FP64) clears alpha_min; each tile's list is in
-    (depth, index) order.  The lists are per binning tile (bin x bin
-    pixels), whatever the compositing tile.  The two scenes take both ways
-    out of the emission: on average a warp's 32 splats own fewer pairs than
-    its 512-pair buffer (ragged) or more (large splats at 16-pixel bins)."""
-    G, views = ragged_scene(n=2500, seed=14) if scene == "ragged" else large_splat_scene()
-    fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
-    per_warp = 32 * fr.last_counters.n_pairs / max(fr.last_counters.n_visible, 1)
-    if scene == "ragged":
-        assert per_warp < 512  # some warp's pairs fit its buffer
-    elif bin == 16:
-        assert per_warp > 512  # some warp's pairs overflow it and are written directly
-    tile = bin  # the geometry below is that of the binning tiles
+def check_tile_lists(G, views, fr, tile):
+    """Every splat is listed in the binning tiles (tile x tile pixels) its
+    support ellipse reaches (R7 with slack): within its support box, once
+    per tile, as many tiles as the binning counted, and in every tile holding
+    a pixel where the record's own alpha (in FP64) clears alpha_min; each
+    tile's list is in (depth, index) order.  Returns (listed pairs, box
+    tiles)."""
     rec, tiles, ranges, vals = read_state(fr)
     n = G["logit"].shape[0]
     amin = 1.0 / 255.0
@@ -231,8 +220,74 @@ def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
             listed_total += len(got)
         tile_base += tx_n * ((v["height"] + tile - 1) // tile)
     assert tile_base == ranges.shape[0]
-    print(f"[bin] bin {tile}: {listed_total} pairs vs {box_total} box tiles ({listed_total / box_total:.3f})")
+    assert sum(len(x) for x in listed.values()) == int(fr.last_counters.n_pairs)
+    return listed_total, box_total
+
+
+def huge_splat_scene():
+    """A 720x560 view (1575 binning tiles of 16 pixels) with a few splats
+    whose support ellipse reaches more than 1024 of them."""
+    G = I.gaussians(150, 33, 3, 2, log_s_xyz=(-2.0, 0.8))
+    return G, [I.view((0.0, 0.2, 3.0), 720, 560, 0.5)]
+
+
+@TILE_BINS
+@pytest.mark.parametrize("scene", ["ragged", "large", "huge"])
+def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
+    """The lists of check_tile_lists, per binning tile (bin x bin pixels)
+    whatever the compositing tile.  The scenes take every way through the
+    pair scatter (a warp stages the pairs of 32 consecutive splats in a
+    1024-entry buffer): rounds whose pairs fit the buffer (ragged), rounds
+    that go through it in runs of lanes (large splats at 16-pixel bins), and
+    single splats with more pairs than it holds, walked alone (huge, at
+    16-pixel bins)."""
+    G, views = {"ragged": lambda: ragged_scene(n=2500, seed=14), "large": large_splat_scene,
+                "huge": huge_splat_scene}[scene]()
+    fr, _, _, _ = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
+    # rounds of the scatter: 32 consecutive splats of a view's (depth, index) ordered run (the
+    # few visible splats whose ellipse reaches no tile hold no pairs and are left out here)
+    rec, tiles, _, _ = read_state(fr)
+    n = G["logit"].shape[0]
+    rounds = []
+    for vi in range(len(views)):
+        vis = [vi * n + g for g in np.nonzero(tiles[vi * n:(vi + 1) * n])[0]]
+        run = [int(tiles[sid]) for sid in sorted(vis, key=lambda sid: (rec[sid, 9], sid))]
+        rounds += [sum(run[k:k + 32]) for k in range(0, len(run), 32)]
+    if scene == "ragged":
+        assert min(rounds) <= 1024  # a round whose pairs fit the warp's staging buffer
+    if scene == "large" and bin == 16:
+        assert max(rounds) > 1024  # and one whose pairs do not
+    if scene == "huge" and bin == 16:
+        assert tiles.max() > 1024  # a splat with more pairs than the buffer
+    listed_total, box_total = check_tile_lists(G, views, fr, bin)
+    print(f"[bin] bin {bin}: {listed_total} pairs vs {box_total} box tiles ({listed_total / box_total:.3f})")
     assert listed_total < box_total  # the ellipse drops tiles the box would keep
+
+
+def test_views_over_8192_tiles_take_the_radix_path():
+    """A view with more than 4096 binning tiles (1600 x 1400 pixels at
+    16-pixel bins: 100 x 88) is binned by a radix sort of the pairs on their
+    tile id instead of the counting sort (the state then holds keys and
+    values, double-buffered: 16 bytes per pair instead of 4).  Its lists pass
+    the same checks, and its image and T equal, bit for bit, those of
+    32-pixel bins, which take the counting path."""
+    from paper_2310_10642_gb300 import native as N
+    G = I.gaussians(6000, 43, 3, 2, log_s_xyz=(-2.5, 0.8))
+    views = [I.view((0.2, 0.3, 3.6), 1600, 1400, 0.45), I.view((-1.0, 0.4, 3.0), 90, 70, 0.2)]
+    out = {}
+    for b in (16, 32):
+        opts = dict(tile_size=16, bin_size=b)
+        fr, _, imgs, Ts = gpu_forward(G, views, opts)
+        per_pair = (N.fgs4d_state_size(6000, fr.c_views, 2, 1000, fr.c_opts) -
+                    N.fgs4d_state_size(6000, fr.c_views, 2, 0, fr.c_opts)) / 1000
+        assert per_pair >= (16 if b == 16 else 4) and per_pair < (17 if b == 16 else 5), per_pair
+        assert fr.counters().status == 0 and fr.last_counters.n_pairs > 10000
+        check_tile_lists(G, views, fr, b)
+        out[b] = (imgs, Ts)
+    for k in range(2):
+        np.testing.assert_array_equal(out[16][0][k], out[32][0][k])
+        np.testing.assert_array_equal(out[16][1][k], out[32][1][k])
+    assert out[16][0][0].max() > 0.1  # not a blank frame
 
 
 @TILE_BINS
