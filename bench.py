@@ -682,13 +682,25 @@ def main():
     rd_b = 32 if mixed else 36    # record bytes a tile stages per list entry
     V = len(views)
     nvis, npairs = counters.n_visible, counters.n_pairs
+    binsz = opts.get("bin_size") or opts["tile_size"]
+    view_tiles = [-(-v["width"] // binsz) * -(-v["height"] // binsz) for v in views]
+    if max(view_tiles) <= 4096:
+        # counting-sort path: compaction (read tile counts + depth keys, write 8 B per visible splat), depth
+        # sort (4 passes x 20 B), view keys (8 B) and view pass (20 B), histogram walk (id, record, count
+        # written) and scatter walk (id, count, record) per visible splat, the (tile, chunk) counts written,
+        # scanned (read twice, written once) and read back, and 4 B per pair written
+        entries = sum(t * -(-nvis // (V * 256)) for t in view_tiles)
+        bin_bytes = (V * n * 8 + nvis * (8 + 4 * 20 + 8 + 20 + (4 + rec_b + 4) + (8 + rec_b))
+                     + entries * (4 + 12 + 4) + npairs * 4)
+    else:
+        # radix path: compaction, depth sort, offsets scan (8 B), emission (8 B per pair), pair sort (passes x
+        # 20 B per pair), ranges (4 B per pair)
+        bin_bytes = (V * n * 8 + nvis * (8 + 4 * 20 + 8) + npairs * (8 + 4)
+                     + npairs * 20 * ((_bits(frame.layout().total_tiles) + 7) // 8))
     alg = {
         # parameters read once + records/tile counts/depth keys written
         "slice_project": n * (17 * 4 + C * shs_b) + nvis * rec_b + V * n * 8,
-        # compaction (read tile counts + depth keys, write 8 B per visible splat), depth sort (4 passes x 20 B),
-        # offsets scan (8 B), emission (8 B per pair), pair sort (passes x 20 B per pair), ranges (4 B per pair)
-        "bin_sort": V * n * 8 + nvis * (8 + 4 * 20 + 8) + npairs * (8 + 4)
-        + npairs * 20 * ((_bits(frame.layout().total_tiles) + 7) // 8),
+        "bin_sort": bin_bytes,
         # list ids + gathered records per pair, 20 B written per pixel
         "render": npairs * (4 + rd_b) + npix * 20,
         # same gathers + dL/dimage, T, n_last per pixel + 48 B gradient record per splat (zeroed) and per

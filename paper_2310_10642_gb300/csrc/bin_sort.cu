@@ -633,12 +633,13 @@ __global__ void __launch_bounds__(kCountWarps * 32) count_hist_kernel(
 
 // Per (view, chunk) warp, after the exclusive scan of H: writes the chunk's
 // splat ids to their slots of the tile-major pair array.  Per round of 32
-// splats, each lane walks its splat's tiles into the warp's buffer and sets
-// its bit in each tile's lane mask (shared atomic OR); a splat's slot in
-// tile t is then the tile's next free slot plus the number of lower lanes
-// (earlier splats) in the mask, and the lowest lane advances the tile by the
-// mask's population and clears it.  So every tile's slots are taken in list
-// order.  A round with more pairs than the buffer holds goes through it in
+// splats, each lane walks its splat's tiles into the warp's buffer, as
+// (tile << 5 | lane), and sets its bit in each tile's lane mask (shared
+// atomic OR); the warp then takes the buffer 32 entries at a time: a
+// splat's slot in tile t is the tile's next free slot plus the number of
+// lower lanes (earlier splats) in the mask, and the entry of the mask's
+// lowest lane advances the tile by the mask's population and clears it.  So
+// every tile's slots are taken in list order.  A round with more pairs than the buffer holds goes through it in
 // runs of consecutive lanes; a splat with more pairs than the buffer holds
 // walks them alone.
 __global__ void __launch_bounds__(kCountWarps * 32) count_scatter_kernel(
@@ -695,35 +696,40 @@ __global__ void __launch_bounds__(kCountWarps * 32) count_scatter_kernel(
                 continue;
             }
             const int l1 = 32 - __clz(fit);  // lanes l0 .. l1 - 1 (fit is contiguous from l0)
-            const uint32_t mine = (lane >= l0 && lane < l1) ? n_t : 0u;
-            const uint32_t at0 = incl - n_t - base;
-            if (mine > 0) {
+            const uint32_t total = __shfl_sync(kFull, incl, l1 - 1) - base;
+            if (lane >= l0 && lane < l1 && n_t > 0) {
+                const uint32_t at0 = incl - n_t - base;
+                const uint32_t tag = (uint32_t)lane;
                 const SplatView r = load_record(rec, rec_fp16, sid, ln_alpha_min);
-                const uint32_t got = for_each_tile(r, V, bin, ln_alpha_min, mine, [&](uint32_t t, uint32_t k) {
-                    buf[at0 + k] = t;
+                const uint32_t got = for_each_tile(r, V, bin, ln_alpha_min, n_t, [&](uint32_t t, uint32_t k) {
+                    buf[at0 + k] = t << 5 | tag;
                     atomicOr(&mask[t], bit);
                 });
-                for (uint32_t k = got; k < mine; k++) buf[at0 + k] = 0xffffffffu;  // never: the walk repeats the count
+                for (uint32_t k = got; k < n_t; k++) buf[at0 + k] = 0xffffffffu;  // never: the walk repeats the count
             }
             __syncwarp();
-#pragma unroll 2
-            for (uint32_t k = 0; k < mine; k++) {
-                const uint32_t t = buf[at0 + k];
+            // the run's entries 32 at a time: slot of (tile t, owner lane o) = next[t] + lanes below o in the mask
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {  // warp-uniform
+                const uint32_t q = q0 + (uint32_t)lane;
+                const uint32_t ent = q < total ? buf[q] : 0xffffffffu;
+                const uint32_t t = ent >> 5, o = ent & 31u;
+                const uint32_t src = __shfl_sync(kFull, sid, (int)o);
                 if (t < nt) {
-                    const uint32_t at_slot = next[t] + __popc(mask[t] & lt);
-                    if (at_slot < capacity) pair_vals[at_slot] = sid;
+                    const uint32_t at_slot = next[t] + __popc(mask[t] & ((1u << o) - 1u));
+                    if (at_slot < capacity) pair_vals[at_slot] = src;
                     else atomicOr(&counters[2], FGS4D_STATUS_PAIR_OVERFLOW);
                 }
             }
             __syncwarp();
-            // the lowest lane of each mask advances its tile and clears the mask (another lane
-            // reads either the mask, in which it is not lowest, or zero)
-#pragma unroll 2
-            for (uint32_t k = 0; k < mine; k++) {
-                const uint32_t t = buf[at0 + k];
+            // the entry of each mask's lowest lane advances its tile and clears the mask (another
+            // entry of the tile reads either the mask, whose lowest lane it is not, or zero)
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {  // warp-uniform
+                const uint32_t q = q0 + (uint32_t)lane;
+                const uint32_t ent = q < total ? buf[q] : 0xffffffffu;
+                const uint32_t t = ent >> 5, o = ent & 31u;
                 if (t < nt) {
                     const uint32_t m = mask[t];
-                    if ((m & lt) == 0u && m != 0u) {
+                    if (m != 0u && (uint32_t)(__ffs(m) - 1) == o) {
                         next[t] += __popc(m);
                         mask[t] = 0u;
                     }

@@ -182,6 +182,32 @@ __device__ __forceinline__ SplatView decode_record(const SplatRecord& r, float) 
     return SplatView{r.r0.x, r.r0.y, r.r0.z, r.r0.w, r.r1.x, r.r1.y, r.r1.z, r.r1.w, r.r2.x, r.r2.z, r.r2.w,
                      0.0f,   0.0f,   0.0f};
 }
+// Hardware approximations (about one to two ulp) for the support ellipse's
+// set-up (ellipse_rows): its spans carry half a pixel (and k 0.2%) of slack,
+// far above their error, and every kernel rounds them alike.  (The support
+// box of decode_record keeps the IEEE forms: with them the adjoint raster
+// kernel, which decodes every staged record, schedules faster.)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// natural log through the hardware base-2 log
+__device__ __forceinline__ float ln_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return __fmul_rn(y, 0.69314718055994531f);
+}
+// k = 2 ln(alpha_eff / alpha_min), 0 when alpha_eff <= alpha_min
+__device__ __forceinline__ float support_k(float alpha_eff, float ln_alpha_min) {
+    return 2.0f * fmaxf(__fsub_rn(ln_approx(alpha_eff), ln_alpha_min), 0.0f);
+}
+
 // ln_alpha_min = log(alpha_min).  With Sigma = Q^-1: Sigma_11 = 1 / l22^2 and
 // Sigma_00 = (l21^2 + l22^2) / (l11 l22)^2, so the support box
 // |dx| <= sqrt(k Sigma_00), |dy| <= sqrt(k Sigma_11), k = 2 ln(alpha_eff /
@@ -545,10 +571,11 @@ __device__ __forceinline__ int box_tiles(float u, float v, float hx, float hy, c
     const float fy0 = fmaxf(ceilf(v - hy), 0.0f);
     const float fy1 = fminf(floorf(v + hy), (float)(V.height - 1));
     if (!(fx0 <= fx1 && fy0 <= fy1)) return 0;
-    rect[0] = (int)fx0 / tile;
-    rect[1] = (int)fy0 / tile;
-    rect[2] = (int)fx1 / tile;
-    rect[3] = (int)fy1 / tile;
+    const int sh = __ffs(tile) - 1;  // tile is a power of two; the pixel bounds are >= 0
+    rect[0] = (int)fx0 >> sh;
+    rect[1] = (int)fy0 >> sh;
+    rect[2] = (int)fx1 >> sh;
+    rect[3] = (int)fy1 >> sh;
     return (rect[2] - rect[0] + 1) * (rect[3] - rect[1] + 1);
 }
 
@@ -574,24 +601,17 @@ __device__ __forceinline__ EllipseRows ellipse_rows(const SplatView& r, float ln
     e.u = r.u;
     e.v = r.v;
     constexpr float kSlack = 1.002f;
-    const float k = 2.0f * fmaxf(logf(r.alpha_eff) - ln_alpha_min, 0.0f);
+    constexpr float kSqrtSlack = 1.0009995f;  // sqrt(kSlack)
+    const float k = support_k(r.alpha_eff, ln_alpha_min);
     const float rx = r.hx - 0.5f, ry = r.hy - 0.5f;
     e.exact = r.a > 0.0f && r.c > 0.0f && rx > 0.0f && ry > 0.0f && k > 0.0f;
-    e.ba = e.exact ? r.b / r.a : 0.0f;
-    e.ia = e.exact ? 1.0f / r.a : 0.0f;
-    e.ks = k * kSlack;
-    e.rys = ry * sqrtf(kSlack);
-    e.irys = e.exact ? 1.0f / e.rys : 0.0f;
-    e.dyl = e.exact ? (r.b / r.c) * rx * sqrtf(kSlack) : 0.0f;
+    e.ia = e.exact ? rcp_approx(r.a) : 0.0f;
+    e.ba = e.exact ? __fmul_rn(r.b, e.ia) : 0.0f;
+    e.ks = __fmul_rn(k, kSlack);
+    e.rys = __fmul_rn(ry, kSqrtSlack);
+    e.irys = e.exact ? rcp_approx(e.rys) : 0.0f;
+    e.dyl = e.exact ? __fmul_rn(__fmul_rn(__fmul_rn(r.b, rcp_approx(r.c)), rx), kSqrtSlack) : 0.0f;
     return e;
-}
-
-// The hardware square root (about one ulp): the spans carry half a pixel of
-// slack, far more than its error.
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
 }
 
 // Pixel columns [*px0, *px1] reached by the ellipse over the pixel rows

@@ -406,13 +406,8 @@ __global__ void __launch_bounds__(kTilePix, 4) render_fwd_kernel(const __grid_co
     }
 }
 
-// 1/x to within about one ulp (the hardware approximation); recovering T
-// back to front through ~10^2..10^3 of these stays within ~1e-4 relative.
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
+// (rcp_approx, 1/x to within about one ulp: recovering T back to front
+// through ~10^2..10^3 of these stays within ~1e-4 relative.)
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll

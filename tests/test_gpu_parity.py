@@ -264,7 +264,7 @@ def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
     assert listed_total < box_total  # the ellipse drops tiles the box would keep
 
 
-def test_views_over_8192_tiles_take_the_radix_path():
+def test_views_over_4096_tiles_take_the_radix_path():
     """A view with more than 4096 binning tiles (1600 x 1400 pixels at
     16-pixel bins: 100 x 88) is binned by a radix sort of the pairs on their
     tile id instead of the counting sort (the state then holds keys and
