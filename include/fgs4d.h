@@ -196,9 +196,10 @@ const char *fgs4d_status_string(fgs4d_status status);
 void fgs4d_default_options(fgs4d_options *opt);
 
 /* Bytes of per-frame state needed for n Gaussians, these views and room for
-   pair_capacity (splat, tile) pairs.  The same n, views and pair capacity must
-   be used by every call that receives this state.  Returns INVALID_ARG for
-   bad sizes. */
+   pair_capacity (splat, tile) pairs (4 bytes per pair on the counting-sort
+   path of fgs4d_bin_sort, 16 on its radix path).  The same n, views and pair
+   capacity must be used by every call that receives this state.  Returns
+   INVALID_ARG for bad sizes. */
 fgs4d_status fgs4d_state_size(int64_t n, const fgs4d_view *views, int n_views, int64_t pair_capacity,
                               const fgs4d_options *opt, size_t *bytes);
 
@@ -215,7 +216,10 @@ fgs4d_status fgs4d_slice_project(const fgs4d_gaussians *g, const fgs4d_view *vie
 
 /* Bin the splats to the binning tiles (bin_size x bin_size pixels) their
    support ellipse reaches and order each tile's list by (depth, Gaussian
-   index) with the library's on-device radix sort (Sec. 3.1/3.2).
+   index) on the device (Sec. 3.1/3.2): a radix sort of the visible splats by
+   depth, then a stable counting sort of the (tile, splat) pairs when every
+   view has at most 4096 binning tiles, else a stable radix sort of the pairs
+   by tile id.  Both give the same lists.
    Pairs beyond the capacity are dropped and FGS4D_STATUS_PAIR_OVERFLOW is set. */
 fgs4d_status fgs4d_bin_sort(int64_t n, const fgs4d_view *views, int n_views, const fgs4d_options *opt, void *state,
                             size_t state_bytes, fgs4d_stream stream);

@@ -3,19 +3,22 @@
 // "Tile" here is a binning tile (bin_size pixels square).  Each tile's list
 // must be ordered by (depth, Gaussian index) (Sec. 3.1: splats are blended in
 // depth order; ties broken by index).  Instead of one radix sort of 64-bit
-// (tile | depth) keys over all (splat, tile) pairs, the pipeline sorts the
-// visible splats once by depth and then stable-sorts the pairs by tile id
-// alone:
+// (tile | depth) keys over all (splat, tile) pairs, the visible splats are
+// sorted once by depth and the pairs are then placed by tile keeping that
+// order:
 //   1. compact the visible (view, Gaussian) splats in index order
 //   2. stable LSD radix sort of the compacted splats by depth (32-bit keys)
-//   3. count the tiles each visible splat's support ellipse reaches, and an
-//      exclusive scan of the counts in depth order -> pair offsets
-//   4. emit one (global tile id, splat id) pair per reached tile
-//   5. stable LSD radix sort of the pairs by tile id (only the bits in use)
-//   6. per-tile [start, end) ranges
-// Stability of both sorts makes each tile's list come out in (depth, index)
-// order.  The pair sort moves 8 bytes per pair per pass over ceil(bits/8)
-// passes instead of 12 bytes over ~6 passes of a (tile|depth) sort.
+//   3. counting path (every view has at most kCountTilesMax binning tiles):
+//      a stable pass by view, per-chunk tile counts, one scan of them, and
+//      an ordered scatter of the splat ids into the tiles' lists (see
+//      "Counting-sort binning" below); or
+//   3'. radix path (larger views): count the tiles each visible splat's
+//      support ellipse reaches, scan the counts in depth order into pair
+//      offsets, emit one (global tile id, splat id) pair per reached tile,
+//      stable LSD radix sort of the pairs by tile id (only the bits in use)
+//   4. per-tile [start, end) ranges
+// Stability makes each tile's list come out in (depth, index) order on both
+// paths.
 //
 // All counts that depend on the data (visible splats, pairs) stay on the
 // device; grids are sized from capacities and every block derives its share
@@ -601,7 +604,7 @@ __device__ __forceinline__ SplatView load_record(const void* rec, int rec_fp16, 
 // count, as the radix path's count kernel leaves it.  Warp 0 also stores
 // the number of entries of H in use to *n_entries.
 __global__ void __launch_bounds__(kCountWarps * 32) count_hist_kernel(
-    const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted,
+    const __grid_constant__ ViewSet VS, const uint32_t* __restrict__ sorted,
     const uint32_t* __restrict__ view_count, const void* __restrict__ rec, int rec_fp16, float ln_alpha_min, int bin,
     uint32_t chunk, uint32_t chunks_per_view, uint32_t tiles_max, uint32_t* __restrict__ tiles,
     uint32_t* __restrict__ H, uint32_t* __restrict__ n_entries) {
@@ -643,7 +646,7 @@ __global__ void __launch_bounds__(kCountWarps * 32) count_hist_kernel(
 // runs of consecutive lanes; a splat with more pairs than the buffer holds
 // walks them alone.
 __global__ void __launch_bounds__(kCountWarps * 32) count_scatter_kernel(
-    const __grid_constant__ ViewSet VS, uint32_t n_gauss, const uint32_t* __restrict__ sorted,
+    const __grid_constant__ ViewSet VS, const uint32_t* __restrict__ sorted,
     const uint32_t* __restrict__ view_count, const void* __restrict__ rec, int rec_fp16, float ln_alpha_min, int bin,
     uint32_t chunk, uint32_t chunks_per_view, uint32_t tiles_max, const uint32_t* __restrict__ tiles,
     const uint32_t* __restrict__ H, uint32_t capacity, uint32_t* counters, uint32_t* __restrict__ pair_vals) {
@@ -871,7 +874,7 @@ static cudaError_t count_bin(const ViewSet& VS, const DevOpts& O, const StateLay
     if ((e = cudaFuncSetAttribute((const void*)count_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_scatter)) != cudaSuccess)
         return e;
-    count_hist_kernel<<<blocks, kCountWarps * 32, smem_hist, st>>>(VS, n_gauss, sorted, view_count, rec,
+    count_hist_kernel<<<blocks, kCountWarps * 32, smem_hist, st>>>(VS, sorted, view_count, rec,
                                                                    O.record_fp16, O.ln_alpha_min, O.bin, lay.chunk,
                                                                    CH, tmax, tiles, H, &counters[8]);
     count_launches(1);
@@ -884,7 +887,7 @@ static cudaError_t count_bin(const ViewSet& VS, const DevOpts& O, const StateLay
     if (e != cudaSuccess) return e;
     const uint32_t cap = (uint32_t)lay.capacity;
     count_scatter_kernel<<<blocks, kCountWarps * 32, smem_scatter, st>>>(
-        VS, n_gauss, sorted, view_count, rec, O.record_fp16, O.ln_alpha_min, O.bin, lay.chunk, CH, tmax, tiles, H,
+        VS, sorted, view_count, rec, O.record_fp16, O.ln_alpha_min, O.bin, lay.chunk, CH, tmax, tiles, H,
         cap, counters, pv);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
