@@ -264,6 +264,31 @@ def test_tile_lists_are_depth_ordered_and_complete(tile, bin, scene):
     assert listed_total < box_total  # the ellipse drops tiles the box would keep
 
 
+@pytest.mark.parametrize("n", [768, 769])
+@pytest.mark.parametrize("tile,bin", [(16, 16), (32, 64)])
+def test_binning_chunks_at_view_edges(n, tile, bin):
+    """The counting path cuts each view's depth-ordered run of visible splats
+    into chunks of 256.  Here every Gaussian is visible in the first and the
+    last view (n = 768: three full chunks; 769: a fourth chunk of one
+    splat) and none in the middle view, which looks away (no chunk at all:
+    its tiles' lists are empty).  Lists as check_tile_lists, images and T
+    against the oracle."""
+    G = I.gaussians(n, 47, 2, 1, log_s_xyz=(-3.5, 0.4))
+    t = 0.4
+    G["mu"][3] = t  # centred in time: p(t) = 1, no splat fails the temporal filter
+    views = [I.view((0.3, 0.2, 4.0), 160, 120, t, fov_x_deg=60.0),
+             I.view((0.0, 0.0, 4.0), 96, 64, t, target=(0.0, 0.0, 8.0), bg=(0.3, 0.5, 0.7)),
+             I.view((-3.5, 0.5, 1.5), 130, 100, t, fov_x_deg=60.0, bg=(1.0, 1.0, 1.0))]
+    fr, _, imgs, Ts = gpu_forward(G, views, dict(tile_size=tile, bin_size=bin))
+    per_view = [O.render(G, v) for v in views]
+    assert [r["n_visible"] for r in per_view] == [n, 0, n]
+    assert fr.last_counters.n_visible == 2 * n
+    check_tile_lists(G, views, fr, bin)
+    for img, T, ref in zip(imgs, Ts, per_view):
+        assert_image_parity(img, T, ref)
+    assert np.allclose(imgs[1], np.array([0.3, 0.5, 0.7])[:, None, None]) and np.all(Ts[1] == 1.0)
+
+
 def test_views_over_4096_tiles_take_the_radix_path():
     """A view with more than 4096 binning tiles (1600 x 1400 pixels at
     16-pixel bins: 100 x 88) is binned by a radix sort of the pairs on their
