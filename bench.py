@@ -787,11 +787,35 @@ def main():
         clocks_e2e.start()
         time.sleep(0.3)
         e0.record(stream)
+        t_host = time.perf_counter()
         pipe.run([(host_p, host_dL)] * ks, [(host_img, host_g)] * ks)
+        t_host = time.perf_counter() - t_host
         e1.record(stream)
         torch.cuda.synchronize()
         clk_e2e = clocks_e2e.stop()
         ms_e2e = e0.elapsed_time(e1) / ks
+        # the same pipeline with the copies left out (compute through its graphs and event waits only), and
+        # with the copies of each direction alone: how much of the gap to the device step the copies make
+        def pipe_pieces(do_in, do_out, k_steps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pipe.s_in.wait_stream(stream)
+            if do_in:
+                pipe._copy_in(pipe.slots[0], host_p, host_dL)
+            for k_ in range(k_steps):
+                if do_in and k_ + 1 < k_steps:
+                    pipe._copy_in(pipe.slots[(k_ + 1) % 2], host_p, host_dL)
+                pipe._compute(pipe.slots[k_ % 2])
+                if do_out:
+                    pipe._copy_out(pipe.slots[k_ % 2], host_img, host_g)
+            stream.wait_stream(pipe.s_out)
+            stream.wait_stream(pipe.s_in)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return round(a.elapsed_time(b) / k_steps, 3)
+        pieces_ms = dict(compute_only=pipe_pieces(False, False, ks), with_copies_in=pipe_pieces(True, False, ks),
+                         with_copies_out=pipe_pieces(False, True, ks), all=pipe_pieces(True, True, ks))
 
         # the copies alone on this machine (same buffers, the pipeline's copy streams): in, out, both at once
         def copies(kind):
@@ -821,7 +845,9 @@ def main():
 
         copy_ms = {k_: copies(k_) for k_ in ("in", "out", "both")}
         e2e = dict(value=npix * world / (ms_e2e * 1e-3) / 1e6, unit="Mpix/s", h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h), ms_per_step=ms_e2e, copies_alone_ms=copy_ms, clocks=clk_e2e,
+                   d2h_bytes_per_step=int(d2h), ms_per_step=ms_e2e, copies_alone_ms=copy_ms,
+                   host_enqueue_ms_per_step=round(t_host * 1e3 / ks, 3), pipeline_pieces_ms=pieces_ms,
+                   clocks=clk_e2e,
                    pipeline="inputs of step k+1 in and outputs of step k-1 out on copy streams while step k "
                             "computes (each buffer set's step replayed as a CUDA graph)")
 
